@@ -1,0 +1,362 @@
+/*
+ * mpcd_oracle.c -- FP64 CPU oracle for one SRD time step.
+ *
+ * TEST INFRASTRUCTURE ONLY: it is the slow, plain statement that the CUDA path is checked
+ * against, and nothing in the library calls it.  Compile with -ffp-contract=off: the only
+ * fused multiply-adds are the explicit fma() calls below.
+ *
+ * The method (arXiv 2212.11878, Sec. 2): particles stream, the collision grid is shifted at
+ * random every step, particles are sorted into the shifted cells (Sec. 3.1, Listing 1), each
+ * cell's mass and momentum are summed (Sec. 3.3, Listing 4), and each particle's velocity
+ * relative to the cell's centre of mass is split along a random axis and its perpendicular
+ * part rotated by a fixed angle (Sec. 2, parts (i)-(iii)).  The readings R1..R14 that fill in
+ * what the paper leaves open are listed in mpcd_oracle.h.
+ */
+#include "mpcd_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+static const double ORC_PI = 3.14159265358979323846;
+
+/* ---------------------------------------------------------------- Philox4x64-10 ---- */
+/* Salmon et al., "Parallel random numbers: as easy as 1, 2, 3", SC'11, Sec. 4:
+ * each round multiplies counter words 0 and 2 by two odd constants, keeps the 64-bit high
+ * and low halves, and mixes the high halves with words 1 and 3 and the round key; the key
+ * advances by two Weyl constants between rounds.  Ten rounds. */
+static const uint64_t PHILOX_M0 = 0xD2E7470EE14C6C93ULL;
+static const uint64_t PHILOX_M1 = 0xCA5A826395121157ULL;
+static const uint64_t PHILOX_W0 = 0x9E3779B97F4A7C15ULL; /* golden ratio */
+static const uint64_t PHILOX_W1 = 0xBB67AE8584CAA73BULL; /* sqrt(3) - 1 */
+
+static void mul_hi_lo(uint64_t a, uint64_t b, uint64_t* hi, uint64_t* lo) {
+  unsigned __int128 prod = (unsigned __int128)a * (unsigned __int128)b;
+  *lo = (uint64_t)prod;
+  *hi = (uint64_t)(prod >> 64);
+}
+
+void orc_philox(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4]) {
+  uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint64_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += PHILOX_W0;
+      k1 += PHILOX_W1;
+    }
+    uint64_t hi0, lo0, hi1, lo1;
+    mul_hi_lo(PHILOX_M0, x0, &hi0, &lo0);
+    mul_hi_lo(PHILOX_M1, x2, &hi1, &lo1);
+    uint64_t y0 = hi1 ^ x1 ^ k0;
+    uint64_t y1 = lo1;
+    uint64_t y2 = hi0 ^ x3 ^ k1;
+    uint64_t y3 = lo0;
+    x0 = y0;
+    x1 = y1;
+    x2 = y2;
+    x3 = y3;
+  }
+  out[0] = x0;
+  out[1] = x1;
+  out[2] = x2;
+  out[3] = x3;
+}
+
+double orc_u53(uint64_t w) { return (double)(w >> 11) * 0x1.0p-53; }
+
+static void draw(const orc_params* p, uint64_t c0, uint64_t c1, uint64_t tag, uint64_t w[4]) {
+  uint64_t ctr[4] = {c0, c1, tag, 0};
+  uint64_t key[2] = {p->seed, 0};
+  orc_philox(ctr, key, w);
+}
+
+/* Box-Muller: two uniforms -> two independent standard normals. */
+static void box_muller(uint64_t w0, uint64_t w1, double* g0, double* g1) {
+  double u1 = 1.0 - orc_u53(w0); /* (0, 1] */
+  double u2 = orc_u53(w1);
+  double rad = sqrt(-2.0 * log(u1));
+  double ang = 2.0 * ORC_PI * u2;
+  *g0 = rad * cos(ang);
+  *g1 = rad * sin(ang);
+}
+
+/* ------------------------------------------------------------------- geometry ---- */
+int64_t orc_num_cells(const orc_params* p) {
+  int64_t lz = p->L[2] + (p->walls_z ? 1 : 0);
+  return (int64_t)p->L[0] * p->L[1] * lz;
+}
+
+static double box_len(const orc_params* p, int d) { return (double)p->L[d] * p->a; }
+
+void orc_shift(const orc_params* p, int64_t t, double s[3]) {
+  uint64_t w[4];
+  draw(p, (uint64_t)t, 0, ORC_TAG_SHIFT, w);
+  for (int d = 0; d < 3; ++d) s[d] = (orc_u53(w[d]) - 0.5) * p->a;
+  if (p->walls_z && s[2] < 0.0) s[2] += p->a; /* R4: fold into [0, a) */
+}
+
+int64_t orc_cell_key(const orc_params* p, const double r[3], const double s[3]) {
+  int64_t c[3];
+  for (int d = 0; d < 3; ++d) {
+    double q = (r[d] - s[d]) / p->a;
+    int64_t k = (int64_t)floor(q);
+    if (d == 2 && p->walls_z) {
+      c[d] = k + 1; /* layers 0 .. Lz */
+    } else {
+      int64_t L = p->L[d];
+      c[d] = ((k % L) + L) % L;
+    }
+  }
+  return c[0] + (int64_t)p->L[0] * (c[1] + (int64_t)p->L[1] * c[2]);
+}
+
+void orc_axis(const orc_params* p, int64_t t, int64_t cell, double n[3]) {
+  /* z uniform on [-1, 1) and azimuth uniform on [0, 2 pi): uniform on the sphere
+   * (Archimedes' hat-box theorem). */
+  uint64_t w[4];
+  draw(p, (uint64_t)t, (uint64_t)cell, ORC_TAG_AXIS, w);
+  double z = 2.0 * orc_u53(w[0]) - 1.0;
+  double phi = 2.0 * ORC_PI * orc_u53(w[1]);
+  double rho = sqrt((1.0 - z) * (1.0 + z));
+  n[0] = rho * cos(phi);
+  n[1] = rho * sin(phi);
+  n[2] = z;
+}
+
+void orc_rotate(const double n[3], double alpha, const double u[3], double v[3]) {
+  double d[3], cr[3], out[3];
+  for (int k = 0; k < 3; ++k) d[k] = v[k] - u[k];               /* relative velocity */
+  double par = n[0] * d[0] + n[1] * d[1] + n[2] * d[2];           /* component along n */
+  cr[0] = n[1] * d[2] - n[2] * d[1];                              /* n x d */
+  cr[1] = n[2] * d[0] - n[0] * d[2];
+  cr[2] = n[0] * d[1] - n[1] * d[0];
+  double c = cos(alpha), s = sin(alpha);
+  for (int k = 0; k < 3; ++k) {
+    double perp = d[k] - par * n[k];                              /* perpendicular part */
+    out[k] = par * n[k] + c * perp + s * cr[k];                   /* rotated by alpha */
+  }
+  for (int k = 0; k < 3; ++k) v[k] = u[k] + out[k];
+}
+
+/* -------------------------------------------------------------------- streaming ---- */
+/* Periodic wrap into [0, B) (R3). */
+static double wrap(double x, double B) {
+  if (x >= B)
+    x -= B;
+  else if (x < 0.0)
+    x += B;
+  if (x >= B || x < 0.0) {
+    x = fmod(x, B);
+    if (x < 0.0) x += B;
+    if (x >= B) x = 0.0;
+  }
+  return x;
+}
+
+/* Ballistic move over dt under the constant acceleration g: r += v dt + g dt^2 / 2 and
+ * v += g dt, written as r = fma(v, dt, r + h) and v = fma(g, dt, v) with h = g dt^2 / 2.
+ * With walls (R13), a particle that reaches z = 0 or z = H has its whole velocity reversed
+ * at the crossing time and moves on for the rest of the step. */
+static void stream_one(const orc_params* p, double* r, double* v) {
+  double H = box_len(p, 2);
+  if (!p->walls_z) {
+    for (int d = 0; d < 3; ++d) {
+      double h = 0.5 * p->g[d] * p->dt * p->dt;
+      r[d] = fma(v[d], p->dt, r[d] + h);
+      v[d] = fma(p->g[d], p->dt, v[d]);
+      r[d] = wrap(r[d], box_len(p, d));
+    }
+    return;
+  }
+  double left = p->dt;
+  for (int bounce = 0; bounce < 64 && left > 0.0; ++bounce) {
+    double z1 = r[2] + v[2] * left; /* g has no z component with walls */
+    double tau = left;
+    double wall = -1.0;
+    if (z1 < 0.0) {
+      tau = (0.0 - r[2]) / v[2];
+      wall = 0.0;
+    } else if (z1 >= H) {
+      tau = (H - r[2]) / v[2];
+      wall = H;
+    }
+    if (tau < 0.0) tau = 0.0;
+    if (tau > left) tau = left;
+    for (int d = 0; d < 2; ++d) {
+      double h = 0.5 * p->g[d] * tau * tau;
+      r[d] = fma(v[d], tau, r[d] + h);
+      v[d] = fma(p->g[d], tau, v[d]);
+    }
+    if (wall < 0.0) {
+      r[2] = fma(v[2], tau, r[2]);
+      left = 0.0;
+    } else {
+      r[2] = wall;
+      for (int d = 0; d < 3; ++d) v[d] = -v[d];
+      left -= tau;
+    }
+  }
+  for (int d = 0; d < 2; ++d) r[d] = wrap(r[d], box_len(p, d));
+  if (r[2] >= H) r[2] = nextafter(H, 0.0);
+  if (r[2] < 0.0) r[2] = 0.0;
+}
+
+/* ---------------------------------------------------------------------- init ---- */
+void orc_init(const orc_params* p, int64_t n, double* r, double* v) {
+  double sigma = sqrt(p->kT / p->mass);
+  double mean[3] = {0.0, 0.0, 0.0};
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t w[4];
+    draw(p, (uint64_t)i, 0, ORC_TAG_INIT, w);
+    for (int d = 0; d < 3; ++d) r[3 * i + d] = orc_u53(w[d]) * box_len(p, d);
+    draw(p, (uint64_t)i, 1, ORC_TAG_INIT, w);
+    double g[4];
+    box_muller(w[0], w[1], &g[0], &g[1]);
+    box_muller(w[2], w[3], &g[2], &g[3]);
+    for (int d = 0; d < 3; ++d) {
+      v[3 * i + d] = sigma * g[d];
+      mean[d] += v[3 * i + d];
+    }
+  }
+  if (n > 0)
+    for (int d = 0; d < 3; ++d) mean[d] /= (double)n;
+  for (int64_t i = 0; i < n; ++i)
+    for (int d = 0; d < 3; ++d) v[3 * i + d] -= mean[d];
+}
+
+/* ---------------------------------------------------------------------- step ---- */
+int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, int32_t* id,
+             int32_t* keys_out, int32_t* counts_out, int32_t* offsets_out, int32_t* perm_out,
+             double* moments_out, double* shift_out) {
+  if (!p || n < 0 || t < 1 || p->a <= 0.0 || p->mass <= 0.0) return -1;
+  for (int d = 0; d < 3; ++d)
+    if (p->L[d] < 1) return -1;
+  if (p->walls_z && p->g[2] != 0.0) return -1;
+  int64_t C = orc_num_cells(p);
+  if (C > INT32_MAX || n > INT32_MAX) return -1;
+
+  int32_t* key = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* cnt = (int32_t*)calloc((size_t)C, sizeof(int32_t));
+  int32_t* off = (int32_t*)malloc(sizeof(int32_t) * (size_t)(C + 1));
+  int32_t* cur = (int32_t*)malloc(sizeof(int32_t) * (size_t)C);
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  if (!key || !cnt || !off || !cur || !perm) {
+    free(key); free(cnt); free(off); free(cur); free(perm);
+    return -2;
+  }
+
+  /* 1. streaming (R1) */
+  for (int64_t i = 0; i < n; ++i) stream_one(p, &r[3 * i], &v[3 * i]);
+
+  /* 2. grid shift of this step (R2) */
+  double s[3];
+  orc_shift(p, t, s);
+
+  /* 3. cell of every particle on the shifted grid (Sec. 3.1) */
+  for (int64_t i = 0; i < n; ++i) key[i] = (int32_t)orc_cell_key(p, &r[3 * i], s);
+
+  /* 4. linked-cell list as a stable counting sort (R6) */
+  for (int64_t i = 0; i < n; ++i) cnt[key[i]] += 1;
+  off[0] = 0;
+  for (int64_t c = 0; c < C; ++c) off[c + 1] = off[c] + cnt[c];
+  for (int64_t c = 0; c < C; ++c) cur[c] = off[c];
+  for (int64_t i = 0; i < n; ++i) perm[cur[key[i]]++] = (int32_t)i;
+
+  /* 5.-7. per cell: centre of mass (Listing 4), relative velocity, rotation (Sec. 2) */
+  const double m = p->mass;
+  for (int64_t c = 0; c < C; ++c) {
+    int32_t nc = cnt[c];
+    double M = 0.0, P[3] = {0.0, 0.0, 0.0}, E = 0.0;
+    for (int32_t j = off[c]; j < off[c + 1]; ++j) {
+      const double* vi = &v[3 * (int64_t)perm[j]];
+      for (int d = 0; d < 3; ++d) P[d] += m * vi[d];
+      M += m;
+      E += 0.5 * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
+    }
+    if (moments_out) {
+      moments_out[5 * c + 0] = M;
+      moments_out[5 * c + 1] = P[0];
+      moments_out[5 * c + 2] = P[1];
+      moments_out[5 * c + 3] = P[2];
+      moments_out[5 * c + 4] = E;
+    }
+    if (nc == 0) continue;
+
+    /* R13: a cell cut by a wall is filled up to ppc with virtual particles at rest on
+     * average, whose summed momentum is Gaussian with variance M_virtual kT. */
+    int virt = 0;
+    if (p->walls_z && s[2] > 0.0) {
+      int64_t layer = c / ((int64_t)p->L[0] * p->L[1]);
+      if ((layer == 0 || layer == p->L[2]) && (double)nc < p->ppc) {
+        double Mv = (p->ppc - (double)nc) * m;
+        uint64_t w[4];
+        draw(p, (uint64_t)t, (uint64_t)c, ORC_TAG_WALL, w);
+        double g[4];
+        box_muller(w[0], w[1], &g[0], &g[1]);
+        box_muller(w[2], w[3], &g[2], &g[3]);
+        double sd = sqrt(Mv * p->kT);
+        for (int d = 0; d < 3; ++d) P[d] += sd * g[d];
+        M += Mv;
+        virt = 1;
+      }
+    }
+    if (nc < 2 && !virt) continue; /* R12 */
+
+    double u[3];
+    for (int d = 0; d < 3; ++d) u[d] = P[d] / M; /* R7 */
+    double ax[3];
+    orc_axis(p, t, c, ax);
+    for (int32_t j = off[c]; j < off[c + 1]; ++j) orc_rotate(ax, p->alpha, u, &v[3 * (int64_t)perm[j]]);
+
+    if (p->thermostat && nc >= 2) {
+      /* R14: rescale the relative velocities so the cell's relative kinetic energy is
+       * (3/2)(n_c - 1) kT. */
+      double K = 0.0;
+      for (int32_t j = off[c]; j < off[c + 1]; ++j) {
+        const double* vi = &v[3 * (int64_t)perm[j]];
+        for (int d = 0; d < 3; ++d) K += 0.5 * m * (vi[d] - u[d]) * (vi[d] - u[d]);
+      }
+      if (K > 0.0) {
+        double f = sqrt(1.5 * (double)(nc - 1) * p->kT / K);
+        for (int32_t j = off[c]; j < off[c + 1]; ++j) {
+          double* vi = &v[3 * (int64_t)perm[j]];
+          for (int d = 0; d < 3; ++d) vi[d] = u[d] + f * (vi[d] - u[d]);
+        }
+      }
+    }
+  }
+
+  if (keys_out) memcpy(keys_out, key, sizeof(int32_t) * (size_t)n);
+  if (counts_out) memcpy(counts_out, cnt, sizeof(int32_t) * (size_t)C);
+  if (offsets_out) memcpy(offsets_out, off, sizeof(int32_t) * (size_t)(C + 1));
+  if (perm_out) memcpy(perm_out, perm, sizeof(int32_t) * (size_t)n);
+  if (shift_out)
+    for (int d = 0; d < 3; ++d) shift_out[d] = s[d];
+
+  /* 8. every k steps the storage itself is put into cell order (Listing 1, permute) */
+  if (p->resort_k > 0 && t % p->resort_k == 0 && n > 0) {
+    double* r2 = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    double* v2 = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+    int32_t* id2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    if (!r2 || !v2 || !id2) {
+      free(r2); free(v2); free(id2);
+      free(key); free(cnt); free(off); free(cur); free(perm);
+      return -2;
+    }
+    for (int64_t j = 0; j < n; ++j) {
+      int64_t i = perm[j];
+      for (int d = 0; d < 3; ++d) {
+        r2[3 * j + d] = r[3 * i + d];
+        v2[3 * j + d] = v[3 * i + d];
+      }
+      id2[j] = id ? id[i] : (int32_t)i;
+    }
+    memcpy(r, r2, sizeof(double) * 3 * (size_t)n);
+    memcpy(v, v2, sizeof(double) * 3 * (size_t)n);
+    if (id) memcpy(id, id2, sizeof(int32_t) * (size_t)n);
+    free(r2); free(v2); free(id2);
+  }
+
+  free(key); free(cnt); free(off); free(cur); free(perm);
+  return 0;
+}

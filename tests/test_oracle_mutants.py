@@ -1,0 +1,55 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a copy of the oracle's C source (a dropped term, a wrong
+sign, a swapped index, an unstable sort, ...), builds it on the CPU and runs the pins that
+should catch it against the broken build, expecting at least one failure.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mpcd_oracle.c")
+
+MUTANTS = [
+    ("rotation sense flipped", "out[k] = par * n[k] + c * perp + s * cr[k];",
+     "out[k] = par * n[k] + c * perp - s * cr[k];", "rotation"),
+    ("parallel part dropped", "out[k] = par * n[k] + c * perp + s * cr[k];",
+     "out[k] = c * perp + s * cr[k];", "rotation"),
+    ("rotation about v instead of v - u", "d[k] = v[k] - u[k];", "d[k] = v[k];", "galilean or conserves"),
+    ("mass weight dropped", "P[d] += m * vi[d];", "P[d] += vi[d];", "closed_form or conserves"),
+    ("key index order swapped", "return c[0] + (int64_t)p->L[0] * (c[1] + (int64_t)p->L[1] * c[2]);",
+     "return c[1] + (int64_t)p->L[1] * (c[0] + (int64_t)p->L[0] * c[2]);", "brute_force or face_point"),
+    ("shift sign flipped", "double q = (r[d] - s[d]) / p->a;", "double q = (r[d] + s[d]) / p->a;",
+     "brute_force or face_point"),
+    ("perm not stable", "for (int64_t i = 0; i < n; ++i) perm[cur[key[i]]++] = (int32_t)i;",
+     "for (int64_t i = n - 1; i >= 0; --i) perm[cur[key[i]]++] = (int32_t)i;", "stable_argsort"),
+    ("philox key schedule skipped", "k0 += PHILOX_W0;", "k0 += 0;", "kat or numpy"),
+    ("philox words swapped", "uint64_t y1 = lo1;", "uint64_t y1 = lo0;", "kat or numpy"),
+    ("no streaming", "r[d] = fma(v[d], p->dt, r[d] + h);", "r[d] = r[d] + h;", "streaming"),
+    ("axis not uniform", "double z = 2.0 * orc_u53(w[0]) - 1.0;", "double z = orc_u53(w[0]);", "axis_uniform"),
+    ("wall bounce keeps velocity", "for (int d = 0; d < 3; ++d) v[d] = -v[d];",
+     "for (int d = 2; d < 3; ++d) v[d] = -v[d];", "bounce_back"),
+]
+
+
+@pytest.mark.parametrize("name,old,new,select", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_mutant(tmp_path, name, old, new, select):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not found: " + name
+    mutated = tmp_path / "mpcd_oracle.c"
+    mutated.write_text(src.replace(old, new))
+    (tmp_path / "mpcd_oracle.h").write_text(open(SRC[:-2] + ".h").read())
+    lib = tmp_path / "libmut.so"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(lib),
+                    str(mutated), "-lm"], check=True)
+    env = dict(os.environ, ORACLE_LIB=str(lib))
+    tests = [os.path.join(ROOT, "tests", f) for f in
+             ("test_oracle_philox.py", "test_oracle_geometry.py", "test_oracle_rotation.py",
+              "test_oracle_step.py", "test_oracle_walls.py")]
+    res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                          "-k", select + " and not poiseuille and not relaxes"] + tests,
+                         cwd=ROOT, env=env, capture_output=True, text=True)
+    assert res.returncode == 1, "mutant survived: %s\n%s" % (name, res.stdout[-2000:])
