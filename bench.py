@@ -1,0 +1,287 @@
+#!/usr/bin/env python
+"""Throughput of the SRD (MPCD) time step on GB300: particle updates per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+One step = stream + shift + bin + counting sort + per-cell sums + rotation of every
+particle (the whole hot path) on one box of the named workload (default: FP64, 128^3 cells,
+10 particles per cell, 20,971,520 particles, full re-sort every 10 steps).  The state
+(1 GB) is larger than L2, so no flush is needed between steps.  Prints one JSON line.
+
+With N > 1 (launched by torch.distributed.run) every rank advances its own independent
+replica box (the single-box path has no exchange step); `value` is the sum over ranks of
+updates divided by the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the plain statement the library is checked
+against) on the same workload on the host cores, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle updates/sec/GPU and % of HBM roofline; mixed/batched vs FP64"
+UNIT = "particle updates/s"
+
+# Algorithmic HBM bytes per launch of each kernel, as (bytes per particle, bytes per cell):
+# what the kernel must read and write once (state, keys, ranks, perm, counts, offsets).
+FP64_BYTES = {
+    "zero_counts": (0.0, 4.0),
+    "stream_bin": (48.0 + 24.0 + 8.0, 4.0),
+    "scan": (0.0, 12.0),
+    "scatter": (12.0, 4.0),
+    "collide": (4.0 + 4.0 + 24.0 + 24.0, 8.0),
+    "end_step": (0.0, 0.0),
+}
+FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # collide on re-sort steps also moves r and the ids
+ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fp64_L128")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 10:
+                continue
+            if self.bus_id and self.bus_id[-12:] not in f[1].lower():
+                continue
+            rows.append(f)
+        os.remove(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[6 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        power = [float(r[4]) for r in rows if r[4].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][3]) if rows[0][3].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+def cpu_oracle_run(w, steps, sample_note):
+    """Time the FP64 oracle (as it stands, one thread) on the workload on the host."""
+    from oracle import oracle as orc
+    p = orc.make_params(w.L, a=w.a, dt=w.dt, alpha_deg=w.alpha_deg, kT=w.kT, mass=w.mass, ppc=w.ppc, seed=w.seed,
+                        resort_k=w.resort_k, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat)
+    r, v = orc.init(p, w.n_particles)
+    st = orc.State(r, v)
+    orc.step(p, st)   # untimed first step (page-in)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        orc.step(p, st)
+    dt = time.perf_counter() - t0
+    value = w.n_particles * steps / dt
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%s: %d oracle steps of the full %d-particle box (%.1f s), single thread" % (
+                sample_note, steps, w.n_particles, dt)}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = cpu_oracle_run(w, max(1, args.steps), "reference arm")
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "L": list(w.L), "particles": w.n_particles, "precision": w.precision},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    from paper_2212_11878_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2212_11878_gb300 import abi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    stream = torch.cuda.Stream()
+    p = abi.params_from_workload(w, seed=w.seed + rank)
+    box = abi.Box(p)
+    h = box.h
+    abi.mpcd_set_stream(h, stream.cuda_stream)
+    n = box.n
+
+    box.step(args.warmup)
+    box.sync()
+
+    props = torch.cuda.get_device_properties(local)
+    bus = getattr(props, "pci_bus_id", None)
+    sampler = ClockSampler(bus if isinstance(bus, str) else None)
+
+    abi.mpcd_timing(h, True)
+    l0 = abi.mpcd_launch_count(h)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    box.step(args.steps)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = abi.mpcd_launch_count(h) - l0
+    ktimes = abi.mpcd_timing_read(h)
+    abi.mpcd_timing(h, False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    total_updates = n * args.steps * world
+    value = total_updates / (ms / 1e3)
+
+    # --- end to end through the host-buffer API: upload, one step, download ---
+    r_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    v_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
+    r_np, v_np = r_h.numpy(), v_h.numpy()
+    abi.mpcd_get_state(h, r_np, v_np)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for k in range(args.e2e_steps):
+        abi.mpcd_set_state(h, r_np, v_np, abi.mpcd_steps_done(h))
+        abi.mpcd_step(h, 1)
+        abi.mpcd_get_state(h, r_np, v_np)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = n * args.e2e_steps * world / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_run(w, args.cpu_steps, "cpu_baseline")
+
+    if rank == 0:
+        import json as _json
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+        hbm_peak = peaks.get("hbm_gbs")
+        peak_src = "measured" if hbm_peak else "fallback"
+        hbm_peak = hbm_peak or 6800.0
+        C = box.ncell
+        kernels = {}
+        total_kernel_ms = sum(v[0] for v in ktimes.values())
+        for name, (kms, cnt) in ktimes.items():
+            per_p, per_c = FP64_BYTES.get(name, (0.0, 0.0))
+            # bytes per launch of this slot (a slot may hold several kernel launches)
+            slot_launches = cnt / args.steps
+            bytes_step = per_p * n + per_c * C
+            if name == "collide" and p.resort_k > 0:
+                bytes_step += FP64_RESORT_EXTRA * n / p.resort_k
+            kernels[name] = {"ms_per_step": kms / args.steps, "launches": cnt, "share": kms / total_kernel_ms,
+                             "algo_bytes_per_step": bytes_step,
+                             "gbs": bytes_step / (kms / args.steps / 1e3) / 1e9 if kms > 0 else None,
+                             "launches_per_step": slot_launches}
+        dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+        d = kernels[dom]
+        achieved = d["gbs"]
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                    "algo_bytes_per_launch": d["algo_bytes_per_step"]}
+        ms_step = ms / args.steps
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if p.precision == abi.MPCD_FP64 else "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "L": list(w.L), "particles": n, "cells": C, "ppc": w.ppc,
+                       "precision": w.precision, "resort_k": w.resort_k, "alpha_deg": w.alpha_deg, "dt": w.dt,
+                       "l2": "no flush: state %.2f GB > 129 MB L2" % (n * 104 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "hbm_roofline_frac_step": value / world * ALGO_STEP_BYTES_FP64 / 1e9 / hbm_peak,
+            "roofline": roofline,
+            "kernels": kernels,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 48, "d2h_bytes_per_step": n * 48,
+                    "steps": args.e2e_steps},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    box.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

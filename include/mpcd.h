@@ -1,0 +1,156 @@
+/*
+ * mpcd.h -- C ABI of libmpcd, a GB300 (sm_103a) implementation of the stochastic rotation
+ * dynamics (SRD) time step of multi-particle collision dynamics (MPCD).
+ *
+ * The method (arXiv 2212.11878, Sec. 2): every step the particles stream ballistically, the
+ * collision grid is shifted at random, the particles are sorted into the shifted cells
+ * (Sec. 3.1, Listing 1), each cell's mass and momentum are summed (Sec. 3.3, Listing 4), and
+ * each particle's velocity relative to its cell's centre-of-mass velocity is split along a
+ * random axis and its perpendicular part rotated by a fixed angle alpha (Sec. 2, parts
+ * (i)-(iii)).  A system is a box of L[0] x L[1] x L[2] cubic cells of edge a holding
+ * N = round(ppc * cells) particles of mass m (Sec. 4: N = L^3 <N_c>).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: MPCD_OK (0) or a negative MPCD_ERR_* code.  A failed call leaves a
+ *     message readable with mpcd_last_error().  After a CUDA error the handle is poisoned:
+ *     every later call except mpcd_last_error / mpcd_destroy returns MPCD_ERR_STATE.
+ *   - Ownership: a handle owns all of its device memory; the caller owns every array it
+ *     passes in.  Host arrays are plain (pageable or pinned) host memory; "_device" entry
+ *     points take device pointers on the handle's GPU.
+ *   - Layout: positions and velocities cross the ABI as FP64 arrays of N x 3, row-major
+ *     (x, y, z of particle 0, then particle 1, ...), always in particle-id order.
+ *   - Asynchrony: mpcd_step only enqueues work on the handle's stream; calls that return
+ *     data to the host synchronise that stream first.
+ *   - Threads: a handle is used by one host thread at a time.
+ */
+#ifndef MPCD_H
+#define MPCD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpcd_s mpcd_t; /* opaque, library-owned */
+
+enum {
+  MPCD_OK = 0,
+  MPCD_ERR_ARG = -1,     /* invalid argument; nothing was changed */
+  MPCD_ERR_CUDA = -2,    /* a CUDA call failed; the handle is now poisoned */
+  MPCD_ERR_OOM = -3,     /* device memory ran out while creating */
+  MPCD_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up; the handle is poisoned */
+  MPCD_ERR_STATE = -5    /* the handle was poisoned by an earlier error */
+};
+
+enum { MPCD_FP64 = 0, MPCD_MIXED = 1 };
+
+/* Parameters of one box.  Readings of points the paper leaves open are noted per field. */
+typedef struct {
+  int32_t L[3];       /* cells per side (>= 1); box edge L[d] * a                          */
+  int32_t precision;  /* MPCD_FP64: FP64 positions and velocities (the paper's `double`,   */
+                      /*   Listing 1); MPCD_MIXED: int32 cell + FP32 in-cell offset         */
+                      /*   positions, FP32 velocities, FP64 per-cell sums                   */
+  double a;           /* cell edge length (> 0)                                             */
+  double ppc;         /* mean particles per cell; N = round(ppc * L0 L1 L2)                 */
+  double dt;          /* streaming time step (>= 0)                                         */
+  double alpha;       /* rotation angle in radians, applied with the right-hand rule        */
+  double kT;          /* temperature of the initial Maxwell-Boltzmann velocities (> 0)      */
+  double mass;        /* particle mass m (> 0), the same for all particles                  */
+  double g[3];        /* constant body-force acceleration (g[2] must be 0 with walls)       */
+  uint64_t seed;      /* Philox4x64-10 key word 0 for every random draw of this box         */
+  int32_t walls_z;    /* 0: periodic in z; 1: bounce-back walls at z = 0 and z = L[2] a,    */
+                      /*   virtual particles in cut cells (Lz + 1 cell layers)               */
+  int32_t thermostat; /* 1: rescale each cell's relative kinetic energy to 3/2 (n-1) kT     */
+  int32_t resort_k;   /* physically re-order storage by cell every k steps (0: never)       */
+  int32_t reserved;   /* must be 0                                                          */
+} mpcd_params;
+
+/* Create a box and initialise it on the current CUDA device (Sec. 4 workload): positions
+ * uniform in the box, velocities N(0, kT/m) per component with the net momentum removed,
+ * drawn from Philox counters (i, 0, 0, 0) and (i, 1, 0, 0).  *out receives the handle, or
+ * NULL on failure.  Errors: MPCD_ERR_ARG for invalid params, MPCD_ERR_OOM, MPCD_ERR_CUDA. */
+int mpcd_create(const mpcd_params* p, mpcd_t** out);
+
+/* Create an ensemble of nbox independent periodic boxes (each with its own L, ppc, dt,
+ * alpha, seed) advanced together: one sort over the concatenated cell keys and one launch
+ * sequence per step.  All boxes must share precision, walls_z = 0, thermostat and resort_k.
+ * Particle and cell data of box b follow those of boxes 0..b-1. */
+int mpcd_batch_create(int32_t nbox, const mpcd_params* p, mpcd_t** out);
+
+/* Free every device buffer of the handle.  NULL is accepted. */
+int mpcd_destroy(mpcd_t* h);
+
+/* Run all later work on `stream` (a cudaStream_t of the handle's device, e.g. a PyTorch
+ * stream); NULL selects the handle's own stream.  Synchronises the previous stream. */
+int mpcd_set_stream(mpcd_t* h, void* stream);
+
+/* Enqueue nsteps full SRD steps (Sec. 2): stream, shift, bin, per-cell sums, rotate.
+ * Steps are numbered from 1 since creation or the last mpcd_set_state.  Asynchronous. */
+int mpcd_step(mpcd_t* h, int64_t nsteps);
+
+/* Wait for all enqueued work; reports a device-side timeout as MPCD_ERR_TIMEOUT. */
+int mpcd_sync(mpcd_t* h);
+
+int64_t mpcd_num_particles(const mpcd_t* h); /* N, or -1 for NULL */
+int64_t mpcd_num_cells(const mpcd_t* h);     /* collision cells (with walls Lx Ly (Lz+1)) */
+int64_t mpcd_steps_done(const mpcd_t* h);    /* steps enqueued since the state was set    */
+int32_t mpcd_num_boxes(const mpcd_t* h);     /* 1 for mpcd_create                          */
+
+/* Copy the state to host arrays r[N*3], v[N*3] (FP64, particle-id order).  Mixed-precision
+ * positions are returned as (cell index + offset) * a.  Synchronises. */
+int mpcd_get_state(mpcd_t* h, double* r, double* v);
+
+/* Replace the state from host arrays r[n*3], v[n*3] (particle-id order) and set the step
+ * counter to t (the next step is t + 1).  n must equal mpcd_num_particles.  Positions must
+ * lie in the box ([0, L a) per axis); MPCD_ERR_ARG otherwise.  Synchronises. */
+int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64_t t);
+
+/* Same as mpcd_get_state / mpcd_set_state with device arrays; enqueued on the handle's
+ * stream without a host synchronisation.  The device variant of set_state does not check
+ * that positions lie in the box. */
+int mpcd_get_state_device(mpcd_t* h, double* r_dev, double* v_dev);
+int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const double* v_dev, int64_t t);
+
+/* Record per-cell moments during later steps (enable = 1) or stop (0).  Recording costs an
+ * extra 40 bytes of HBM traffic per cell per step. */
+int mpcd_record_moments(mpcd_t* h, int32_t enable);
+
+/* Per-cell moments of the last recorded step (Listing 4's vcm plus the kinetic energy):
+ * out[5*c + 0..4] = M, Px, Py, Pz, E = sum m v^2 / 2 over the real particles of cell c,
+ * before the rotation; shift_out[3] = that step's grid shift (may be NULL).
+ * MPCD_ERR_STATE if no step was recorded since recording was enabled.  Synchronises. */
+int mpcd_cell_moments(mpcd_t* h, double* out, double* shift_out);
+
+/* The sort of the most recent step (Sec. 3.1 linked-cell list as a stable counting sort):
+ * keys[N] = cell key of each storage slot at the start of that step, counts[C],
+ * offsets[C+1] (exclusive prefix sum), perm[N] = storage slot of the j-th particle in cell
+ * order (stable by storage slot), ids[N] = particle id held by each storage slot at the
+ * start of that step.  Any pointer may be NULL.  Key of cell (cx, cy, cz) is
+ * cx + Lx (cy + Ly cz).  MPCD_ERR_STATE if no step has run.  Synchronises. */
+int mpcd_debug_sort(mpcd_t* h, int32_t* keys, int32_t* counts, int32_t* offsets, int32_t* perm,
+                    int32_t* ids);
+
+/* Per-kernel timing with CUDA events on the launching stream.  While enabled, mpcd_step
+ * launches kernels one by one (no CUDA graph) and brackets each with events.
+ * mpcd_timing_read synchronises and returns, for up to nmax kernels, the summed device
+ * milliseconds and launch counts since timing was enabled, plus their names
+ * (names[k] points into library-owned storage valid until mpcd_destroy).
+ * Returns the number of kernels with data (>= 0) or an error. */
+int mpcd_timing(mpcd_t* h, int32_t enable);
+int mpcd_timing_read(mpcd_t* h, int32_t nmax, const char** names, double* ms, int64_t* launches);
+
+/* Number of kernels this handle has launched (graph replays count each kernel node). */
+int64_t mpcd_launch_count(const mpcd_t* h);
+
+/* Message of the last failure on this handle (or of the last failed create when h is NULL).
+ * The string is owned by the library. */
+const char* mpcd_last_error(const mpcd_t* h);
+
+/* Library build description, e.g. "libmpcd sm_103a". */
+const char* mpcd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

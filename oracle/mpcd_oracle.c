@@ -101,7 +101,11 @@ int64_t orc_cell_key(const orc_params* p, const double r[3], const double s[3]) 
     double q = (r[d] - s[d]) / p->a;
     int64_t k = (int64_t)floor(q);
     if (d == 2 && p->walls_z) {
-      c[d] = k + 1; /* layers 0 .. Lz */
+      /* layers 0 .. Lz; for z just below H, (z - s)/a can round up to Lz when a is not a
+       * power of two, so the layer is clamped into range */
+      c[d] = k + 1;
+      if (c[d] < 0) c[d] = 0;
+      if (c[d] > p->L[2]) c[d] = p->L[2];
     } else {
       int64_t L = p->L[d];
       c[d] = ((k % L) + L) % L;

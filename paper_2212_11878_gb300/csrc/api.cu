@@ -1,0 +1,550 @@
+// api.cu -- host runtime behind include/mpcd.h: handle lifetime, parameter checks, device
+// buffers, the per-step launch sequence (replayed from a captured CUDA graph), per-kernel
+// event timing and error reporting.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/mpcd.h"
+#include "device_common.cuh"
+#include "mpcd_internal.h"
+
+using namespace mpcd;
+
+namespace {
+
+enum KernelSlot { kSlotZero = 0, kSlotStreamBin, kSlotScan, kSlotScatter, kSlotCollide, kSlotEndStep, kNumSlots };
+const char* kSlotNames[kNumSlots] = {"zero_counts", "stream_bin", "scan", "scatter", "collide", "end_step"};
+// kernels launched per slot per step
+const int kSlotLaunches[kNumSlots] = {1, 1, 3, 1, 1, 1};
+
+std::mutex g_err_mu;
+std::string g_create_err;
+
+struct PendingTiming {
+  int slot;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct mpcd_s {
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  int precision = MPCD_FP64;
+  int nbox = 1;
+  Geom geom{};
+  int64_t n = 0, ncell = 0;
+  Fp64Bufs f64{};
+  Scratch scr{};
+  Ctl* ctl = nullptr;
+  int red_blocks = 0;
+  std::vector<void*> allocations;
+
+  // host mirror of the device step control
+  int64_t t = 0;
+  int cur = 0;
+  bool last_resorted = false;
+  bool any_step = false;
+
+  bool record_moments = false;
+  bool moments_valid = false;
+
+  cudaGraphExec_t graph = nullptr;
+  bool graph_moments = false;
+
+  bool timing = false;
+  std::vector<PendingTiming> pending;
+  std::vector<cudaEvent_t> free_events;
+  double slot_ms[kNumSlots] = {};
+  int64_t slot_launches[kNumSlots] = {};
+
+  int64_t launches = 0;
+  std::string err;
+  bool poisoned = false;
+};
+
+namespace {
+
+int fail(mpcd_t* h, int code, const std::string& msg) {
+  if (h) {
+    h->err = msg;
+    if (code == MPCD_ERR_CUDA || code == MPCD_ERR_TIMEOUT) h->poisoned = true;
+  } else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    g_create_err = msg;
+  }
+  return code;
+}
+
+int cuda_fail(mpcd_t* h, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(h, e == cudaErrorMemoryAllocation ? MPCD_ERR_OOM : MPCD_ERR_CUDA, msg);
+}
+
+#define MPCD_TRY(h, call)                                    \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call); \
+  } while (0)
+
+bool is_pow2(double a) {
+  int e;
+  const double m = std::frexp(a, &e);
+  return m == 0.5;
+}
+
+int check_params(const mpcd_params* p, std::string* why) {
+  if (!p) return *why = "params is NULL", MPCD_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (p->L[d] < 1) return *why = "L must be >= 1 in every direction", MPCD_ERR_ARG;
+  if (p->precision != MPCD_FP64 && p->precision != MPCD_MIXED) return *why = "unknown precision", MPCD_ERR_ARG;
+  if (!(p->a > 0.0) || !std::isfinite(p->a)) return *why = "a must be > 0", MPCD_ERR_ARG;
+  if (!(p->ppc >= 0.0) || !std::isfinite(p->ppc)) return *why = "ppc must be >= 0", MPCD_ERR_ARG;
+  if (!(p->dt >= 0.0) || !std::isfinite(p->dt)) return *why = "dt must be >= 0", MPCD_ERR_ARG;
+  if (!std::isfinite(p->alpha)) return *why = "alpha must be finite", MPCD_ERR_ARG;
+  if (!(p->kT > 0.0) || !std::isfinite(p->kT)) return *why = "kT must be > 0", MPCD_ERR_ARG;
+  if (!(p->mass > 0.0) || !std::isfinite(p->mass)) return *why = "mass must be > 0", MPCD_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!std::isfinite(p->g[d])) return *why = "g must be finite", MPCD_ERR_ARG;
+  if (p->walls_z != 0 && p->walls_z != 1) return *why = "walls_z must be 0 or 1", MPCD_ERR_ARG;
+  if (p->walls_z && p->g[2] != 0.0) return *why = "g[2] must be 0 with walls in z", MPCD_ERR_ARG;
+  if (p->thermostat != 0 && p->thermostat != 1) return *why = "thermostat must be 0 or 1", MPCD_ERR_ARG;
+  if (p->resort_k < 0) return *why = "resort_k must be >= 0", MPCD_ERR_ARG;
+  if (p->reserved != 0) return *why = "reserved must be 0", MPCD_ERR_ARG;
+  const double cells = (double)p->L[0] * p->L[1] * ((double)p->L[2] + (p->walls_z ? 1 : 0));
+  if (cells > 2.0e9) return *why = "too many cells (limit 2e9)", MPCD_ERR_ARG;
+  const double n = std::round(p->ppc * (double)p->L[0] * p->L[1] * p->L[2]);
+  if (n > 2.0e9) return *why = "too many particles (limit 2e9)", MPCD_ERR_ARG;
+  return MPCD_OK;
+}
+
+Geom make_geom(const mpcd_params* p) {
+  Geom g{};
+  for (int d = 0; d < 3; ++d) g.L[d] = p->L[d];
+  g.walls = p->walls_z;
+  g.thermostat = p->thermostat;
+  g.resort_k = p->resort_k;
+  g.a = p->a;
+  g.inv_a = 1.0 / p->a;
+  g.pow2a = is_pow2(p->a) ? 1 : 0;
+  for (int d = 0; d < 3; ++d) g.B[d] = (double)p->L[d] * p->a;
+  g.dt = p->dt;
+  g.force = 0;
+  for (int d = 0; d < 3; ++d) {
+    g.g[d] = p->g[d];
+    g.h[d] = ((0.5 * p->g[d]) * p->dt) * p->dt;
+    if (p->g[d] != 0.0) g.force = 1;
+  }
+  g.cos_a = std::cos(p->alpha);
+  g.sin_a = std::sin(p->alpha);
+  g.mass = p->mass;
+  g.kT = p->kT;
+  g.ppc = p->ppc;
+  g.seed = p->seed;
+  g.n = (int64_t)std::llround(p->ppc * (double)p->L[0] * p->L[1] * p->L[2]);
+  g.ncell = (int64_t)p->L[0] * p->L[1] * ((int64_t)p->L[2] + (p->walls_z ? 1 : 0));
+  return g;
+}
+
+template <typename T>
+int dalloc(mpcd_t* h, T** out, int64_t count) {
+  void* p = nullptr;
+  const size_t bytes = sizeof(T) * (size_t)(count > 0 ? count : 1);
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(h, e, "cudaMalloc");
+  }
+  h->allocations.push_back(p);
+  *out = static_cast<T*>(p);
+  return MPCD_OK;
+}
+
+bool resort_at(const mpcd_t* h, int64_t t1) { return h->geom.resort_k > 0 && (t1 % h->geom.resort_k) == 0; }
+
+cudaEvent_t get_event(mpcd_t* h) {
+  if (!h->free_events.empty()) {
+    cudaEvent_t e = h->free_events.back();
+    h->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch one slot's kernels, bracketed by events when timing.
+template <typename F>
+int run_slot(mpcd_t* h, int slot, F&& launch) {
+  PendingTiming pt{slot, nullptr, nullptr};
+  if (h->timing) {
+    pt.a = get_event(h);
+    pt.b = get_event(h);
+    MPCD_TRY(h, cudaEventRecord(pt.a, h->stream));
+  }
+  launch();
+  MPCD_TRY(h, cudaGetLastError());
+  if (h->timing) {
+    MPCD_TRY(h, cudaEventRecord(pt.b, h->stream));
+    h->pending.push_back(pt);
+  }
+  return MPCD_OK;
+}
+
+// Enqueue one full step on h->stream.
+int enqueue_step(mpcd_t* h, bool moments) {
+  const Geom& g = h->geom;
+  Scratch s = h->scr;
+  int rc;
+  if ((rc = run_slot(h, kSlotZero, [&] { launch_zero_i32(s.count, g.ncell, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotStreamBin, [&] { launch_stream_bin_fp64(g, h->f64, s, h->ctl, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(s.count, s.offset, s.partial, g.ncell, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotScatter, [&] { launch_scatter(g, s, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotCollide, [&] { launch_collide_fp64(g, h->f64, s, h->ctl, moments, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step(g, h->ctl, h->stream); }))) return rc;
+  return MPCD_OK;
+}
+
+int launches_per_step() {
+  int k = 0;
+  for (int s = 0; s < kNumSlots; ++s) k += kSlotLaunches[s];
+  return k;
+}
+
+void drop_graph(mpcd_t* h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+}
+
+int build_graph(mpcd_t* h) {
+  drop_graph(h);
+  cudaGraph_t graph = nullptr;
+  MPCD_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  const bool saved = h->timing;
+  h->timing = false;
+  int rc = enqueue_step(h, h->record_moments);
+  h->timing = saved;
+  cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  h->graph_moments = h->record_moments;
+  return MPCD_OK;
+}
+
+int guard(mpcd_t* h) {
+  if (!h) return MPCD_ERR_ARG;
+  if (h->poisoned) return MPCD_ERR_STATE;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+  return MPCD_OK;
+}
+
+int create_common(const mpcd_params* p, mpcd_t** out) {
+  std::string why;
+  int rc = check_params(p, &why);
+  if (rc) return fail(nullptr, rc, why);
+  if (p->precision != MPCD_FP64) return fail(nullptr, MPCD_ERR_ARG, "mixed precision is not built into this library yet");
+  mpcd_t* h = new mpcd_t();
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(nullptr, MPCD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  h->geom = make_geom(p);
+  h->precision = p->precision;
+  h->n = h->geom.n;
+  h->ncell = h->geom.ncell;
+  auto bail = [&](int code) {
+    std::string msg = h->err;
+    mpcd_destroy(h);
+    *out = nullptr;
+    return fail(nullptr, code, msg);
+  };
+  if ((e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail(h, e, "cudaStreamCreate"));
+  h->stream = h->own_stream;
+  const int64_t n = h->n, C = h->ncell;
+  for (int k = 0; k < 2; ++k) {
+    for (int d = 0; d < 3; ++d) {
+      if ((rc = dalloc(h, &h->f64.r[k][d], n))) return bail(rc);
+      if ((rc = dalloc(h, &h->f64.v[k][d], n))) return bail(rc);
+    }
+    if ((rc = dalloc(h, &h->f64.id[k], n))) return bail(rc);
+  }
+  if ((rc = dalloc(h, &h->scr.key, n))) return bail(rc);
+  if ((rc = dalloc(h, &h->scr.rank, n))) return bail(rc);
+  if ((rc = dalloc(h, &h->scr.perm, n))) return bail(rc);
+  if ((rc = dalloc(h, &h->scr.count, C))) return bail(rc);
+  if ((rc = dalloc(h, &h->scr.offset, C + 1))) return bail(rc);
+  if ((rc = dalloc(h, &h->scr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
+  if ((rc = dalloc(h, &h->ctl, 1))) return bail(rc);
+  h->red_blocks = 152 * 4;
+  if ((rc = dalloc(h, &h->scr.red, 3 * (int64_t)h->red_blocks))) return bail(rc);
+  Ctl c0{};
+  if ((e = cudaMemcpyAsync(h->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+    return bail(cuda_fail(h, e, "cudaMemcpyAsync"));
+  launch_init_fp64(h->geom, h->f64, h->scr.red, h->red_blocks, h->ctl, h->stream);
+  if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(h, e, "init kernels"));
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "init sync"));
+  *out = h;
+  return MPCD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpcd_create(const mpcd_params* p, mpcd_t** out) {
+  if (!out) return fail(nullptr, MPCD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  return create_common(p, out);
+}
+
+int mpcd_batch_create(int32_t nbox, const mpcd_params* p, mpcd_t** out) {
+  if (!out) return fail(nullptr, MPCD_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (nbox < 1 || !p) return fail(nullptr, MPCD_ERR_ARG, "nbox must be >= 1 and params non-NULL");
+  return fail(nullptr, MPCD_ERR_ARG, "batched boxes are not built into this library yet");
+}
+
+int mpcd_destroy(mpcd_t* h) {
+  if (!h) return MPCD_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  for (auto& pt : h->pending) {
+    cudaEventDestroy(pt.a);
+    cudaEventDestroy(pt.b);
+  }
+  for (auto e : h->free_events) cudaEventDestroy(e);
+  for (void* p : h->allocations) cudaFree(p);
+  if (h->own_stream) cudaStreamDestroy(h->own_stream);
+  delete h;
+  return MPCD_OK;
+}
+
+int mpcd_set_stream(mpcd_t* h, void* stream) {
+  int rc = guard(h);
+  if (rc) return rc;
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  h->stream = stream ? static_cast<cudaStream_t>(stream) : h->own_stream;
+  return MPCD_OK;
+}
+
+int mpcd_step(mpcd_t* h, int64_t nsteps) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (nsteps < 0) return fail(h, MPCD_ERR_ARG, "nsteps must be >= 0");
+  for (int64_t k = 0; k < nsteps; ++k) {
+    if (h->timing) {
+      if ((rc = enqueue_step(h, h->record_moments))) return rc;
+    } else {
+      if (!h->graph || h->graph_moments != h->record_moments)
+        if ((rc = build_graph(h))) return rc;
+      MPCD_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+    }
+    h->launches += launches_per_step();
+    h->t += 1;
+    h->last_resorted = resort_at(h, h->t);
+    if (h->last_resorted) h->cur ^= 1;
+    h->any_step = true;
+    h->moments_valid = h->record_moments;
+  }
+  return MPCD_OK;
+}
+
+int mpcd_sync(mpcd_t* h) {
+  int rc = guard(h);
+  if (rc) return rc;
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPCD_OK;
+}
+
+int64_t mpcd_num_particles(const mpcd_t* h) { return h ? h->n : -1; }
+int64_t mpcd_num_cells(const mpcd_t* h) { return h ? h->ncell : -1; }
+int64_t mpcd_steps_done(const mpcd_t* h) { return h ? h->t : -1; }
+int32_t mpcd_num_boxes(const mpcd_t* h) { return h ? h->nbox : -1; }
+
+int mpcd_get_state_device(mpcd_t* h, double* r_dev, double* v_dev) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (!r_dev || !v_dev) return fail(h, MPCD_ERR_ARG, "NULL output");
+  launch_get_state_fp64(h->geom, h->f64, h->cur, r_dev, v_dev, h->stream);
+  MPCD_TRY(h, cudaGetLastError());
+  h->launches += 1;
+  return MPCD_OK;
+}
+
+int mpcd_get_state(mpcd_t* h, double* r, double* v) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (!r || !v) return fail(h, MPCD_ERR_ARG, "NULL output");
+  // gather into a stream-ordered scratch of 6 N doubles, then copy to the host
+  double* scratch = nullptr;
+  MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 6 * (size_t)(h->n > 0 ? h->n : 1),
+                              h->stream));
+  launch_get_state_fp64(h->geom, h->f64, h->cur, scratch, scratch + 3 * h->n, h->stream);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r, scratch, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(v, scratch + 3 * h->n, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
+  cudaFreeAsync(scratch, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+  h->launches += 1;
+  return MPCD_OK;
+}
+
+int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const double* v_dev, int64_t t) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
+  if (!r_dev || !v_dev || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
+  launch_set_state_fp64(h->geom, h->f64, r_dev, v_dev, h->stream);
+  MPCD_TRY(h, cudaGetLastError());
+  Ctl c0{};
+  c0.t = t;
+  c0.cur = 0;
+  MPCD_TRY(h, cudaMemcpyAsync(h->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+  h->launches += 1;
+  h->t = t;
+  h->cur = 0;
+  h->any_step = false;
+  h->last_resorted = false;
+  h->moments_valid = false;
+  return MPCD_OK;
+}
+
+int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64_t t) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
+  if (!r || !v || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
+  for (int64_t i = 0; i < n; ++i)
+    for (int d = 0; d < 3; ++d) {
+      const double x = r[3 * i + d];
+      if (!(x >= 0.0 && x < h->geom.B[d]))
+        return fail(h, MPCD_ERR_ARG, "position outside the box at particle " + std::to_string(i));
+      if (!std::isfinite(v[3 * i + d])) return fail(h, MPCD_ERR_ARG, "non-finite velocity at particle " + std::to_string(i));
+    }
+  double* scratch = nullptr;
+  MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 6 * (size_t)(n > 0 ? n : 1), h->stream));
+  cudaError_t e = cudaMemcpyAsync(scratch, r, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + 3 * n, v, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(scratch, h->stream);
+    return cuda_fail(h, e, "set_state copy");
+  }
+  rc = mpcd_set_state_device(h, n, scratch, scratch + 3 * n, t);
+  cudaFreeAsync(scratch, h->stream);
+  if (rc) return rc;
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPCD_OK;
+}
+
+int mpcd_record_moments(mpcd_t* h, int32_t enable) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (enable && !h->scr.moments)
+    if ((rc = dalloc(h, &h->scr.moments, 5 * h->ncell))) return rc;
+  h->record_moments = enable != 0;
+  h->moments_valid = false;
+  return MPCD_OK;
+}
+
+int mpcd_cell_moments(mpcd_t* h, double* out, double* shift_out) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (!out) return fail(h, MPCD_ERR_ARG, "NULL output");
+  if (!h->moments_valid) return fail(h, MPCD_ERR_STATE, "no step has recorded moments (call mpcd_record_moments first)");
+  MPCD_TRY(h, cudaMemcpyAsync(out, h->scr.moments, sizeof(double) * 5 * (size_t)h->ncell, cudaMemcpyDeviceToHost, h->stream));
+  Ctl c{};
+  MPCD_TRY(h, cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  if (shift_out)
+    for (int d = 0; d < 3; ++d) shift_out[d] = c.shift[d];
+  return MPCD_OK;
+}
+
+int mpcd_debug_sort(mpcd_t* h, int32_t* keys, int32_t* counts, int32_t* offsets, int32_t* perm, int32_t* ids) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (!h->any_step) return fail(h, MPCD_ERR_STATE, "no step has run since the state was set");
+  const size_t nb = sizeof(int32_t) * (size_t)h->n, cb = sizeof(int32_t) * (size_t)h->ncell;
+  if (keys) MPCD_TRY(h, cudaMemcpyAsync(keys, h->scr.key, nb, cudaMemcpyDeviceToHost, h->stream));
+  if (counts) MPCD_TRY(h, cudaMemcpyAsync(counts, h->scr.count, cb, cudaMemcpyDeviceToHost, h->stream));
+  if (offsets) MPCD_TRY(h, cudaMemcpyAsync(offsets, h->scr.offset, cb + sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (perm) MPCD_TRY(h, cudaMemcpyAsync(perm, h->scr.perm, nb, cudaMemcpyDeviceToHost, h->stream));
+  if (ids) {
+    const int before = h->last_resorted ? (h->cur ^ 1) : h->cur;
+    MPCD_TRY(h, cudaMemcpyAsync(ids, h->f64.id[before], nb, cudaMemcpyDeviceToHost, h->stream));
+  }
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPCD_OK;
+}
+
+int mpcd_timing(mpcd_t* h, int32_t enable) {
+  int rc = guard(h);
+  if (rc) return rc;
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  for (auto& pt : h->pending) {
+    h->free_events.push_back(pt.a);
+    h->free_events.push_back(pt.b);
+  }
+  h->pending.clear();
+  for (int s = 0; s < kNumSlots; ++s) {
+    h->slot_ms[s] = 0.0;
+    h->slot_launches[s] = 0;
+  }
+  h->timing = enable != 0;
+  return MPCD_OK;
+}
+
+int mpcd_timing_read(mpcd_t* h, int32_t nmax, const char** names, double* ms, int64_t* launches) {
+  int rc = guard(h);
+  if (rc) return rc;
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  for (auto& pt : h->pending) {
+    float el = 0.f;
+    MPCD_TRY(h, cudaEventElapsedTime(&el, pt.a, pt.b));
+    h->slot_ms[pt.slot] += el;
+    h->slot_launches[pt.slot] += kSlotLaunches[pt.slot];
+    h->free_events.push_back(pt.a);
+    h->free_events.push_back(pt.b);
+  }
+  h->pending.clear();
+  int k = 0;
+  for (int s = 0; s < kNumSlots && k < nmax; ++s) {
+    if (h->slot_launches[s] == 0) continue;
+    if (names) names[k] = kSlotNames[s];
+    if (ms) ms[k] = h->slot_ms[s];
+    if (launches) launches[k] = h->slot_launches[s];
+    ++k;
+  }
+  return k;
+}
+
+int64_t mpcd_launch_count(const mpcd_t* h) { return h ? h->launches : -1; }
+
+const char* mpcd_last_error(const mpcd_t* h) {
+  if (h) return h->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  return g_create_err.c_str();
+}
+
+const char* mpcd_version(void) { return "libmpcd sm_103a"; }
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// mpcd_internal.h -- data structures shared by the libmpcd host runtime (api.cu) and the
+// kernel translation units.  Not part of the public ABI (include/mpcd.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace mpcd {
+
+// One box as the kernels see it.  All values derived on the host from mpcd_params.
+struct Geom {
+  int32_t L[3];
+  int32_t walls;       // bounce-back walls in z
+  int32_t thermostat;  // cell-level rescale of the relative kinetic energy
+  int32_t resort_k;    // physical re-sort period (0: never)
+  int32_t pow2a;       // a is a power of two: (r - s) * (1/a) == (r - s) / a exactly
+  int32_t force;       // any g component non-zero
+  double a, inv_a;
+  double B[3];         // box edge lengths L[d] * a
+  double dt;
+  double g[3];         // body-force acceleration
+  double h[3];         // g dt^2 / 2, evaluated as ((0.5 * g) * dt) * dt
+  double cos_a, sin_a; // rotation by alpha
+  double mass, kT, ppc;
+  uint64_t seed;
+  int64_t n;           // particles
+  int64_t ncell;       // collision cells (walls: Lx Ly (Lz + 1))
+  int64_t pbase;       // first particle of the box in the concatenated arrays (batched)
+  int64_t cbase;       // first cell key of the box (batched)
+};
+
+// Device-resident step control, read by every kernel of a step so that one captured CUDA
+// graph can replay any step.
+struct Ctl {
+  int64_t t;          // completed steps; the step in flight is t + 1
+  int32_t cur;        // particle buffer set holding the state (0 or 1)
+  int32_t err;        // error bits raised by kernels
+  double shift[3];    // grid shift of the step in flight / the last step
+  double mean[3];     // scratch for the initial-momentum removal
+};
+
+// FP64 particle state, structure of arrays, two buffer sets for out-of-place re-sorting.
+struct Fp64Bufs {
+  double* r[2][3];
+  double* v[2][3];
+  int32_t* id[2];
+};
+
+// Mixed-precision particle state: pos = {ox, oy, oz, cell index as int bits},
+// vel = {vx, vy, vz, particle id as int bits}; 32 bytes per particle.
+struct MixBufs {
+  float4* pos[2];
+  float4* vel[2];
+};
+
+// Per-step scratch of the counting sort and the cell reduction.
+struct Scratch {
+  int32_t* key;      // [N] cell key per storage slot
+  int32_t* rank;     // [N] arrival rank inside the cell (from the counting atomics)
+  int32_t* perm;     // [N] storage slot of the j-th particle in cell order
+  int32_t* count;    // [C] particles per cell
+  int32_t* offset;   // [C + 1] exclusive prefix sum of count
+  int32_t* partial;  // scan partial sums
+  double* moments;   // [5 C] per-cell M, Px, Py, Pz, E (only when recording)
+  double* red;       // [3 * reduce blocks] partial sums for the initial mean removal
+};
+
+// ---- kernel launchers (kernels_*.cu).  All are asynchronous on `st`. ----
+int scan_tiles(int64_t count);
+void launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
+void launch_scan(const int32_t* count, int32_t* offset, int32_t* partial, int64_t n, cudaStream_t st);
+
+void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
+void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
+void launch_scatter(const Geom& g, Scratch s, cudaStream_t st);
+void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st);
+void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st);
+void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
+void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st);
+
+}  // namespace mpcd

@@ -1,0 +1,189 @@
+"""GPU parity of the FP64 SRD step (libmpcd through the C ABI) against the FP64 CPU oracle,
+from identical states: keys, counts, offsets, perm bit-exact; positions and velocities
+within 1e-12 relative (tests/parity.py states the bound)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2212_11878_gb300 import abi, inputs
+from parity import assert_sort_equal, assert_state_close, oracle_params
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True):
+    """Advance the library and the oracle from the same state; compare after every step."""
+    box = abi.Box(p)
+    try:
+        box.set_state(r, v, t0)
+        op = oracle_params(orc, p)
+        st = orc.State(r, v, t=t0)
+        for k in range(steps):
+            box.step(1)
+            ref = orc.step(op, st, debug=check_sort_every)
+            if check_sort_every:
+                assert_sort_equal(box.debug_sort(), ref)
+            rg, vg = box.state()
+            rr, vr = st.by_id()
+            assert_state_close(rg, vg, rr, vr, p, what="step %d" % (t0 + k + 1))
+        return box.state(), st
+    finally:
+        box.close()
+
+
+CASES = {
+    "cubic_L16": dict(L=(16, 16, 16)),
+    "ragged_5x7x3": dict(L=(5, 7, 3)),
+    "single_cell": dict(L=(1, 1, 1), ppc=12),
+    "sparse": dict(L=(9, 8, 7), ppc=0.7),
+    "dense": dict(L=(4, 4, 4), ppc=40),
+    "a_half": dict(L=(6, 6, 6), a=0.5),
+    "a_non_pow2": dict(L=(6, 5, 4), a=0.7),
+    "mass_dt": dict(L=(6, 6, 6), mass=1.7, dt=0.37, kT=2.5, alpha_deg=77.0),
+    "no_resort": dict(L=(8, 8, 8), resort_k=0),
+    "resort_3": dict(L=(8, 8, 8), resort_k=3),
+    "force": dict(L=(6, 6, 6), g=(0.01, -0.02, 0.005)),
+    "walls": dict(L=(6, 5, 8), walls_z=1, g=(0.01, 0.0, 0.0)),
+    "walls_thermo": dict(L=(6, 5, 8), walls_z=1, g=(0.02, 0.0, 0.0), thermostat=1, ppc=15),
+    "thermo_periodic": dict(L=(6, 6, 6), thermostat=1, kT=0.8),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_steps_match_oracle(orc, name):
+    kw = dict(CASES[name])
+    p = abi.make_params(seed=1000 + len(name), **kw)
+    n = int(round(p.ppc * p.L[0] * p.L[1] * p.L[2]))
+    r, v = inputs.uniform_gaussian_state(tuple(p.L), n, 31 + len(name), a=p.a, kT=p.kT, mass=p.mass)
+    run_pair(orc, p, r, v, steps=6, t0=3)
+
+
+def test_face_positions_bit_exact_keys(orc):
+    p = abi.make_params((6, 6, 6), dt=0.0)
+    r, v = inputs.face_state((6, 6, 6), 2000, 5)
+    run_pair(orc, p, r, v, steps=3)
+
+
+def test_empty_box(orc):
+    p = abi.make_params((4, 4, 4), ppc=0.0)
+    with abi.Box(p) as box:
+        assert box.n == 0
+        box.step(3)
+        dbg = box.debug_sort()
+        assert np.all(dbg["counts"] == 0) and np.all(dbg["offsets"] == 0)
+
+
+def test_init_matches_oracle(orc):
+    w = inputs.WORKLOADS["fp64_L16"]
+    p = abi.params_from_workload(w)
+    with abi.Box(p) as box:
+        rg, vg = box.state()
+    rr, vr = orc.init(oracle_params(orc, p), box_n := rg.shape[0])
+    assert box_n == w.n_particles
+    assert np.array_equal(rg, rr)                 # U53 * L: exact on both sides
+    assert_state_close(rg, vg, rr, vr, p, what="init")
+    assert np.abs(vg.sum(axis=0)).max() < 1e-10
+
+
+def test_trajectory_100_steps_L16(orc):
+    """The small workload: 16^3 cells, 40,960 particles, 100 steps, compared by particle id
+    after every 10 steps and in full at the end."""
+    w = inputs.WORKLOADS["fp64_L16"]
+    p = abi.params_from_workload(w)
+    op = oracle_params(orc, p)
+    r0, v0 = orc.init(op, w.n_particles)
+    st = orc.State(r0, v0)
+    with abi.Box(p) as box:
+        box.set_state(r0, v0, 0)
+        for _ in range(10):
+            box.step(10)
+            orc.run(op, st, 10)
+            rg, vg = box.state()
+            rr, vr = st.by_id()
+            assert_state_close(rg, vg, rr, vr, p, what="t=%d" % st.t)
+        box.step(1)
+        ref = orc.step(op, st, debug=True)
+        assert_sort_equal(box.debug_sort(), ref)
+
+
+def test_moments_match_oracle(orc):
+    p = abi.make_params((7, 6, 5), mass=1.3)
+    n = int(round(p.ppc * 7 * 6 * 5))
+    r, v = inputs.uniform_gaussian_state((7, 6, 5), n, 8)
+    with abi.Box(p) as box:
+        box.set_state(r, v, 0)
+        abi.mpcd_record_moments(box.h, True)
+        box.step(1)
+        mom, shift = box.moments()
+    st = orc.State(r, v)
+    ref = orc.step(oracle_params(orc, p), st, debug=True)
+    assert np.array_equal(shift, ref["shift"])
+    assert np.array_equal(mom[:, 0], ref["moments"][:, 0]) or np.allclose(mom[:, 0], ref["moments"][:, 0], rtol=1e-15)
+    scale = np.maximum(np.abs(ref["moments"]).max(axis=0), 1.0)
+    assert np.all(np.abs(mom - ref["moments"]) <= 1e-12 * scale)
+
+
+def test_graph_and_timed_paths_agree():
+    """Graph replay and the event-timed launch path run the same kernels: identical bits."""
+    p = abi.make_params((12, 12, 12), resort_k=2)
+    outs = []
+    for timed in (False, True):
+        with abi.Box(p) as box:
+            if timed:
+                abi.mpcd_timing(box.h, True)
+            box.step(7)
+            outs.append(box.state())
+            if timed:
+                t = abi.mpcd_timing_read(box.h)
+                assert t["collide"][1] == 7 and t["scan"][1] == 21
+                assert all(ms >= 0 for ms, _ in t.values())
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_checkpoint_resume_bit_exact():
+    """Run 2n steps, or n steps + get_state/set_state + n steps: identical (storage kept in
+    id order so the summation order is the same in both runs)."""
+    p = abi.make_params((10, 10, 10), resort_k=0)
+    with abi.Box(p) as a, abi.Box(p) as b:
+        a.step(8)
+        b.step(4)
+        r, v = b.state()
+        b.set_state(r, v, 4)
+        b.step(4)
+        ra, va = a.state()
+        rb, vb = b.state()
+    assert np.array_equal(ra, rb) and np.array_equal(va, vb)
+
+
+def test_conservation_on_gpu():
+    p = abi.make_params((20, 20, 20))
+    with abi.Box(p) as box:
+        r, v = box.state()
+        P0, E0 = v.sum(axis=0), 0.5 * (v * v).sum()
+        box.step(50)
+        r, v = box.state()
+    assert np.abs(v.sum(axis=0) - P0).max() < 1e-9
+    assert abs(0.5 * (v * v).sum() / E0 - 1) < 1e-12
+
+
+def test_errors_reported():
+    p = abi.make_params((4, 4, 4))
+    with abi.Box(p) as box:
+        with pytest.raises(abi.MpcdError) as e:
+            box.debug_sort()
+        assert e.value.code == abi.MPCD_ERR_STATE
+        with pytest.raises(abi.MpcdError) as e:
+            box.moments()
+        assert e.value.code == abi.MPCD_ERR_STATE
+        r, v = box.state()
+        r[3, 1] = 4.0                              # outside [0, L a)
+        with pytest.raises(abi.MpcdError) as e:
+            box.set_state(r, v)
+        assert e.value.code == abi.MPCD_ERR_ARG
+        rc = abi.lib().mpcd_set_state(box.h, box.n - 1, r.ctypes.data, v.ctypes.data, 0)
+        assert rc == abi.MPCD_ERR_ARG
+        # the handle is still usable after argument errors
+        box.step(2)
+        assert abi.mpcd_steps_done(box.h) == 2
+        assert abi.mpcd_launch_count(box.h) > 0

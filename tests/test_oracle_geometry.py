@@ -106,3 +106,14 @@ def test_walls_layers(orc):
             assert key == _exact_key(L, (0.0, 0.0, z), (0.0, 0.0, sz), 1.0, walls=True)
             assert 0 <= key // 4 <= 4
     assert orc.num_cells(p) == 2 * 2 * 5
+
+
+def test_walls_layer_stays_in_range_for_inexact_a(orc):
+    """z just below H with a = 0.7, Lz = 5: (z - s)/a rounds to exactly Lz in FP64; the
+    layer must still be Lz (the top layer), not Lz + 1."""
+    p = orc.make_params((2, 2, 5), a=0.7, walls_z=1)
+    H = 5 * 0.7
+    z = np.nextafter(H, 0.0)
+    assert (z - 0.0) / 0.7 == 5.0        # the rounding that makes this an edge case
+    key = orc.cell_key(p, (0.1, 0.1, z), (0.0, 0.0, 0.0))
+    assert key // 4 == 5
