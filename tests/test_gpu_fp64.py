@@ -60,7 +60,7 @@ def test_steps_match_oracle(orc, name):
 
 
 def test_face_positions_bit_exact_keys(orc):
-    p = abi.make_params((6, 6, 6), dt=0.0)
+    p = abi.make_params((6, 6, 6), dt=0.0, ppc=2000 / 216)
     r, v = inputs.face_state((6, 6, 6), 2000, 5)
     run_pair(orc, p, r, v, steps=3)
 
