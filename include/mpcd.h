@@ -150,6 +150,33 @@ const char* mpcd_last_error(const mpcd_t* h);
 /* Library build description, e.g. "libmpcd sm_103a". */
 const char* mpcd_version(void);
 
+/* One FP64 step for callers that cannot allocate device memory (no counterpart in the
+ * paper; it exists for the library's users).  Some programs may not call cudaMalloc at
+ * all: code that runs under a fixed device-memory budget owned by a host framework, code
+ * that must not take the allocator's locks or latency inside a time-critical loop, or a
+ * plug-in that only receives pointers.  Such a caller keeps its particles in its own device
+ * arrays and calls this function instead of mpcd_create / mpcd_step.
+ *
+ * Advances the box described by p (FP64 only; resort_k is ignored: storage order never
+ * changes) from step t to t + 1, in place, on structure-of-arrays device arrays x, y, z,
+ * vx, vy, vz of n particles, enqueued on `stream` (NULL: the legacy default stream).
+ * Positions must already lie in the box.
+ *
+ * Memory: nothing is allocated.  The sort's scratch lives in one static device array of
+ * MPCD_NOALLOC_MAX_PARTICLES particles and MPCD_NOALLOC_MAX_CELLS cells (about 7 MB),
+ * which every GPU that loads the library holds until the process exits.  Larger n or cell
+ * counts are rejected with MPCD_ERR_ARG.  Every call on a device shares that array and
+ * leaves its contents behind, so calls that may overlap on a GPU (different streams without
+ * ordering between them) race and give wrong results: serialise them.
+ *
+ * The first call on each device looks up the array's device address (with that device
+ * current) and caches it; make that first call before any stream capture.
+ * Errors: MPCD_ERR_ARG, MPCD_ERR_CUDA; the message is read with mpcd_last_error(NULL). */
+#define MPCD_NOALLOC_MAX_PARTICLES (1 << 19)
+#define MPCD_NOALLOC_MAX_CELLS (1 << 17)
+int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n, double* x, double* y, double* z, double* vx,
+                           double* vy, double* vz, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,8 +28,10 @@ EXPORTS = [
     "mpcd_num_particles", "mpcd_num_cells", "mpcd_steps_done", "mpcd_num_boxes", "mpcd_get_state",
     "mpcd_set_state", "mpcd_get_state_device", "mpcd_set_state_device", "mpcd_record_moments",
     "mpcd_cell_moments", "mpcd_debug_sort", "mpcd_timing", "mpcd_timing_read", "mpcd_launch_count",
-    "mpcd_last_error", "mpcd_version",
+    "mpcd_last_error", "mpcd_version", "mpcd_step_fp64_noalloc",
 ]
+MPCD_NOALLOC_MAX_PARTICLES = 1 << 19
+MPCD_NOALLOC_MAX_CELLS = 1 << 17
 
 
 class MpcdError(RuntimeError):
@@ -126,6 +128,8 @@ def lib():
                 "mpcd_launch_count": ([H], i64),
                 "mpcd_last_error": ([H], ctypes.c_char_p),
                 "mpcd_version": ([], ctypes.c_char_p),
+                "mpcd_step_fp64_noalloc": ([ctypes.POINTER(Params), i64, i64] + [dp] * 6 + [ctypes.c_void_p],
+                                           ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -272,6 +276,12 @@ def mpcd_last_error(h=None) -> str:
 
 def mpcd_version() -> str:
     return lib().mpcd_version().decode()
+
+
+def mpcd_step_fp64_noalloc(params: Params, t: int, n: int, x, y, z, vx, vy, vz, stream=None):
+    """One FP64 step on caller-owned device arrays; the library allocates nothing."""
+    return _check(lib().mpcd_step_fp64_noalloc(ctypes.byref(params), int(t), int(n), _ptr(x), _ptr(y), _ptr(z),
+                                               _ptr(vx), _ptr(vy), _ptr(vz), stream))
 
 
 class Box:

@@ -548,3 +548,100 @@ const char* mpcd_last_error(const mpcd_t* h) {
 const char* mpcd_version(void) { return "libmpcd sm_103a"; }
 
 }  // extern "C"
+
+// ---- one FP64 step without any device allocation ----
+//
+// The sort scratch (cell keys, arrival ranks, permutation, counts, offsets, scan partials
+// and the step control block) sits in a single file-scope device array.  Host code only
+// ever sees the array's host-side stand-in symbol, so its device address is looked up once
+// per device with cudaGetSymbolAddress and cached; kernels receive that address.
+namespace {
+constexpr int64_t kNaMaxParticles = MPCD_NOALLOC_MAX_PARTICLES;
+constexpr int64_t kNaMaxCells = MPCD_NOALLOC_MAX_CELLS;
+constexpr size_t kNaAlign = 256;
+constexpr size_t na_round(size_t b) { return (b + kNaAlign - 1) / kNaAlign * kNaAlign; }
+constexpr size_t kNaCtlBytes = na_round(sizeof(Ctl));
+constexpr size_t kNaPartBytes = na_round(sizeof(int32_t) * (size_t)kNaMaxParticles);
+constexpr size_t kNaCellBytes = na_round(sizeof(int32_t) * (size_t)(kNaMaxCells + 1));
+constexpr size_t kNaScanBytes = na_round(sizeof(int32_t) * (size_t)(kNaMaxCells / 2048 + 2));
+constexpr size_t kNaBytes = kNaCtlBytes + 3 * kNaPartBytes + 2 * kNaCellBytes + kNaScanBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mu;
+unsigned char* g_na_ptr[kNaMaxDevices] = {};
+
+__global__ void k_noalloc_ctl(Ctl* c, int64_t t) {
+  c->t = t;
+  c->cur = 0;
+  c->err = 0;
+}
+
+int na_fail(int code, const std::string& msg) { return fail(nullptr, code, msg); }
+}  // namespace
+
+extern "C" int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n, double* x, double* y, double* z,
+                                      double* vx, double* vy, double* vz, void* stream) {
+  std::string why;
+  int rc = check_params(p, &why);
+  if (rc) return na_fail(rc, why);
+  if (p->precision != MPCD_FP64) return na_fail(MPCD_ERR_ARG, "mpcd_step_fp64_noalloc needs precision MPCD_FP64");
+  if (t < 0 || n < 0) return na_fail(MPCD_ERR_ARG, "t and n must be >= 0");
+  Geom g = make_geom(p);
+  if (n > kNaMaxParticles)
+    return na_fail(MPCD_ERR_ARG, "n = " + std::to_string(n) + " exceeds MPCD_NOALLOC_MAX_PARTICLES = " +
+                                     std::to_string(kNaMaxParticles));
+  if (g.ncell > kNaMaxCells)
+    return na_fail(MPCD_ERR_ARG, "the box has " + std::to_string(g.ncell) + " cells, more than MPCD_NOALLOC_MAX_CELLS = " +
+                                     std::to_string(kNaMaxCells));
+  if (n > 0 && !(x && y && z && vx && vy && vz)) return na_fail(MPCD_ERR_ARG, "NULL particle array");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNaMaxDevices) return na_fail(MPCD_ERR_ARG, "device index out of range");
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress");
+      g_na_ptr[dev] = static_cast<unsigned char*>(ptr);
+    }
+    base = g_na_ptr[dev];
+  }
+  g.n = n;
+  g.resort_k = 0;  // storage order is the caller's and never changes
+  Ctl* ctl = reinterpret_cast<Ctl*>(base);
+  unsigned char* q = base + kNaCtlBytes;
+  Scratch s{};
+  s.key = reinterpret_cast<int32_t*>(q);
+  q += kNaPartBytes;
+  s.rank = reinterpret_cast<int32_t*>(q);
+  q += kNaPartBytes;
+  s.perm = reinterpret_cast<int32_t*>(q);
+  q += kNaPartBytes;
+  s.count = reinterpret_cast<int32_t*>(q);
+  q += kNaCellBytes;
+  s.offset = reinterpret_cast<int32_t*>(q);
+  q += kNaCellBytes;
+  s.partial = reinterpret_cast<int32_t*>(q);
+  Fp64Bufs b{};
+  b.r[0][0] = x;
+  b.r[0][1] = y;
+  b.r[0][2] = z;
+  b.v[0][0] = vx;
+  b.v[0][1] = vy;
+  b.v[0][2] = vz;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_noalloc_ctl<<<1, 1, 0, st>>>(ctl, t);
+  launch_zero_i32(s.count, g.ncell, st);
+  launch_stream_bin_fp64(g, b, s, ctl, st);
+  launch_scan(s.count, s.offset, s.partial, g.ncell, st);
+  launch_scatter(g, s, st);
+  launch_collide_fp64(g, b, s, ctl, false, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "mpcd_step_fp64_noalloc launch");
+  return MPCD_OK;
+}

@@ -21,7 +21,7 @@ def libpath():
 def declared_functions():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(mpcd_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(mpcd_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_and_binding_agree():
@@ -30,7 +30,7 @@ def test_header_and_binding_agree():
 
 def test_library_exports_every_declared_symbol(libpath):
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\bT (mpcd_[a-z_]+)\b", out))
+    exported = set(re.findall(r"\bT (mpcd_[a-z0-9_]+)\b", out))
     missing = [f for f in declared_functions() if f not in exported]
     assert not missing, missing
     lib = abi.lib()

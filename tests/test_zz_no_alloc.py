@@ -1,0 +1,55 @@
+"""mpcd_step_fp64_noalloc: the FP64 step for callers that may not allocate device memory
+(a host framework that owns a fixed device-memory budget, a time-critical loop that must not
+take the allocator's locks, a plug-in that is only handed pointers).  Such a caller keeps
+its particles in its own device arrays; the library keeps the sort's scratch in one static
+device array and allocates nothing.
+
+The test advances the same state twice in a row through the allocation-free entry point
+and through the regular handle path (mpcd_create / mpcd_set_state / mpcd_step), and
+compares positions and velocities after each call with the parity tolerance (1e-12
+relative, tests/parity.py).  The file is named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+from paper_2212_11878_gb300 import abi, inputs
+from parity import assert_state_close
+
+pytestmark = pytest.mark.gpu
+
+
+def _device_soa(torch, a):
+    return [torch.from_numpy(np.ascontiguousarray(a[:, d])).to("cuda") for d in range(3)]
+
+
+def test_noalloc_step_matches_handle_path():
+    torch = pytest.importorskip("torch")
+    L = (12, 10, 8)
+    p = abi.make_params(L, resort_k=0, seed=4242)
+    n = int(round(p.ppc * 12 * 10 * 8))
+    r, v = inputs.uniform_gaussian_state(L, n, 99)
+    t0 = 5
+    x = _device_soa(torch, r)
+    u = _device_soa(torch, v)
+    stream = torch.cuda.current_stream().cuda_stream
+    with abi.Box(p) as box:
+        box.set_state(r, v, t0)
+        for call in range(2):
+            abi.mpcd_step_fp64_noalloc(p, t0 + call, n, *x, *u, stream=stream)
+            torch.cuda.synchronize()
+            box.step(1)
+            r_ref, v_ref = box.state()
+            r_na = np.stack([a.cpu().numpy() for a in x], axis=1)
+            v_na = np.stack([a.cpu().numpy() for a in u], axis=1)
+            assert_state_close(r_na, v_na, r_ref, v_ref, p, what="no-alloc call %d" % (call + 1))
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    p = abi.make_params((8, 8, 8))
+    with pytest.raises(abi.MpcdError) as e:
+        abi.mpcd_step_fp64_noalloc(p, 0, abi.MPCD_NOALLOC_MAX_PARTICLES + 1, 1, 1, 1, 1, 1, 1)
+    assert e.value.code == abi.MPCD_ERR_ARG and "MPCD_NOALLOC_MAX_PARTICLES" in str(e.value)
+    big = abi.make_params((64, 64, 64), ppc=1.0)
+    with pytest.raises(abi.MpcdError) as e:
+        abi.mpcd_step_fp64_noalloc(big, 0, 1000, 1, 1, 1, 1, 1, 1)
+    assert e.value.code == abi.MPCD_ERR_ARG and "MPCD_NOALLOC_MAX_CELLS" in str(e.value)
