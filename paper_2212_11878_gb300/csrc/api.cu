@@ -20,8 +20,8 @@ namespace {
 
 enum KernelSlot { kSlotZero = 0, kSlotStreamBin, kSlotScan, kSlotScatter, kSlotCollide, kSlotEndStep, kNumSlots };
 const char* kSlotNames[kNumSlots] = {"zero_counts", "stream_bin", "scan", "scatter", "collide", "end_step"};
-// kernels launched per slot per step
-const int kSlotLaunches[kNumSlots] = {1, 1, 3, 1, 1, 1};
+// kernels launched per slot per step (collide: two for periodic boxes without thermostat)
+const int kSlotLaunchesBase[kNumSlots] = {1, 1, 3, 1, 1, 1};
 
 std::mutex g_err_mu;
 std::string g_create_err;
@@ -52,6 +52,7 @@ struct mpcd_s {
   int cur = 0;
   bool last_resorted = false;
   bool any_step = false;
+  bool perm_sorted = false;  // perm of the last step is in storage order inside each cell
 
   bool record_moments = false;
   bool moments_valid = false;
@@ -65,6 +66,7 @@ struct mpcd_s {
   double slot_ms[kNumSlots] = {};
   int64_t slot_launches[kNumSlots] = {};
 
+  int per_step[kNumSlots] = {};  // kernels per slot per step for this box kind
   int64_t launches = 0;
   std::string err;
   bool poisoned = false;
@@ -134,6 +136,11 @@ Geom make_geom(const mpcd_params* p) {
   g.a = p->a;
   g.inv_a = 1.0 / p->a;
   g.pow2a = is_pow2(p->a) ? 1 : 0;
+  {
+    int e2 = 0;
+    std::frexp(p->a, &e2);
+    g.log2a = g.pow2a ? e2 - 1 : 0;
+  }
   for (int d = 0; d < 3; ++d) g.B[d] = (double)p->L[d] * p->a;
   g.dt = p->dt;
   g.force = 0;
@@ -212,9 +219,9 @@ int enqueue_step(mpcd_t* h, bool moments) {
   return MPCD_OK;
 }
 
-int launches_per_step() {
+int launches_per_step(const mpcd_t* h) {
   int k = 0;
-  for (int s = 0; s < kNumSlots; ++s) k += kSlotLaunches[s];
+  for (int s = 0; s < kNumSlots; ++s) k += h->per_step[s];
   return k;
 }
 
@@ -265,6 +272,8 @@ int create_common(const mpcd_params* p, mpcd_t** out) {
   }
   h->geom = make_geom(p);
   h->precision = p->precision;
+  for (int k = 0; k < kNumSlots; ++k) h->per_step[k] = kSlotLaunchesBase[k];
+  if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotCollide] = 2;
   h->n = h->geom.n;
   h->ncell = h->geom.ncell;
   auto bail = [&](int code) {
@@ -290,6 +299,10 @@ int create_common(const mpcd_params* p, mpcd_t** out) {
   if ((rc = dalloc(h, &h->scr.count, C))) return bail(rc);
   if ((rc = dalloc(h, &h->scr.offset, C + 1))) return bail(rc);
   if ((rc = dalloc(h, &h->scr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
+  if (!h->geom.walls && !h->geom.thermostat) {
+    if ((rc = dalloc(h, &h->scr.frame, 16 * C))) return bail(rc);
+    if ((rc = dalloc(h, &h->scr.inv, n))) return bail(rc);
+  }
   if ((rc = dalloc(h, &h->ctl, 1))) return bail(rc);
   h->red_blocks = 152 * 4;
   if ((rc = dalloc(h, &h->scr.red, 3 * (int64_t)h->red_blocks))) return bail(rc);
@@ -356,9 +369,10 @@ int mpcd_step(mpcd_t* h, int64_t nsteps) {
         if ((rc = build_graph(h))) return rc;
       MPCD_TRY(h, cudaGraphLaunch(h->graph, h->stream));
     }
-    h->launches += launches_per_step();
+    h->launches += launches_per_step(h);
     h->t += 1;
     h->last_resorted = resort_at(h, h->t);
+    h->perm_sorted = h->last_resorted || h->geom.walls || h->geom.thermostat;
     if (h->last_resorted) h->cur ^= 1;
     h->any_step = true;
     h->moments_valid = h->record_moments;
@@ -483,6 +497,13 @@ int mpcd_debug_sort(mpcd_t* h, int32_t* keys, int32_t* counts, int32_t* offsets,
   int rc = guard(h);
   if (rc) return rc;
   if (!h->any_step) return fail(h, MPCD_ERR_STATE, "no step has run since the state was set");
+  if (perm && !h->perm_sorted) {
+    // ordinary steps leave each cell's entries in arrival order; sort them for the caller
+    launch_sort_segments(h->geom, h->scr, h->stream);
+    MPCD_TRY(h, cudaGetLastError());
+    h->launches += 1;
+    h->perm_sorted = true;
+  }
   const size_t nb = sizeof(int32_t) * (size_t)h->n, cb = sizeof(int32_t) * (size_t)h->ncell;
   if (keys) MPCD_TRY(h, cudaMemcpyAsync(keys, h->scr.key, nb, cudaMemcpyDeviceToHost, h->stream));
   if (counts) MPCD_TRY(h, cudaMemcpyAsync(counts, h->scr.count, cb, cudaMemcpyDeviceToHost, h->stream));
@@ -521,7 +542,7 @@ int mpcd_timing_read(mpcd_t* h, int32_t nmax, const char** names, double* ms, in
     float el = 0.f;
     MPCD_TRY(h, cudaEventElapsedTime(&el, pt.a, pt.b));
     h->slot_ms[pt.slot] += el;
-    h->slot_launches[pt.slot] += kSlotLaunches[pt.slot];
+    h->slot_launches[pt.slot] += h->per_step[pt.slot];
     h->free_events.push_back(pt.a);
     h->free_events.push_back(pt.b);
   }
@@ -640,7 +661,7 @@ extern "C" int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n
   launch_stream_bin_fp64(g, b, s, ctl, st);
   launch_scan(s.count, s.offset, s.partial, g.ncell, st);
   launch_scatter(g, s, st);
-  launch_collide_fp64(g, b, s, ctl, false, st);
+  launch_collide_fp64_generic(g, b, s, ctl, false, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "mpcd_step_fp64_noalloc launch");
   return MPCD_OK;

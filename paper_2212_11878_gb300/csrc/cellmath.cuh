@@ -1,0 +1,174 @@
+// cellmath.cuh -- per-cell arithmetic of the collision step shared by every kernel path, so
+// that the dense and the generic collide kernels give bit-identical results.
+//
+//  * Exact cell sums: each FP64 velocity component is added to a 128-bit two's-complement
+//    fixed-point accumulator with 2^-80 resolution.  Integer addition is associative, so the
+//    sum does not depend on the order the particles arrive in, and converting the total
+//    back to FP64 rounds once.  The work runs on the integer pipe, which on GB300 is ~30x
+//    wider than the FP64 pipe.
+//  * Rotation frame: for a cell with centre-of-mass velocity u and random axis n, the
+//    collision v' = u + R(n, alpha)(v - u) (paper Sec. 2, parts (ii)-(iii)) is applied as
+//    v' = R v + b with b = u - R u, i.e. nine FMAs per particle.
+//  * Cell coordinates: floor() and the periodic-wrap comparisons are done on the IEEE bit
+//    patterns with integer instructions; only the operations whose rounding decides the
+//    cell (r + v dt, r - s) stay in FP64.
+#pragma once
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "mpcd_internal.h"
+
+namespace mpcd {
+
+// ------------------------------------------------------------ exact accumulator ----
+struct Fx128 {
+  unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ void fx_zero(Fx128& a) {
+  a.lo = 0ull;
+  a.hi = 0ull;
+}
+
+// a += x * 2^80 (exact for |x| >= 2^-27, truncated below 2^-80).  Returns false, leaving a
+// unchanged, when |x| >= 2^16: beyond that range a sum of up to 2^31 values could overflow.
+__device__ __forceinline__ bool fx_add(Fx128& a, double x) {
+  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(x));
+  const int e = static_cast<int>((bits >> 52) & 0x7FF);
+  if (e == 0) return true;          // zero or subnormal: below the 2^-80 grid
+  if (e > 1038) return false;       // |x| >= 2^16, or inf / NaN
+  const unsigned long long m = (bits & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int s = e - 995;            // x * 2^80 = m * 2^s, s <= 43
+  unsigned long long lo, hi;
+  if (s > 0) {
+    lo = m << s;
+    hi = m >> (64 - s);
+  } else if (s > -64) {
+    lo = m >> (-s);
+    hi = 0ull;
+  } else {
+    return true;
+  }
+  if (bits >> 63) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(a.lo), "+l"(a.hi) : "l"(lo), "l"(hi));
+  return true;
+}
+
+__device__ __forceinline__ double pow2i(int k) {  // 2^k for -1022 <= k <= 1023
+  return __longlong_as_double(static_cast<long long>(k + 1023) << 52);
+}
+
+// The accumulated value rounded once to FP64 (round to nearest even).
+__device__ __forceinline__ double fx_value(const Fx128& a) {
+  unsigned long long lo = a.lo, hi = a.hi;
+  const bool neg = static_cast<long long>(hi) < 0;
+  if (neg) {
+    lo = ~lo + 1ull;
+    hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+  }
+  if ((hi | lo) == 0ull) return 0.0;
+  unsigned long long top;
+  int k;
+  if (hi) {
+    const int lz = __clzll(static_cast<long long>(hi));
+    top = lz ? ((hi << lz) | (lo >> (64 - lz))) : hi;
+    const unsigned long long rest = lz ? (lo << lz) : lo;
+    top |= (rest != 0ull) ? 1ull : 0ull;  // sticky bit: keeps the single rounding correct
+    k = 64 - lz;
+  } else {
+    const int lz = __clzll(static_cast<long long>(lo));
+    top = lo << lz;
+    k = -lz;
+  }
+  const double d = __dmul_rn(__ull2double_rn(top), pow2i(k - 80));
+  return neg ? -d : d;
+}
+
+// 1/n for the common occupancies (constant-folded, correctly rounded); others divide.
+#define MPCD_INV8(k) 1.0 / (k), 1.0 / (k + 1), 1.0 / (k + 2), 1.0 / (k + 3), 1.0 / (k + 4), 1.0 / (k + 5), \
+                     1.0 / (k + 6), 1.0 / (k + 7)
+__constant__ double c_inv_n[65] = {0.0,           MPCD_INV8(1),  MPCD_INV8(9),  MPCD_INV8(17), MPCD_INV8(25),
+                                   MPCD_INV8(33), MPCD_INV8(41), MPCD_INV8(49), MPCD_INV8(57)};
+#undef MPCD_INV8
+
+__device__ __noinline__ double inv_count_slow(int n) { return 1.0 / static_cast<double>(n); }
+__device__ __forceinline__ double inv_count(int n) { return n <= 64 ? c_inv_n[n] : inv_count_slow(n); }
+
+// ---------------------------------------------------------------- rotation frame ----
+// R(n, alpha) v = cos(a) v + sin(a) (n x v) + (1 - cos(a)) (n . v) n; b = u - R u.
+__device__ __forceinline__ void make_frame(const Geom& g, int64_t t1, int64_t cell, double u0, double u1, double u2,
+                                           double R[9], double bvec[3]) {
+  double n[3];
+  random_axis(g.seed, t1, cell, n);
+  const double c = g.cos_a, s = g.sin_a, w = 1.0 - g.cos_a;
+  const double wx = w * n[0], wy = w * n[1], wz = w * n[2];
+  const double sx = s * n[0], sy = s * n[1], sz = s * n[2];
+  R[0] = fma(wx, n[0], c);
+  R[1] = fma(wx, n[1], -sz);
+  R[2] = fma(wx, n[2], sy);
+  R[3] = fma(wy, n[0], sz);
+  R[4] = fma(wy, n[1], c);
+  R[5] = fma(wy, n[2], -sx);
+  R[6] = fma(wz, n[0], -sy);
+  R[7] = fma(wz, n[1], sx);
+  R[8] = fma(wz, n[2], c);
+  bvec[0] = u0 - fma(R[0], u0, fma(R[1], u1, R[2] * u2));
+  bvec[1] = u1 - fma(R[3], u0, fma(R[4], u1, R[5] * u2));
+  bvec[2] = u2 - fma(R[6], u0, fma(R[7], u1, R[8] * u2));
+}
+
+__device__ __forceinline__ void apply_frame(const double R[9], const double bvec[3], double& v0, double& v1,
+                                            double& v2) {
+  const double a0 = fma(R[0], v0, fma(R[1], v1, fma(R[2], v2, bvec[0])));
+  const double a1 = fma(R[3], v0, fma(R[4], v1, fma(R[5], v2, bvec[1])));
+  const double a2 = fma(R[6], v0, fma(R[7], v1, fma(R[8], v2, bvec[2])));
+  v0 = a0;
+  v1 = a1;
+  v2 = a2;
+}
+
+// -------------------------------------------------------------- cell coordinates ----
+// floor(q * 2^k) for |q * 2^k| < 2^30 from the bit pattern of q (integer pipe only; the
+// power-of-two scale is an exponent shift, so no FP64 multiply is needed).  Larger
+// magnitudes return +-2^30; callers clamp coordinates into range.
+__device__ __forceinline__ int floor_bits(double q, int k = 0) {
+  const long long b = __double_as_longlong(q);
+  const int eb = static_cast<int>((b >> 52) & 0x7FF);
+  if (eb == 0) return (b < 0 && (b << 1) != 0) ? -1 : 0;  // zero or subnormal
+  const int e = eb - 1023 + k;
+  if (e < 0) return (b < 0) ? -1 : 0;                      // 0 < |q 2^k| < 1
+  if (e > 29) return (b < 0) ? -(1 << 30) : (1 << 30);
+  const unsigned long long m = (static_cast<unsigned long long>(b) & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int sh = 52 - e;
+  const int ip = static_cast<int>(m >> sh);
+  if (b >= 0) return ip;
+  return (m & ((1ull << sh) - 1ull)) ? -ip - 1 : -ip;
+}
+
+// Out-of-range part of the periodic wrap; kept out of line so that the compiler does not
+// evaluate its FP64 comparisons on the common in-range path.
+__device__ __noinline__ double wrap_slow(double x, double B) {
+  if (x >= B)
+    x = __dsub_rn(x, B);
+  else if (x < 0.0)
+    x = __dadd_rn(x, B);
+  if (x >= B || x < 0.0) {  // moved more than one box length, or rounded onto B
+    x = fmod(x, B);
+    if (x < 0.0) x = __dadd_rn(x, B);
+    if (x >= B) x = 0.0;
+  }
+  return x;
+}
+
+// Periodic wrap into [0, B): the in-range test runs on the bit patterns (for x >= +0 the
+// IEEE order is the integer order; negative x has the sign bit set).
+__device__ __forceinline__ double wrap_box(double x, double B, long long Bbits) {
+  const long long b = __double_as_longlong(x);
+  if (b < Bbits && (b >= 0 || (b << 1) == 0)) return x;  // 0 <= x < B (or -0.0)
+  return wrap_slow(x, B);
+}
+
+}  // namespace mpcd

@@ -11,6 +11,13 @@
 //               member's relative velocity by alpha (Sec. 2 (ii)-(iii)); on re-sort steps
 //               write the members to the other buffer set in cell order (Listing 1 permute).
 //   end_step    advances the device-side step counter.
+//
+// GB300 executes about 2 FP64 FMAs per clock per SM against ~128 FP32 and ~64 integer
+// operations, so these kernels keep in FP64 only what decides the result's rounding:
+// the streaming FMA and the r - s of the cell key (bit-exact keys), the nine FMAs of the
+// rotation and the per-cell frame.  Wraps, floors and the cell sums run on the integer
+// pipe (cellmath.cuh).
+#include "cellmath.cuh"
 #include "device_common.cuh"
 #include "mpcd_internal.h"
 
@@ -19,31 +26,31 @@ namespace mpcd {
 namespace {
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ double wrap_periodic(double x, double B) {
-  if (x >= B)
-    x = __dsub_rn(x, B);
-  else if (x < 0.0)
-    x = __dadd_rn(x, B);
-  if (x >= B || x < 0.0) {  // moved more than one box length, or rounded onto B
-    x = fmod(x, B);
-    if (x < 0.0) x = __dadd_rn(x, B);
-    if (x >= B) x = 0.0;
-  }
-  return x;
+unsigned grid_for(int64_t n, int per_thread = 1) {
+  int64_t blocks = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+  if (blocks < 1) blocks = 1;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  return static_cast<unsigned>(blocks);
 }
 
-// Cell coordinate along one axis on the grid shifted by s.
+
+__device__ __forceinline__ double wrap_periodic(double x, double B) {
+  return wrap_box(x, B, __double_as_longlong(B));
+}
+
+// Cell coordinate along one axis on the grid shifted by s (POW2A: a is a power of two, so
+// the division is an exponent shift inside floor_bits).
+template <int POW2A>
 __device__ __forceinline__ int cell_coord(double x, double s, const Geom& g, int d) {
   const double diff = __dsub_rn(x, s);
-  const double q = g.pow2a ? __dmul_rn(diff, g.inv_a) : __ddiv_rn(diff, g.a);
-  int c = static_cast<int>(floor(q));
+  int c = POW2A ? floor_bits(diff, -g.log2a) : floor_bits(__ddiv_rn(diff, g.a));
   if (g.walls && d == 2) {  // layers 0 .. Lz; rounding of (z - s)/a may reach Lz + 1
     c += 1;
     return c < 0 ? 0 : (c > g.L[2] ? g.L[2] : c);
   }
   if (c < 0) c += g.L[d];
   else if (c >= g.L[d]) c -= g.L[d];
-  return c;
+  return c < 0 ? 0 : (c >= g.L[d] ? g.L[d] - 1 : c);  // only a state outside the box gets here
 }
 
 // Ballistic move over dt with bounce-back at z = 0 and z = H (velocity reversed at the
@@ -86,8 +93,33 @@ __device__ __forceinline__ void stream_walls(const Geom& g, double r[3], double 
   if (r[2] < 0.0) r[2] = 0.0;
 }
 
-template <int WALLS, int FORCE>
-__global__ void __launch_bounds__(kThreads) k_stream_bin_fp64(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
+// Move one particle and return its cell key on the grid shifted by sh.
+template <int WALLS, int FORCE, int POW2A>
+__device__ __forceinline__ int move_and_key(const Geom& g, double r[3], double v[3], const double sh[3]) {
+  if (WALLS) {
+    stream_walls(g, r, v);
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (FORCE) {
+        r[d] = fma(v[d], g.dt, __dadd_rn(r[d], g.h[d]));
+        v[d] = fma(g.g[d], g.dt, v[d]);
+      } else {
+        r[d] = fma(v[d], g.dt, r[d]);
+      }
+    }
+    r[0] = wrap_box(r[0], g.B[0], __double_as_longlong(g.B[0]));
+    r[1] = wrap_box(r[1], g.B[1], __double_as_longlong(g.B[1]));
+    r[2] = wrap_box(r[2], g.B[2], __double_as_longlong(g.B[2]));
+  }
+  const int cx = cell_coord<POW2A>(r[0], sh[0], g, 0);
+  const int cy = cell_coord<POW2A>(r[1], sh[1], g, 1);
+  const int cz = cell_coord<POW2A>(r[2], sh[2], g, 2);
+  return cx + g.L[0] * (cy + g.L[1] * cz);
+}
+
+template <int WALLS, int FORCE, int POW2A>
+__global__ void __launch_bounds__(kThreads, 4) k_stream_bin_fp64(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
   __shared__ double sh[3];
   __shared__ int scur;
   if (threadIdx.x == 0) {
@@ -105,43 +137,55 @@ __global__ void __launch_bounds__(kThreads) k_stream_bin_fp64(Geom g, Fp64Bufs b
   }
   __syncthreads();
   const int cur = scur;
+  const double shl[3] = {sh[0], sh[1], sh[2]};
   double* __restrict__ rx = b.r[cur][0];
   double* __restrict__ ry = b.r[cur][1];
   double* __restrict__ rz = b.r[cur][2];
   double* __restrict__ vx = b.v[cur][0];
   double* __restrict__ vy = b.v[cur][1];
   double* __restrict__ vz = b.v[cur][2];
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
-    double r[3] = {rx[i], ry[i], rz[i]};
-    double v[3] = {vx[i], vy[i], vz[i]};
-    if (WALLS) {
-      stream_walls(g, r, v);
-    } else {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        if (FORCE) {
-          r[d] = fma(v[d], g.dt, __dadd_rn(r[d], g.h[d]));
-          v[d] = fma(g.g[d], g.dt, v[d]);
-        } else {
-          r[d] = fma(v[d], g.dt, r[d]);
-        }
-        r[d] = wrap_periodic(r[d], g.B[d]);
-      }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // two particles per thread and iteration, both loaded before either atomic: twice the
+  // loads in flight
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += 2 * stride) {
+    const int64_t j = i + stride;
+    const bool two = j < g.n;
+    double r0[3] = {rx[i], ry[i], rz[i]}, v0[3] = {vx[i], vy[i], vz[i]};
+    double r1[3] = {0.0, 0.0, 0.0}, v1[3] = {0.0, 0.0, 0.0};
+    if (two) {
+      r1[0] = rx[j];
+      r1[1] = ry[j];
+      r1[2] = rz[j];
+      v1[0] = vx[j];
+      v1[1] = vy[j];
+      v1[2] = vz[j];
     }
-    rx[i] = r[0];
-    ry[i] = r[1];
-    rz[i] = r[2];
+    const int k0 = move_and_key<WALLS, FORCE, POW2A>(g, r0, v0, shl);
+    const int k1 = two ? move_and_key<WALLS, FORCE, POW2A>(g, r1, v1, shl) : 0;
+    rx[i] = r0[0];
+    ry[i] = r0[1];
+    rz[i] = r0[2];
     if (WALLS || FORCE) {
-      vx[i] = v[0];
-      vy[i] = v[1];
-      vz[i] = v[2];
+      vx[i] = v0[0];
+      vy[i] = v0[1];
+      vz[i] = v0[2];
     }
-    const int cx = cell_coord(r[0], sh[0], g, 0);
-    const int cy = cell_coord(r[1], sh[1], g, 1);
-    const int cz = cell_coord(r[2], sh[2], g, 2);
-    const int key = cx + g.L[0] * (cy + g.L[1] * cz);
-    s.key[i] = key;
-    s.rank[i] = atomicAdd(&s.count[key], 1);
+    s.key[i] = k0;
+    if (two) {
+      rx[j] = r1[0];
+      ry[j] = r1[1];
+      rz[j] = r1[2];
+      if (WALLS || FORCE) {
+        vx[j] = v1[0];
+        vy[j] = v1[1];
+        vz[j] = v1[2];
+      }
+      s.key[j] = k1;
+    }
+    const int a0 = atomicAdd(&s.count[k0], 1);
+    const int a1 = two ? atomicAdd(&s.count[k1], 1) : 0;
+    s.rank[i] = a0;
+    if (two) s.rank[j] = a1;
   }
 }
 
@@ -152,19 +196,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter(int64_t n, const int32_t* 
     perm[offset[key[i]] + rank[i]] = static_cast<int32_t>(i);
 }
 
-// One thread per collision cell (the shape of Listing 4).
-template <int WALLS, int THERMO, int MOMENTS>
-__global__ void __launch_bounds__(kThreads) k_collide_fp64(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
-  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= g.ncell) return;
-  const int64_t t1 = ctl->t + 1;
-  const int cur = ctl->cur;
-  const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
-  const int o = s.offset[c];
-  const int n = s.offset[c + 1] - o;
-  int32_t* __restrict__ pm = s.perm + o;
-
-  // the counting atomics hand out arrival ranks in no fixed order: restore storage order
+// Insertion sort of a cell's perm entries: the counting atomics hand out arrival ranks in
+// no fixed order, the linked-cell list keeps storage order inside a cell.
+__device__ __forceinline__ void sort_entries(int32_t* pm, int n) {
   for (int j = 1; j < n; ++j) {
     const int x = pm[j];
     int k = j - 1;
@@ -174,97 +208,255 @@ __global__ void __launch_bounds__(kThreads) k_collide_fp64(Geom g, Fp64Bufs b, S
     }
     pm[k + 1] = x;
   }
+}
 
-  const double m = g.mass;
-  double M = 0.0, P0 = 0.0, P1 = 0.0, P2 = 0.0, E = 0.0;
-  for (int j = 0; j < n; ++j) {
+// Exact sums of a cell's velocities (and of v.v for the moments), four members at a time
+// so that their loads are in flight together.  `ok` turns false if a component reaches
+// 2^16; the cell is then summed in plain FP64 in perm order.
+template <int MOMENTS>
+__device__ __forceinline__ void cell_sums(const Fp64Bufs& b, int cur, const int32_t* pm, int n, double S[3], double& SE) {
+  const double* __restrict__ vx = b.v[cur][0];
+  const double* __restrict__ vy = b.v[cur][1];
+  const double* __restrict__ vz = b.v[cur][2];
+  Fx128 a0, a1, a2, ae;
+  fx_zero(a0);
+  fx_zero(a1);
+  fx_zero(a2);
+  fx_zero(ae);
+  bool ok = true;
+  int j = 0;
+  for (; j + 4 <= n; j += 4) {
+    int ii[4];
+    double x[4], y[4], z[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ii[k] = pm[j + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      x[k] = vx[ii[k]];
+      y[k] = vy[ii[k]];
+      z[k] = vz[ii[k]];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ok &= fx_add(a0, x[k]);
+      ok &= fx_add(a1, y[k]);
+      ok &= fx_add(a2, z[k]);
+      if (MOMENTS) ok &= fx_add(ae, fma(x[k], x[k], fma(y[k], y[k], z[k] * z[k])));
+    }
+  }
+  for (; j < n; ++j) {
     const int i = pm[j];
-    const double v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
-    P0 += m * v0;
-    P1 += m * v1;
-    P2 += m * v2;
-    M += m;
-    if (MOMENTS) E += 0.5 * m * (v0 * v0 + v1 * v1 + v2 * v2);
+    const double v0 = vx[i], v1 = vy[i], v2 = vz[i];
+    ok &= fx_add(a0, v0);
+    ok &= fx_add(a1, v1);
+    ok &= fx_add(a2, v2);
+    if (MOMENTS) ok &= fx_add(ae, fma(v0, v0, fma(v1, v1, v2 * v2)));
   }
-  if (MOMENTS) {
-    double* mo = s.moments + 5 * c;
-    mo[0] = M;
-    mo[1] = P0;
-    mo[2] = P1;
-    mo[3] = P2;
-    mo[4] = E;
+  if (ok) {
+    S[0] = fx_value(a0);
+    S[1] = fx_value(a1);
+    S[2] = fx_value(a2);
+    SE = MOMENTS ? fx_value(ae) : 0.0;
+    return;
   }
-  if (n == 0) return;
+  S[0] = S[1] = S[2] = SE = 0.0;
+  for (j = 0; j < n; ++j) {
+    const int i = pm[j];
+    const double v0 = vx[i], v1 = vy[i], v2 = vz[i];
+    S[0] += v0;
+    S[1] += v1;
+    S[2] += v2;
+    if (MOMENTS) SE += fma(v0, v0, fma(v1, v1, v2 * v2));
+  }
+}
 
+__device__ __forceinline__ void write_moments(const Geom& g, Scratch& s, int64_t c, int n, const double S[3], double SE) {
+  double* mo = s.moments + 5 * c;
+  mo[0] = static_cast<double>(n) * g.mass;
+  mo[1] = g.mass * S[0];
+  mo[2] = g.mass * S[1];
+  mo[3] = g.mass * S[2];
+  mo[4] = 0.5 * g.mass * SE;
+}
+
+// The whole collision of one cell by one thread (the shape of Listing 4): used for walls
+// and the thermostat, and by the dense kernel for groups of cells too large to stage.
+template <int WALLS, int THERMO, int MOMENTS>
+__device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& s, int64_t c, int64_t t1, int cur,
+                                     bool resort, double shift_z) {
+  const int o = s.offset[c];
+  const int n = s.offset[c + 1] - o;
+  int32_t* __restrict__ pm = s.perm + o;
+  sort_entries(pm, n);
+  double S[3], SE;
+  cell_sums<MOMENTS>(b, cur, pm, n, S, SE);
+  if (MOMENTS) write_moments(g, s, c, n, S, SE);
+  if (n == 0) return;
+  double u0 = S[0] * inv_count(n), u1 = S[1] * inv_count(n), u2 = S[2] * inv_count(n);
   bool virt = false;
   if (WALLS) {
-    const double sz = ctl->shift[2];
     const int64_t layer = c / ((int64_t)g.L[0] * g.L[1]);
-    if (sz > 0.0 && (layer == 0 || layer == g.L[2]) && (double)n < g.ppc) {
+    if (shift_z > 0.0 && (layer == 0 || layer == g.L[2]) && (double)n < g.ppc) {
+      // R13: virtual particles fill the cut cell to ppc, at rest on average
+      const double m = g.mass;
       const double Mv = (g.ppc - (double)n) * m;
       const u64x4 w = draw(g.seed, static_cast<uint64_t>(t1), static_cast<uint64_t>(c), kTagWall);
       double g0, g1, g2, g3;
       gauss_pair(w.x, w.y, g0, g1);
       gauss_pair(w.z, w.w, g2, g3);
       const double sd = sqrt(Mv * g.kT);
-      P0 += sd * g0;
-      P1 += sd * g1;
-      P2 += sd * g2;
-      M += Mv;
+      const double M = (double)n * m + Mv;
+      u0 = (m * S[0] + sd * g0) / M;
+      u1 = (m * S[1] + sd * g1) / M;
+      u2 = (m * S[2] + sd * g2) / M;
       virt = true;
     }
   }
-
+  const bool rotate = n >= 2 || virt;
+  double R[9], bv[3];
+  if (rotate) make_frame(g, t1, c, u0, u1, u2, R, bv);
   const int ob = cur ^ 1;
-  if (n >= 2 || virt) {
-    const double u0 = P0 / M, u1 = P1 / M, u2 = P2 / M;
-    double ax[3];
-    random_axis(g.seed, t1, c, ax);
-    const double ca = g.cos_a, sa = g.sin_a;
+  double f = 1.0;
+  if (rotate && THERMO && n >= 2) {
+    double K = 0.0;
     for (int j = 0; j < n; ++j) {
       const int i = pm[j];
-      const double d0 = b.v[cur][0][i] - u0, d1 = b.v[cur][1][i] - u1, d2 = b.v[cur][2][i] - u2;
-      const double par = ax[0] * d0 + ax[1] * d1 + ax[2] * d2;
-      const double c0 = ax[1] * d2 - ax[2] * d1;
-      const double c1 = ax[2] * d0 - ax[0] * d2;
-      const double c2 = ax[0] * d1 - ax[1] * d0;
-      const double w0 = par * ax[0] + ca * (d0 - par * ax[0]) + sa * c0;
-      const double w1 = par * ax[1] + ca * (d1 - par * ax[1]) + sa * c1;
-      const double w2 = par * ax[2] + ca * (d2 - par * ax[2]) + sa * c2;
-      b.v[cur][0][i] = u0 + w0;
-      b.v[cur][1][i] = u1 + w1;
-      b.v[cur][2][i] = u2 + w2;
+      double v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
+      apply_frame(R, bv, v0, v1, v2);
+      const double d0 = v0 - u0, d1 = v1 - u1, d2 = v2 - u2;
+      K += 0.5 * g.mass * fma(d0, d0, fma(d1, d1, d2 * d2));
     }
-    if (THERMO && n >= 2) {
-      double K = 0.0;
-      for (int j = 0; j < n; ++j) {
-        const int i = pm[j];
-        const double d0 = b.v[cur][0][i] - u0, d1 = b.v[cur][1][i] - u1, d2 = b.v[cur][2][i] - u2;
-        K += 0.5 * m * (d0 * d0 + d1 * d1 + d2 * d2);
-      }
-      if (K > 0.0) {
-        const double f = sqrt(1.5 * (double)(n - 1) * g.kT / K);
-        for (int j = 0; j < n; ++j) {
-          const int i = pm[j];
-          b.v[cur][0][i] = u0 + f * (b.v[cur][0][i] - u0);
-          b.v[cur][1][i] = u1 + f * (b.v[cur][1][i] - u1);
-          b.v[cur][2][i] = u2 + f * (b.v[cur][2][i] - u2);
-        }
+    if (K > 0.0) f = sqrt(1.5 * (double)(n - 1) * g.kT / K);
+  }
+  for (int j = 0; j < n; ++j) {
+    const int i = pm[j];
+    double v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
+    if (rotate) {
+      apply_frame(R, bv, v0, v1, v2);
+      if (THERMO && n >= 2) {
+        v0 = fma(f, v0 - u0, u0);
+        v1 = fma(f, v1 - u1, u1);
+        v2 = fma(f, v2 - u2, u2);
       }
     }
+    if (resort) {
+      const int dst = o + j;
+      b.r[ob][0][dst] = b.r[cur][0][i];
+      b.r[ob][1][dst] = b.r[cur][1][i];
+      b.r[ob][2][dst] = b.r[cur][2][i];
+      b.v[ob][0][dst] = v0;
+      b.v[ob][1][dst] = v1;
+      b.v[ob][2][dst] = v2;
+      b.id[ob][dst] = b.id[cur][i];
+    } else if (rotate) {
+      b.v[cur][0][i] = v0;
+      b.v[cur][1][i] = v1;
+      b.v[cur][2][i] = v2;
+    }
+  }
+}
+
+template <int WALLS, int THERMO, int MOMENTS>
+__global__ void __launch_bounds__(kThreads) k_collide_fp64_generic(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int64_t t1 = ctl->t + 1;
+  const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
+  collide_cell_generic<WALLS, THERMO, MOMENTS>(g, b, s, c, t1, ctl->cur, resort, ctl->shift[2]);
+}
+
+// Periodic box, no thermostat, in two passes so that each runs at full occupancy:
+//  k_cell_frame  one thread per cell: exact sums (order-independent, so the arrival order
+//                of the atomics does not matter), centre-of-mass velocity, random axis and
+//                the frame (R, b), written as one 128-byte record per cell.  On re-sort
+//                steps it also restores storage order inside the cell and records each
+//                particle's destination slot.
+//  k_rotate      one thread per storage slot: v' = R v + b with the frame of its cell (nine
+//                FP64 FMAs on full warps, coalesced state access); on re-sort steps the
+//                particle is written to its destination slot in the other buffer set.
+constexpr int kFrameStride = 16;  // doubles per cell record: R[9], b[3], flag, 3 unused
+
+template <int MOMENTS>
+__global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= g.ncell) return;
+  const int64_t t1 = ctl->t + 1;
+  const int cur = ctl->cur;
+  const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
+  const int o = s.offset[c];
+  const int n = s.offset[c + 1] - o;
+  int32_t* __restrict__ pm = s.perm + o;
+  if (resort) {
+    sort_entries(pm, n);
+    for (int j = 0; j < n; ++j) s.inv[pm[j]] = o + j;
+  }
+  double S[3], SE;
+  cell_sums<MOMENTS>(b, cur, pm, n, S, SE);
+  if (MOMENTS) write_moments(g, s, c, n, S, SE);
+  double2* __restrict__ rec = reinterpret_cast<double2*>(s.frame + kFrameStride * c);
+  const bool rotate = n >= 2;
+  if (!rotate) {
+    rec[6] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double in = inv_count(n);
+  double R[9], bv[3];
+  make_frame(g, t1, c, S[0] * in, S[1] * in, S[2] * in, R, bv);
+  rec[0] = make_double2(R[0], R[1]);
+  rec[1] = make_double2(R[2], R[3]);
+  rec[2] = make_double2(R[4], R[5]);
+  rec[3] = make_double2(R[6], R[7]);
+  rec[4] = make_double2(R[8], bv[0]);
+  rec[5] = make_double2(bv[1], bv[2]);
+  rec[6] = make_double2(1.0, 0.0);
+}
+
+__device__ __forceinline__ void rotate_slot(const Geom& g, const Fp64Bufs& b, const Scratch& s, int64_t i, int cur,
+                                            bool resort) {
+  const int c = s.key[i];
+  double v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
+  const double2* __restrict__ rec = reinterpret_cast<const double2*>(s.frame + kFrameStride * (int64_t)c);
+  const double2 f6 = rec[6];
+  const bool rot = f6.x != 0.0;
+  if (rot) {
+    const double2 f0 = rec[0], f1 = rec[1], f2 = rec[2], f3 = rec[3], f4 = rec[4], f5 = rec[5];
+    const double R[9] = {f0.x, f0.y, f1.x, f1.y, f2.x, f2.y, f3.x, f3.y, f4.x};
+    const double bv[3] = {f4.y, f5.x, f5.y};
+    apply_frame(R, bv, v0, v1, v2);
   }
   if (resort) {
-    for (int j = 0; j < n; ++j) {
-      const int i = pm[j];
-      const int dst = o + j;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        b.r[ob][d][dst] = b.r[cur][d][i];
-        b.v[ob][d][dst] = b.v[cur][d][i];
-      }
-      b.id[ob][dst] = b.id[cur][i];
-    }
+    const int ob = cur ^ 1;
+    const int dst = s.inv[i];
+    b.r[ob][0][dst] = b.r[cur][0][i];
+    b.r[ob][1][dst] = b.r[cur][1][i];
+    b.r[ob][2][dst] = b.r[cur][2][i];
+    b.v[ob][0][dst] = v0;
+    b.v[ob][1][dst] = v1;
+    b.v[ob][2][dst] = v2;
+    b.id[ob][dst] = b.id[cur][i];
+  } else if (rot) {
+    b.v[cur][0][i] = v0;
+    b.v[cur][1][i] = v1;
+    b.v[cur][2][i] = v2;
   }
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
+  const int64_t t1 = ctl->t + 1;
+  const int cur = ctl->cur;
+  const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
+    rotate_slot(g, b, s, i, cur, resort);
+}
+
+// Put every cell's perm entries in storage order (the linked-cell list's order); run on
+// demand when the last step did not need the sorted order itself.
+__global__ void __launch_bounds__(kThreads) k_sort_segments(int64_t ncell, const int32_t* __restrict__ offset,
+                                                            int32_t* __restrict__ perm) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncell) return;
+  const int o = offset[c];
+  sort_entries(perm + o, offset[c + 1] - o);
 }
 
 __global__ void k_end_step(Ctl* ctl, int32_t resort_k) {
@@ -362,12 +554,6 @@ __global__ void __launch_bounds__(kThreads) k_set_state_fp64(int64_t n, const do
   }
 }
 
-unsigned grid_for(int64_t n, int per_thread = 1) {
-  int64_t blocks = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
-  if (blocks < 1) blocks = 1;
-  if (blocks > 152 * 64) blocks = 152 * 64;
-  return static_cast<unsigned>(blocks);
-}
 }  // namespace
 
 void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st) {
@@ -377,32 +563,53 @@ void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ct
 }
 
 void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st) {
-  const unsigned grid = grid_for(g.n);
-  if (g.walls)
-    k_stream_bin_fp64<1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl);
-  else if (g.force)
-    k_stream_bin_fp64<0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl);
-  else
-    k_stream_bin_fp64<0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl);
+  const unsigned grid = grid_for(g.n, 2);
+  const int sel = (g.walls ? 4 : (g.force ? 2 : 0)) | (g.pow2a ? 1 : 0);
+  switch (sel) {
+    case 0: k_stream_bin_fp64<0, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 1: k_stream_bin_fp64<0, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 2: k_stream_bin_fp64<0, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 3: k_stream_bin_fp64<0, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 4: k_stream_bin_fp64<1, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    default: k_stream_bin_fp64<1, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+  }
 }
 
 void launch_scatter(const Geom& g, Scratch s, cudaStream_t st) {
   k_scatter<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.key, s.rank, s.offset, s.perm);
 }
 
-void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st) {
+void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st) {
   const unsigned grid = static_cast<unsigned>((g.ncell + kThreads - 1) / kThreads);
   const int sel = (g.walls ? 4 : 0) | (g.thermostat ? 2 : 0) | (moments ? 1 : 0);
   switch (sel) {
-    case 0: k_collide_fp64<0, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 1: k_collide_fp64<0, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 2: k_collide_fp64<0, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 3: k_collide_fp64<0, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 4: k_collide_fp64<1, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 5: k_collide_fp64<1, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 6: k_collide_fp64<1, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    default: k_collide_fp64<1, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 0: k_collide_fp64_generic<0, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 1: k_collide_fp64_generic<0, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 2: k_collide_fp64_generic<0, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 3: k_collide_fp64_generic<0, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 4: k_collide_fp64_generic<1, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 5: k_collide_fp64_generic<1, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 6: k_collide_fp64_generic<1, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    default: k_collide_fp64_generic<1, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
   }
+}
+
+void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st) {
+  if (g.walls || g.thermostat || !s.frame || !s.inv) {
+    launch_collide_fp64_generic(g, b, s, ctl, moments, st);
+    return;
+  }
+  const unsigned cgrid = static_cast<unsigned>((g.ncell + kThreads - 1) / kThreads);
+  if (moments)
+    k_cell_frame<1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl);
+  else
+    k_cell_frame<0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl);
+  k_rotate<<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl);
+}
+
+void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st) {
+  const unsigned grid = static_cast<unsigned>((g.ncell + kThreads - 1) / kThreads);
+  k_sort_segments<<<grid, kThreads, 0, st>>>(g.ncell, s.offset, s.perm);
 }
 
 void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st) { k_end_step<<<1, 1, 0, st>>>(ctl, g.resort_k); }

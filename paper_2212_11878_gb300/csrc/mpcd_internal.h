@@ -15,6 +15,8 @@ struct Geom {
   int32_t resort_k;    // physical re-sort period (0: never)
   int32_t pow2a;       // a is a power of two: (r - s) * (1/a) == (r - s) / a exactly
   int32_t force;       // any g component non-zero
+  int32_t log2a;       // a = 2^log2a when pow2a
+  int32_t pad0;
   double a, inv_a;
   double B[3];         // box edge lengths L[d] * a
   double dt;
@@ -62,6 +64,8 @@ struct Scratch {
   int32_t* offset;   // [C + 1] exclusive prefix sum of count
   int32_t* partial;  // scan partial sums
   double* moments;   // [5 C] per-cell M, Px, Py, Pz, E (only when recording)
+  double* frame;     // [16 C] per-cell record: R (9), b (3), rotate flag, 3 unused
+  int32_t* inv;      // [N] destination slot of each storage slot on re-sort steps
   double* red;       // [3 * reduce blocks] partial sums for the initial mean removal
 };
 
@@ -73,8 +77,13 @@ void launch_scan(const int32_t* count, int32_t* offset, int32_t* partial, int64_
 void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
 void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
 void launch_scatter(const Geom& g, Scratch s, cudaStream_t st);
+// periodic boxes without thermostat: cell_frame + rotate (needs s.frame, s.rotflag);
+// otherwise one thread per cell
 void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st);
+// one thread per cell for every box kind (no frame buffer needed)
+void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st);
 void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st);
+void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
 void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st);
 

@@ -57,6 +57,8 @@ class Workload:
 WORKLOADS = {
     "fp64_L16": Workload("fp64_L16", (16, 16, 16), seed=BASE_SEED + 0, steps=100, resort_k=1,
                          notes="plain FP64 SRD, 40,960 particles, 100 steps"),
+    "fp64_L64": Workload("fp64_L64", (64, 64, 64), seed=BASE_SEED + 1, steps=100, resort_k=10,
+                         notes="plain FP64 SRD, 2,621,440 particles (profiling size, state > L2)"),
     "fp64_L128": Workload("fp64_L128", (128, 128, 128), seed=BASE_SEED + 1, steps=1000, resort_k=10,
                           notes="plain FP64 SRD, 20,971,520 particles, full re-sort every 10 steps"),
     "mixed_L256": Workload("mixed_L256", (256, 256, 256), seed=BASE_SEED + 2, steps=500, precision="mixed",
