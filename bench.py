@@ -44,6 +44,17 @@ FP64_BYTES = {
 }
 FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # collide on re-sort steps also moves r and the ids
 ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step
+# mixed form: 32-byte records; collide_stream gathers through perm, writes in cell order and
+# writes the next step's keys and ranks
+MIXED_BYTES = {
+    "zero_counts": (0.0, 4.0),
+    "stream_bin": (32.0 + 8.0, 4.0),     # first step only
+    "scan": (0.0, 12.0),
+    "scatter": (12.0, 4.0),
+    "collide": (4.0 + 32.0 + 32.0 + 8.0, 8.0),
+    "end_step": (0.0, 0.0),
+}
+ALGO_STEP_BYTES_MIXED = 64.0
 
 
 def parse():
@@ -241,12 +252,14 @@ def main():
         C = box.ncell
         kernels = {}
         total_kernel_ms = sum(v[0] for v in ktimes.values())
+        mixed = p.precision == abi.MPCD_MIXED
+        model = MIXED_BYTES if mixed else FP64_BYTES
         for name, (kms, cnt) in ktimes.items():
-            per_p, per_c = FP64_BYTES.get(name, (0.0, 0.0))
+            per_p, per_c = model.get(name, (0.0, 0.0))
             # bytes per launch of this slot (a slot may hold several kernel launches)
             slot_launches = cnt / args.steps
             bytes_step = per_p * n + per_c * C
-            if name == "collide" and p.resort_k > 0:
+            if name == "collide" and p.resort_k > 0 and not mixed:
                 bytes_step += FP64_RESORT_EXTRA * n / p.resort_k
             kernels[name] = {"ms_per_step": kms / args.steps, "launches": cnt, "share": kms / total_kernel_ms,
                              "algo_bytes_per_step": bytes_step,
@@ -266,9 +279,10 @@ def main():
             "data": "synthetic",
             "config": {"workload": w.name, "L": list(w.L), "particles": n, "cells": C, "ppc": w.ppc,
                        "precision": w.precision, "resort_k": w.resort_k, "alpha_deg": w.alpha_deg, "dt": w.dt,
-                       "l2": "no flush: state %.2f GB > 129 MB L2" % (n * 104 / 1e9),
+                       "l2": "no flush: state %.2f GB > 129 MB L2" % (n * (64 if mixed else 104) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},
-            "hbm_roofline_frac_step": value / world * ALGO_STEP_BYTES_FP64 / 1e9 / hbm_peak,
+            "hbm_roofline_frac_step": value / world * (ALGO_STEP_BYTES_MIXED if mixed else ALGO_STEP_BYTES_FP64) / 1e9
+            / hbm_peak,
             "roofline": roofline,
             "kernels": kernels,
             "gpu_launches": launches,

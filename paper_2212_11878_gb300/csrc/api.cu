@@ -10,7 +10,8 @@
 #include <string>
 #include <vector>
 
-#include "../../include/mpcd.h"
+#include "mpcd.h"
+#include "cellmath.cuh"
 #include "device_common.cuh"
 #include "mpcd_internal.h"
 
@@ -43,7 +44,11 @@ struct mpcd_s {
   int64_t n = 0, ncell = 0;
   Fp64Bufs f64{};
   Scratch scr{};
+  MixBufs mix{};
+  MixScratch mscr{};
+  bool mixed_keys_valid = false;  // keys/ranks/counts of the next step exist (mixed form)
   Ctl* ctl = nullptr;
+  Ctl ctl_host{};  // host copy used to (re)initialise the device control block
   int red_blocks = 0;
   std::vector<void*> allocations;
 
@@ -57,7 +62,8 @@ struct mpcd_s {
   bool record_moments = false;
   bool moments_valid = false;
 
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;     // FP64: one step
+  cudaGraphExec_t graph_par[2] = {};   // mixed: one step starting from buffer set 0 / 1
   bool graph_moments = false;
 
   bool timing = false;
@@ -120,6 +126,15 @@ int check_params(const mpcd_params* p, std::string* why) {
   if (p->thermostat != 0 && p->thermostat != 1) return *why = "thermostat must be 0 or 1", MPCD_ERR_ARG;
   if (p->resort_k < 0) return *why = "resort_k must be >= 0", MPCD_ERR_ARG;
   if (p->reserved != 0) return *why = "reserved must be 0", MPCD_ERR_ARG;
+  if (p->precision == MPCD_MIXED) {
+    int bits = 0;
+    for (int d = 0; d < 3; ++d) {
+      int b = 0;
+      while ((1 << b) < p->L[d]) ++b;
+      bits += b;
+    }
+    if (bits > 31) return *why = "mixed precision packs the cell coordinates in 31 bits: box too large", MPCD_ERR_ARG;
+  }
   const double cells = (double)p->L[0] * p->L[1] * ((double)p->L[2] + (p->walls_z ? 1 : 0));
   if (cells > 2.0e9) return *why = "too many cells (limit 2e9)", MPCD_ERR_ARG;
   const double n = std::round(p->ppc * (double)p->L[0] * p->L[1] * p->L[2]);
@@ -155,6 +170,16 @@ Geom make_geom(const mpcd_params* p) {
   g.kT = p->kT;
   g.ppc = p->ppc;
   g.seed = p->seed;
+  g.dta = static_cast<float>(p->dt / p->a);
+  for (int d = 0; d < 3; ++d) {
+    g.ha[d] = static_cast<float>(0.5 * p->g[d] * p->dt * p->dt / p->a);
+    g.gdt[d] = static_cast<float>(p->g[d] * p->dt);
+    int b = 0;
+    while ((1 << b) < p->L[d]) ++b;
+    g.bits[d] = b;
+  }
+  g.cos_af = static_cast<float>(g.cos_a);
+  g.sin_af = static_cast<float>(g.sin_a);
   g.n = (int64_t)std::llround(p->ppc * (double)p->L[0] * p->L[1] * p->L[2]);
   g.ncell = (int64_t)p->L[0] * p->L[1] * ((int64_t)p->L[2] + (p->walls_z ? 1 : 0));
   return g;
@@ -205,17 +230,50 @@ int run_slot(mpcd_t* h, int slot, F&& launch) {
   return MPCD_OK;
 }
 
-// Enqueue one full step on h->stream.
-int enqueue_step(mpcd_t* h, bool moments) {
+// Enqueue one full step on h->stream.  `par` is the mixed form's buffer set at the start of
+// the step (the FP64 kernels read theirs from the control block).
+int enqueue_step(mpcd_t* h, bool moments, int par = 0) {
   const Geom& g = h->geom;
-  Scratch s = h->scr;
   int rc;
+  if (h->precision == MPCD_MIXED) {
+    MixScratch m = h->mscr;
+    const int nx = par ^ 1;
+    if ((rc = run_slot(h, kSlotZero, [&] {
+           launch_zero_i32(m.count[nx], g.ncell, h->stream);
+           launch_zero_i32(m.cursor, g.ncell, h->stream);
+         })))
+      return rc;
+    if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(m.count[par], m.offset, m.partial, g.ncell, h->stream); })))
+      return rc;
+    if ((rc = run_slot(h, kSlotScatter,
+                       [&] { launch_scatter_cursor(g.n, m.key[par], m.offset, m.cursor, m.perm, h->stream); })))
+      return rc;
+    if ((rc = run_slot(h, kSlotCollide,
+                       [&] { launch_collide_stream_mixed(g, h->mix, m, h->ctl, moments, h->stream); })))
+      return rc;
+    if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step_mixed(g, h->ctl, h->stream); }))) return rc;
+    return MPCD_OK;
+  }
+  Scratch s = h->scr;
   if ((rc = run_slot(h, kSlotZero, [&] { launch_zero_i32(s.count, g.ncell, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotStreamBin, [&] { launch_stream_bin_fp64(g, h->f64, s, h->ctl, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(s.count, s.offset, s.partial, g.ncell, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotScatter, [&] { launch_scatter(g, s, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotCollide, [&] { launch_collide_fp64(g, h->f64, s, h->ctl, moments, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step(g, h->ctl, h->stream); }))) return rc;
+  return MPCD_OK;
+}
+
+// Mixed form: keys, ranks and counts for the first step after the state was set.
+int enqueue_bin_mixed(mpcd_t* h) {
+  const Geom& g = h->geom;
+  MixScratch m = h->mscr;
+  const int par = h->cur;
+  int rc;
+  if ((rc = run_slot(h, kSlotZero, [&] { launch_zero_i32(m.count[par], g.ncell, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotStreamBin, [&] { launch_bin_mixed(g, h->mix, m, h->ctl, h->stream); }))) return rc;
+  h->launches += 2;
+  h->mixed_keys_valid = true;
   return MPCD_OK;
 }
 
@@ -228,15 +286,18 @@ int launches_per_step(const mpcd_t* h) {
 void drop_graph(mpcd_t* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (h->graph_par[k]) cudaGraphExecDestroy(h->graph_par[k]);
+    h->graph_par[k] = nullptr;
+  }
 }
 
-int build_graph(mpcd_t* h) {
-  drop_graph(h);
+int capture_step(mpcd_t* h, int par, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   MPCD_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   const bool saved = h->timing;
   h->timing = false;
-  int rc = enqueue_step(h, h->record_moments);
+  int rc = enqueue_step(h, h->record_moments, par);
   h->timing = saved;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   if (rc) {
@@ -244,9 +305,21 @@ int build_graph(mpcd_t* h) {
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&h->graph, graph, 0);
+  e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  return MPCD_OK;
+}
+
+int build_graph(mpcd_t* h) {
+  drop_graph(h);
+  int rc;
+  if (h->precision == MPCD_MIXED) {
+    for (int k = 0; k < 2; ++k)
+      if ((rc = capture_step(h, k, &h->graph_par[k]))) return rc;
+  } else {
+    if ((rc = capture_step(h, 0, &h->graph))) return rc;
+  }
   h->graph_moments = h->record_moments;
   return MPCD_OK;
 }
@@ -263,7 +336,6 @@ int create_common(const mpcd_params* p, mpcd_t** out) {
   std::string why;
   int rc = check_params(p, &why);
   if (rc) return fail(nullptr, rc, why);
-  if (p->precision != MPCD_FP64) return fail(nullptr, MPCD_ERR_ARG, "mixed precision is not built into this library yet");
   mpcd_t* h = new mpcd_t();
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
@@ -286,30 +358,48 @@ int create_common(const mpcd_params* p, mpcd_t** out) {
     return bail(cuda_fail(h, e, "cudaStreamCreate"));
   h->stream = h->own_stream;
   const int64_t n = h->n, C = h->ncell;
-  for (int k = 0; k < 2; ++k) {
-    for (int d = 0; d < 3; ++d) {
-      if ((rc = dalloc(h, &h->f64.r[k][d], n))) return bail(rc);
-      if ((rc = dalloc(h, &h->f64.v[k][d], n))) return bail(rc);
+  if (h->precision == MPCD_MIXED) {
+    h->per_step[kSlotStreamBin] = 0;  // binning is fused into the collide kernel
+    for (int k = 0; k < 2; ++k) {
+      if ((rc = dalloc(h, &h->mix.rec[k], n))) return bail(rc);
+      if ((rc = dalloc(h, &h->mscr.key[k], n))) return bail(rc);
+      if ((rc = dalloc(h, &h->mscr.count[k], C))) return bail(rc);
     }
-    if ((rc = dalloc(h, &h->f64.id[k], n))) return bail(rc);
-  }
-  if ((rc = dalloc(h, &h->scr.key, n))) return bail(rc);
-  if ((rc = dalloc(h, &h->scr.rank, n))) return bail(rc);
-  if ((rc = dalloc(h, &h->scr.perm, n))) return bail(rc);
-  if ((rc = dalloc(h, &h->scr.count, C))) return bail(rc);
-  if ((rc = dalloc(h, &h->scr.offset, C + 1))) return bail(rc);
-  if ((rc = dalloc(h, &h->scr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
-  if (!h->geom.walls && !h->geom.thermostat) {
-    if ((rc = dalloc(h, &h->scr.frame, 16 * C))) return bail(rc);
-    if ((rc = dalloc(h, &h->scr.inv, n))) return bail(rc);
+    if ((rc = dalloc(h, &h->mscr.cursor, C))) return bail(rc);
+    h->per_step[kSlotZero] = 2;
+    if ((rc = dalloc(h, &h->mscr.perm, n))) return bail(rc);
+    if ((rc = dalloc(h, &h->mscr.offset, C + 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->mscr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
+  } else {
+    for (int k = 0; k < 2; ++k) {
+      for (int d = 0; d < 3; ++d) {
+        if ((rc = dalloc(h, &h->f64.r[k][d], n))) return bail(rc);
+        if ((rc = dalloc(h, &h->f64.v[k][d], n))) return bail(rc);
+      }
+      if ((rc = dalloc(h, &h->f64.id[k], n))) return bail(rc);
+    }
+    if ((rc = dalloc(h, &h->scr.key, n))) return bail(rc);
+    if ((rc = dalloc(h, &h->scr.rank, n))) return bail(rc);
+    if ((rc = dalloc(h, &h->scr.perm, n))) return bail(rc);
+    if ((rc = dalloc(h, &h->scr.count, C))) return bail(rc);
+    if ((rc = dalloc(h, &h->scr.offset, C + 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->scr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
+    if (!h->geom.walls && !h->geom.thermostat) {
+      if ((rc = dalloc(h, &h->scr.frame, 16 * C))) return bail(rc);
+      if ((rc = dalloc(h, &h->scr.inv, n))) return bail(rc);
+    }
   }
   if ((rc = dalloc(h, &h->ctl, 1))) return bail(rc);
   h->red_blocks = 152 * 4;
   if ((rc = dalloc(h, &h->scr.red, 3 * (int64_t)h->red_blocks))) return bail(rc);
-  Ctl c0{};
-  if ((e = cudaMemcpyAsync(h->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+  h->ctl_host = Ctl{};
+  set_shifts(h->geom, &h->ctl_host);
+  if ((e = cudaMemcpyAsync(h->ctl, &h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
     return bail(cuda_fail(h, e, "cudaMemcpyAsync"));
-  launch_init_fp64(h->geom, h->f64, h->scr.red, h->red_blocks, h->ctl, h->stream);
+  if (h->precision == MPCD_MIXED)
+    launch_init_mixed(h->geom, h->mix, h->scr.red, h->red_blocks, h->ctl, h->stream);
+  else
+    launch_init_fp64(h->geom, h->f64, h->scr.red, h->red_blocks, h->ctl, h->stream);
   if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(h, e, "init kernels"));
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "init sync"));
   *out = h;
@@ -361,19 +451,22 @@ int mpcd_step(mpcd_t* h, int64_t nsteps) {
   int rc = guard(h);
   if (rc) return rc;
   if (nsteps < 0) return fail(h, MPCD_ERR_ARG, "nsteps must be >= 0");
+  const bool mixed = h->precision == MPCD_MIXED;
   for (int64_t k = 0; k < nsteps; ++k) {
+    if (mixed && !h->mixed_keys_valid)
+      if ((rc = enqueue_bin_mixed(h))) return rc;
     if (h->timing) {
-      if ((rc = enqueue_step(h, h->record_moments))) return rc;
+      if ((rc = enqueue_step(h, h->record_moments, h->cur))) return rc;
     } else {
-      if (!h->graph || h->graph_moments != h->record_moments)
+      if ((mixed ? !h->graph_par[0] : !h->graph) || h->graph_moments != h->record_moments)
         if ((rc = build_graph(h))) return rc;
-      MPCD_TRY(h, cudaGraphLaunch(h->graph, h->stream));
+      MPCD_TRY(h, cudaGraphLaunch(mixed ? h->graph_par[h->cur] : h->graph, h->stream));
     }
     h->launches += launches_per_step(h);
     h->t += 1;
-    h->last_resorted = resort_at(h, h->t);
-    h->perm_sorted = h->last_resorted || h->geom.walls || h->geom.thermostat;
+    h->last_resorted = mixed || resort_at(h, h->t);
     if (h->last_resorted) h->cur ^= 1;
+    h->perm_sorted = !mixed && (h->last_resorted || h->geom.walls || h->geom.thermostat);
     h->any_step = true;
     h->moments_valid = h->record_moments;
   }
@@ -396,7 +489,10 @@ int mpcd_get_state_device(mpcd_t* h, double* r_dev, double* v_dev) {
   int rc = guard(h);
   if (rc) return rc;
   if (!r_dev || !v_dev) return fail(h, MPCD_ERR_ARG, "NULL output");
-  launch_get_state_fp64(h->geom, h->f64, h->cur, r_dev, v_dev, h->stream);
+  if (h->precision == MPCD_MIXED)
+    launch_get_state_mixed(h->geom, h->mix, h->cur, r_dev, v_dev, h->stream);
+  else
+    launch_get_state_fp64(h->geom, h->f64, h->cur, r_dev, v_dev, h->stream);
   MPCD_TRY(h, cudaGetLastError());
   h->launches += 1;
   return MPCD_OK;
@@ -410,7 +506,10 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v) {
   double* scratch = nullptr;
   MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 6 * (size_t)(h->n > 0 ? h->n : 1),
                               h->stream));
-  launch_get_state_fp64(h->geom, h->f64, h->cur, scratch, scratch + 3 * h->n, h->stream);
+  if (h->precision == MPCD_MIXED)
+    launch_get_state_mixed(h->geom, h->mix, h->cur, scratch, scratch + 3 * h->n, h->stream);
+  else
+    launch_get_state_fp64(h->geom, h->f64, h->cur, scratch, scratch + 3 * h->n, h->stream);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(r, scratch, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess)
@@ -427,12 +526,16 @@ int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const doubl
   if (rc) return rc;
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!r_dev || !v_dev || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
-  launch_set_state_fp64(h->geom, h->f64, r_dev, v_dev, h->stream);
+  if (h->precision == MPCD_MIXED)
+    launch_set_state_mixed(h->geom, h->mix, r_dev, v_dev, h->stream);
+  else
+    launch_set_state_fp64(h->geom, h->f64, r_dev, v_dev, h->stream);
   MPCD_TRY(h, cudaGetLastError());
-  Ctl c0{};
-  c0.t = t;
-  c0.cur = 0;
-  MPCD_TRY(h, cudaMemcpyAsync(h->ctl, &c0, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+  h->mixed_keys_valid = false;
+  h->ctl_host = Ctl{};
+  h->ctl_host.t = t;
+  set_shifts(h->geom, &h->ctl_host);
+  MPCD_TRY(h, cudaMemcpyAsync(h->ctl, &h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
   h->launches += 1;
   h->t = t;
   h->cur = 0;
@@ -472,8 +575,10 @@ int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64
 int mpcd_record_moments(mpcd_t* h, int32_t enable) {
   int rc = guard(h);
   if (rc) return rc;
-  if (enable && !h->scr.moments)
+  if (enable && !h->scr.moments) {
     if ((rc = dalloc(h, &h->scr.moments, 5 * h->ncell))) return rc;
+    h->mscr.moments = h->scr.moments;
+  }
   h->record_moments = enable != 0;
   h->moments_valid = false;
   return MPCD_OK;
@@ -489,7 +594,7 @@ int mpcd_cell_moments(mpcd_t* h, double* out, double* shift_out) {
   MPCD_TRY(h, cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   if (shift_out)
-    for (int d = 0; d < 3; ++d) shift_out[d] = c.shift[d];
+    for (int d = 0; d < 3; ++d) shift_out[d] = c.shift_last[d];
   return MPCD_OK;
 }
 
@@ -497,21 +602,38 @@ int mpcd_debug_sort(mpcd_t* h, int32_t* keys, int32_t* counts, int32_t* offsets,
   int rc = guard(h);
   if (rc) return rc;
   if (!h->any_step) return fail(h, MPCD_ERR_STATE, "no step has run since the state was set");
+  const bool mixed = h->precision == MPCD_MIXED;
+  // the storage order at the start of the last step: the other buffer set after a re-sort
+  const int before = h->last_resorted ? (h->cur ^ 1) : h->cur;
+  Scratch s = h->scr;
+  if (mixed) {
+    s.key = h->mscr.key[before];
+    s.count = h->mscr.count[before];
+    s.offset = h->mscr.offset;
+    s.perm = h->mscr.perm;
+  }
   if (perm && !h->perm_sorted) {
     // ordinary steps leave each cell's entries in arrival order; sort them for the caller
-    launch_sort_segments(h->geom, h->scr, h->stream);
+    launch_sort_segments(h->geom, s, h->stream);
     MPCD_TRY(h, cudaGetLastError());
     h->launches += 1;
     h->perm_sorted = true;
   }
   const size_t nb = sizeof(int32_t) * (size_t)h->n, cb = sizeof(int32_t) * (size_t)h->ncell;
-  if (keys) MPCD_TRY(h, cudaMemcpyAsync(keys, h->scr.key, nb, cudaMemcpyDeviceToHost, h->stream));
-  if (counts) MPCD_TRY(h, cudaMemcpyAsync(counts, h->scr.count, cb, cudaMemcpyDeviceToHost, h->stream));
-  if (offsets) MPCD_TRY(h, cudaMemcpyAsync(offsets, h->scr.offset, cb + sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
-  if (perm) MPCD_TRY(h, cudaMemcpyAsync(perm, h->scr.perm, nb, cudaMemcpyDeviceToHost, h->stream));
+  if (keys) MPCD_TRY(h, cudaMemcpyAsync(keys, s.key, nb, cudaMemcpyDeviceToHost, h->stream));
+  if (counts) MPCD_TRY(h, cudaMemcpyAsync(counts, s.count, cb, cudaMemcpyDeviceToHost, h->stream));
+  if (offsets) MPCD_TRY(h, cudaMemcpyAsync(offsets, s.offset, cb + sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  if (perm) MPCD_TRY(h, cudaMemcpyAsync(perm, s.perm, nb, cudaMemcpyDeviceToHost, h->stream));
   if (ids) {
-    const int before = h->last_resorted ? (h->cur ^ 1) : h->cur;
-    MPCD_TRY(h, cudaMemcpyAsync(ids, h->f64.id[before], nb, cudaMemcpyDeviceToHost, h->stream));
+    if (mixed) {
+      std::vector<MixRec> recs((size_t)h->n);
+      MPCD_TRY(h, cudaMemcpyAsync(recs.data(), h->mix.rec[before], sizeof(MixRec) * (size_t)h->n,
+                                  cudaMemcpyDeviceToHost, h->stream));
+      MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+      for (int64_t i = 0; i < h->n; ++i) ids[i] = recs[(size_t)i].id;
+    } else {
+      MPCD_TRY(h, cudaMemcpyAsync(ids, h->f64.id[before], nb, cudaMemcpyDeviceToHost, h->stream));
+    }
   }
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   return MPCD_OK;
@@ -593,10 +715,11 @@ constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mu;
 unsigned char* g_na_ptr[kNaMaxDevices] = {};
 
-__global__ void k_noalloc_ctl(Ctl* c, int64_t t) {
+__global__ void k_noalloc_ctl(Geom g, Ctl* c, int64_t t) {
   c->t = t;
   c->cur = 0;
   c->err = 0;
+  set_shifts(g, c);
 }
 
 int na_fail(int code, const std::string& msg) { return fail(nullptr, code, msg); }
@@ -656,7 +779,7 @@ extern "C" int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n
   b.v[0][1] = vy;
   b.v[0][2] = vz;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  k_noalloc_ctl<<<1, 1, 0, st>>>(ctl, t);
+  k_noalloc_ctl<<<1, 1, 0, st>>>(g, ctl, t);
   launch_zero_i32(s.count, g.ncell, st);
   launch_stream_bin_fp64(g, b, s, ctl, st);
   launch_scan(s.count, s.offset, s.partial, g.ncell, st);

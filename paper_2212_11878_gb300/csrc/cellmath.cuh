@@ -90,11 +90,11 @@ __device__ __forceinline__ double fx_value(const Fx128& a) {
 // 1/n for the common occupancies (constant-folded, correctly rounded); others divide.
 #define MPCD_INV8(k) 1.0 / (k), 1.0 / (k + 1), 1.0 / (k + 2), 1.0 / (k + 3), 1.0 / (k + 4), 1.0 / (k + 5), \
                      1.0 / (k + 6), 1.0 / (k + 7)
-__constant__ double c_inv_n[65] = {0.0,           MPCD_INV8(1),  MPCD_INV8(9),  MPCD_INV8(17), MPCD_INV8(25),
+static __constant__ double c_inv_n[65] = {0.0,           MPCD_INV8(1),  MPCD_INV8(9),  MPCD_INV8(17), MPCD_INV8(25),
                                    MPCD_INV8(33), MPCD_INV8(41), MPCD_INV8(49), MPCD_INV8(57)};
 #undef MPCD_INV8
 
-__device__ __noinline__ double inv_count_slow(int n) { return 1.0 / static_cast<double>(n); }
+static __device__ __noinline__ double inv_count_slow(int n) { return 1.0 / static_cast<double>(n); }
 __device__ __forceinline__ double inv_count(int n) { return n <= 64 ? c_inv_n[n] : inv_count_slow(n); }
 
 // ---------------------------------------------------------------- rotation frame ----
@@ -150,7 +150,7 @@ __device__ __forceinline__ int floor_bits(double q, int k = 0) {
 
 // Out-of-range part of the periodic wrap; kept out of line so that the compiler does not
 // evaluate its FP64 comparisons on the common in-range path.
-__device__ __noinline__ double wrap_slow(double x, double B) {
+static __device__ __noinline__ double wrap_slow(double x, double B) {
   if (x >= B)
     x = __dsub_rn(x, B);
   else if (x < 0.0)
@@ -169,6 +169,22 @@ __device__ __forceinline__ double wrap_box(double x, double B, long long Bbits) 
   const long long b = __double_as_longlong(x);
   if (b < Bbits && (b >= 0 || (b << 1) == 0)) return x;  // 0 <= x < B (or -0.0)
   return wrap_slow(x, B);
+}
+
+// ------------------------------------------------------------------ grid shifts ----
+// Shift of step t in cell units for the mixed form; with walls the z part lies in [0, 1).
+__host__ __device__ __forceinline__ void shift_in_cells(const Geom& g, const double sd[3], float sf[3]) {
+  for (int d = 0; d < 3; ++d) sf[d] = static_cast<float>(sd[d] * g.inv_a);
+  if (g.walls && sf[2] >= 1.0f) sf[2] = 0.99999994f;
+}
+
+// Advance the control block's shifts so that they describe steps t + 1 and t + 2 (computed
+// once per step here instead of in every block of the step's kernels).
+__host__ __device__ __forceinline__ void set_shifts(const Geom& g, Ctl* c) {
+  grid_shift(g.seed, c->t + 1, g.a, g.walls, c->shift);
+  grid_shift(g.seed, c->t + 2, g.a, g.walls, c->shift_next);
+  shift_in_cells(g, c->shift, c->sf);
+  shift_in_cells(g, c->shift_next, c->sf_next);
 }
 
 }  // namespace mpcd

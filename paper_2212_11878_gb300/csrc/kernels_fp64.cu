@@ -120,24 +120,8 @@ __device__ __forceinline__ int move_and_key(const Geom& g, double r[3], double v
 
 template <int WALLS, int FORCE, int POW2A>
 __global__ void __launch_bounds__(kThreads, 4) k_stream_bin_fp64(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
-  __shared__ double sh[3];
-  __shared__ int scur;
-  if (threadIdx.x == 0) {
-    double sv[3];
-    grid_shift(g.seed, ctl->t + 1, g.a, g.walls, sv);
-    sh[0] = sv[0];
-    sh[1] = sv[1];
-    sh[2] = sv[2];
-    scur = ctl->cur;
-    if (blockIdx.x == 0) {
-      ctl->shift[0] = sv[0];
-      ctl->shift[1] = sv[1];
-      ctl->shift[2] = sv[2];
-    }
-  }
-  __syncthreads();
-  const int cur = scur;
-  const double shl[3] = {sh[0], sh[1], sh[2]};
+  const int cur = ctl->cur;
+  const double shl[3] = {ctl->shift[0], ctl->shift[1], ctl->shift[2]};
   double* __restrict__ rx = b.r[cur][0];
   double* __restrict__ ry = b.r[cur][1];
   double* __restrict__ rz = b.r[cur][2];
@@ -459,10 +443,12 @@ __global__ void __launch_bounds__(kThreads) k_sort_segments(int64_t ncell, const
   sort_entries(perm + o, offset[c + 1] - o);
 }
 
-__global__ void k_end_step(Ctl* ctl, int32_t resort_k) {
+__global__ void k_end_step(Geom g, Ctl* ctl) {
   const int64_t t1 = ctl->t + 1;
-  if (resort_k > 0 && (t1 % resort_k) == 0) ctl->cur ^= 1;
+  if (g.resort_k > 0 && (t1 % g.resort_k) == 0) ctl->cur ^= 1;
+  for (int d = 0; d < 3; ++d) ctl->shift_last[d] = ctl->shift[d];
   ctl->t = t1;
+  set_shifts(g, ctl);
 }
 
 // ---- initial state ----
@@ -612,7 +598,7 @@ void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st) {
   k_sort_segments<<<grid, kThreads, 0, st>>>(g.ncell, s.offset, s.perm);
 }
 
-void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st) { k_end_step<<<1, 1, 0, st>>>(ctl, g.resort_k); }
+void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st) { k_end_step<<<1, 1, 0, st>>>(g, ctl); }
 
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st) {
   k_get_state_fp64<<<grid_for(g.n), kThreads, 0, st>>>(g.n, b.r[cur][0], b.r[cur][1], b.r[cur][2], b.v[cur][0],

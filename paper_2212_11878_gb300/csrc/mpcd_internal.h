@@ -29,16 +29,26 @@ struct Geom {
   int64_t ncell;       // collision cells (walls: Lx Ly (Lz + 1))
   int64_t pbase;       // first particle of the box in the concatenated arrays (batched)
   int64_t cbase;       // first cell key of the box (batched)
+  // mixed form: positions in cell units (int cell coordinate + FP32 offset in [0, 1))
+  float dta;           // dt / a
+  float ha[3];         // g dt^2 / (2 a)
+  float gdt[3];        // g dt
+  float cos_af, sin_af;
+  int32_t bits[3];     // bits of each packed cell coordinate
 };
 
 // Device-resident step control, read by every kernel of a step so that one captured CUDA
 // graph can replay any step.
 struct Ctl {
-  int64_t t;          // completed steps; the step in flight is t + 1
-  int32_t cur;        // particle buffer set holding the state (0 or 1)
-  int32_t err;        // error bits raised by kernels
-  double shift[3];    // grid shift of the step in flight / the last step
-  double mean[3];     // scratch for the initial-momentum removal
+  int64_t t;            // completed steps; the step in flight is t + 1
+  int32_t cur;          // particle buffer set holding the state (0 or 1)
+  int32_t err;          // error bits raised by kernels
+  double shift[3];      // grid shift of step t + 1 (the next step to run)
+  double shift_next[3]; // grid shift of step t + 2
+  double shift_last[3]; // grid shift of step t (the last completed step)
+  double mean[3];       // scratch for the initial-momentum removal
+  float sf[3];          // shift of step t + 1 in cell units (mixed form)
+  float sf_next[3];     // shift of step t + 2 in cell units (mixed form)
 };
 
 // FP64 particle state, structure of arrays, two buffer sets for out-of-place re-sorting.
@@ -48,11 +58,32 @@ struct Fp64Bufs {
   int32_t* id[2];
 };
 
-// Mixed-precision particle state: pos = {ox, oy, oz, cell index as int bits},
-// vel = {vx, vy, vz, particle id as int bits}; 32 bytes per particle.
+// Mixed-precision particle record, 32 bytes (one DRAM sector): in-cell offsets in cell
+// units [0, 1), the home cell's coordinates packed as cx | cy << bits[0] | cz << (bits[0] +
+// bits[1]), FP32 velocity and the particle id.
+struct alignas(32) MixRec {
+  float ox, oy, oz;
+  int32_t cell;
+  float vx, vy, vz;
+  int32_t id;
+};
+
+// Two record buffers: every mixed step reads one and writes the other in cell order.
 struct MixBufs {
-  float4* pos[2];
-  float4* vel[2];
+  MixRec* rec[2];
+};
+
+// Scratch of the mixed step.  key/count are double-buffered: step t's collide kernel writes
+// the keys and counts of step t + 1 for the records it writes; the scatter takes each
+// particle's place in its cell from the per-cell cursor.
+struct MixScratch {
+  int32_t* key[2];
+  int32_t* count[2];
+  int32_t* cursor;
+  int32_t* offset;
+  int32_t* perm;
+  int32_t* partial;
+  double* moments;
 };
 
 // Per-step scratch of the counting sort and the cell reduction.
@@ -86,5 +117,16 @@ void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st);
 void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
 void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st);
+
+// ---- mixed form (kernels_mixed.cu) ----
+int mixed_cap(double ppc, int* cells_per_warp);  // staged records per warp; cells per warp group
+void launch_init_mixed(const Geom& g, MixBufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
+void launch_bin_mixed(const Geom& g, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st);
+void launch_collide_stream_mixed(const Geom& g, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st);
+void launch_end_step_mixed(const Geom& g, Ctl* ctl, cudaStream_t st);
+void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
+                           cudaStream_t st);
+void launch_get_state_mixed(const Geom& g, MixBufs b, int cur, double* r, double* v, cudaStream_t st);
+void launch_set_state_mixed(const Geom& g, MixBufs b, const double* r, const double* v, cudaStream_t st);
 
 }  // namespace mpcd

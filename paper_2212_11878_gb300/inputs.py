@@ -61,6 +61,10 @@ WORKLOADS = {
                          notes="plain FP64 SRD, 2,621,440 particles (profiling size, state > L2)"),
     "fp64_L128": Workload("fp64_L128", (128, 128, 128), seed=BASE_SEED + 1, steps=1000, resort_k=10,
                           notes="plain FP64 SRD, 20,971,520 particles, full re-sort every 10 steps"),
+    "mixed_L64": Workload("mixed_L64", (64, 64, 64), seed=BASE_SEED + 2, steps=500, precision="mixed", resort_k=1,
+                          notes="mixed form, 2,621,440 particles (error sub-run and profiling size)"),
+    "mixed_L128": Workload("mixed_L128", (128, 128, 128), seed=BASE_SEED + 2, steps=500, precision="mixed", resort_k=1,
+                           notes="mixed form, 20,971,520 particles"),
     "mixed_L256": Workload("mixed_L256", (256, 256, 256), seed=BASE_SEED + 2, steps=500, precision="mixed",
                            resort_k=1, notes="int32 cell + FP32 offset positions, FP32 velocities"),
     "poiseuille_256x64x64": Workload("poiseuille_256x64x64", (256, 64, 64), ppc=20.0, seed=BASE_SEED + 3,
