@@ -26,6 +26,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -159,11 +161,32 @@ def run_reference(args, w):
     print(json.dumps(line))
 
 
+class EnsembleWorkload:
+    """Adapter so that an ensemble recipe looks like a single workload to the bench."""
+
+    def __init__(self, name, rec):
+        self.name = name
+        self.rec = rec
+        self.L = (len(rec.sides), 0, 0)
+        self.n_particles = rec.n_particles
+        self.precision = "mixed"
+        self.ppc = float(np.mean(rec.ppc)) if rec.nbox else 0.0
+        self.resort_k = 1
+        self.alpha_deg = None
+        self.dt = None
+        self.seed = rec.seeds[0] if rec.nbox else 0
+
+
 def main():
     args = parse()
     from paper_2212_11878_gb300 import inputs
-    w = inputs.WORKLOADS[args.workload]
+    ensemble = args.workload in inputs.BATCH_WORKLOADS
+    w = (EnsembleWorkload(args.workload, inputs.batch_workload(args.workload)) if ensemble
+         else inputs.WORKLOADS[args.workload])
     if args.impl == "reference":
+        if ensemble:
+            print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle times single-box workloads"}))
+            return
         run_reference(args, w)
         return
 
@@ -179,8 +202,15 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     stream = torch.cuda.Stream()
-    p = abi.params_from_workload(w, seed=w.seed + rank)
-    box = abi.Box(p)
+    if ensemble:
+        plist = abi.params_from_recipe(w.rec)
+        for q in plist:
+            q.seed = q.seed + 1000003 * rank
+        box = abi.Box(batch=plist)
+        p = plist[0]
+    else:
+        p = abi.params_from_workload(w, seed=w.seed + rank)
+        box = abi.Box(p)
     h = box.h
     abi.mpcd_set_stream(h, stream.cuda_stream)
     n = box.n
@@ -239,7 +269,7 @@ def main():
     e2e_value = n * args.e2e_steps * world / e2e_s
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not ensemble:
         cpu = cpu_oracle_run(w, args.cpu_steps, "cpu_baseline")
 
     if rank == 0:
@@ -277,7 +307,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if p.precision == abi.MPCD_FP64 else "f32",
             "data": "synthetic",
-            "config": {"workload": w.name, "L": list(w.L), "particles": n, "cells": C, "ppc": w.ppc,
+            "config": {"workload": w.name, "L": list(w.L) if not ensemble else None,
+                       "boxes": w.rec.nbox if ensemble else 1, "particles": n, "cells": C, "ppc": w.ppc,
                        "precision": w.precision, "resort_k": w.resort_k, "alpha_deg": w.alpha_deg, "dt": w.dt,
                        "l2": "no flush: state %.2f GB > 129 MB L2" % (n * (64 if mixed else 104) / 1e9),
                        "parallelism": "replicas" if world > 1 else "single"},

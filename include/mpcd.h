@@ -72,11 +72,17 @@ typedef struct {
  * NULL on failure.  Errors: MPCD_ERR_ARG for invalid params, MPCD_ERR_OOM, MPCD_ERR_CUDA. */
 int mpcd_create(const mpcd_params* p, mpcd_t** out);
 
-/* Create an ensemble of nbox independent periodic boxes (each with its own L, ppc, dt,
- * alpha, seed) advanced together: one sort over the concatenated cell keys and one launch
- * sequence per step.  All boxes must share precision, walls_z = 0, thermostat and resort_k.
- * Particle and cell data of box b follow those of boxes 0..b-1. */
+/* Create an ensemble of nbox independent boxes (each with its own L, ppc, dt, alpha, g,
+ * seed) advanced together: one counting sort over the concatenated cell keys and one
+ * launch sequence per step (replayed from a CUDA graph).  Boxes use the mixed form
+ * (precision MPCD_MIXED) and must share walls_z and thermostat.  Particle and cell data of
+ * box b follow those of boxes 0..b-1 (mpcd_box_offsets).  Each box draws its random
+ * numbers from its own seed and is advanced exactly as if it were created alone. */
 int mpcd_batch_create(int32_t nbox, const mpcd_params* p, mpcd_t** out);
+
+/* First particle and first cell of every box: particle_base[nbox + 1], cell_base[nbox + 1]
+ * (either may be NULL).  Particle ids of box b are particle_base[b] .. particle_base[b+1]-1. */
+int mpcd_box_offsets(const mpcd_t* h, int64_t* particle_base, int64_t* cell_base);
 
 /* Free every device buffer of the handle.  NULL is accepted. */
 int mpcd_destroy(mpcd_t* h);
@@ -139,6 +145,26 @@ int mpcd_debug_sort(mpcd_t* h, int32_t* keys, int32_t* counts, int32_t* offsets,
  * Returns the number of kernels with data (>= 0) or an error. */
 int mpcd_timing(mpcd_t* h, int32_t enable);
 int mpcd_timing_read(mpcd_t* h, int32_t nmax, const char** names, double* ms, int64_t* launches);
+
+/* Launch and layout parameters that do not change results (the cell sums are exact, so
+ * the order in which particles are stored or visited never matters). */
+typedef struct {
+  int32_t group_target; /* mixed form: mean particles per warp's group of cells (32..224) */
+  int32_t warps;        /* mixed form: warps per collide block (2 or 4) */
+  int32_t resort_k;     /* FP64 form: physical re-sort period in steps (0: never) */
+  int32_t reserved;     /* must be 0 */
+} mpcd_tuning;
+
+int mpcd_get_tuning(const mpcd_t* h, mpcd_tuning* out);
+/* Errors: MPCD_ERR_ARG for out-of-range values. */
+int mpcd_set_tuning(mpcd_t* h, const mpcd_tuning* t);
+
+/* Autotuner: times each candidate tuning on the handle's own box(es) for trial_steps steps
+ * (CUDA events on the handle's stream), keeps the fastest and restores the state, so the
+ * simulation is unchanged.  Candidates: group_target in {96, 128, 160, 192, 224} x warps
+ * in {2, 4} for the mixed form; resort_k in {1, 2, 5, 10, 20, 50} for the FP64 form.
+ * *best receives the choice and *best_ms its time per step (either may be NULL). */
+int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* best_ms);
 
 /* Number of kernels this handle has launched (graph replays count each kernel node). */
 int64_t mpcd_launch_count(const mpcd_t* h);

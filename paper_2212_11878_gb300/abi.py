@@ -28,7 +28,8 @@ EXPORTS = [
     "mpcd_num_particles", "mpcd_num_cells", "mpcd_steps_done", "mpcd_num_boxes", "mpcd_get_state",
     "mpcd_set_state", "mpcd_get_state_device", "mpcd_set_state_device", "mpcd_record_moments",
     "mpcd_cell_moments", "mpcd_debug_sort", "mpcd_timing", "mpcd_timing_read", "mpcd_launch_count",
-    "mpcd_last_error", "mpcd_version", "mpcd_step_fp64_noalloc",
+    "mpcd_last_error", "mpcd_version", "mpcd_step_fp64_noalloc", "mpcd_box_offsets", "mpcd_get_tuning",
+    "mpcd_set_tuning", "mpcd_autotune",
 ]
 MPCD_NOALLOC_MAX_PARTICLES = 1 << 19
 MPCD_NOALLOC_MAX_CELLS = 1 << 17
@@ -61,6 +62,16 @@ class Params(ctypes.Structure):
     ]
 
 
+class Tuning(ctypes.Structure):
+    """Mirror of ``mpcd_tuning``."""
+
+    _fields_ = [("group_target", ctypes.c_int32), ("warps", ctypes.c_int32), ("resort_k", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {"group_target": self.group_target, "warps": self.warps, "resort_k": self.resort_k}
+
+
 def make_params(L, a=1.0, ppc=10.0, dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=20221211,
                 precision="fp64", walls_z=0, g=(0.0, 0.0, 0.0), thermostat=0, resort_k=1, alpha=None) -> Params:
     p = Params()
@@ -88,6 +99,12 @@ def params_from_workload(w, **override) -> Params:
               precision=w.precision, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat, resort_k=w.resort_k)
     kw.update(override)
     return make_params(**kw)
+
+
+def params_from_recipe(rec, precision="mixed", kT=1.0, mass=1.0):
+    """One Params per box of an ensemble recipe (paper_2212_11878_gb300.inputs.BatchRecipe)."""
+    return [make_params((s, s, s), ppc=ppc, alpha_deg=al, dt=dt, seed=sd, precision=precision, kT=kT, mass=mass)
+            for s, ppc, al, dt, sd in zip(rec.sides, rec.ppc, rec.alpha_deg, rec.dt, rec.seeds)]
 
 
 _lock = threading.Lock()
@@ -130,6 +147,10 @@ def lib():
                 "mpcd_version": ([], ctypes.c_char_p),
                 "mpcd_step_fp64_noalloc": ([ctypes.POINTER(Params), i64, i64] + [dp] * 6 + [ctypes.c_void_p],
                                            ctypes.c_int),
+                "mpcd_box_offsets": ([H, dp, dp], ctypes.c_int),
+                "mpcd_get_tuning": ([H, ctypes.POINTER(Tuning)], ctypes.c_int),
+                "mpcd_set_tuning": ([H, ctypes.POINTER(Tuning)], ctypes.c_int),
+                "mpcd_autotune": ([H, i32, ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -282,6 +303,39 @@ def mpcd_step_fp64_noalloc(params: Params, t: int, n: int, x, y, z, vx, vy, vz, 
     """One FP64 step on caller-owned device arrays; the library allocates nothing."""
     return _check(lib().mpcd_step_fp64_noalloc(ctypes.byref(params), int(t), int(n), _ptr(x), _ptr(y), _ptr(z),
                                                _ptr(vx), _ptr(vy), _ptr(vz), stream))
+
+
+def mpcd_box_offsets(h):
+    nb = mpcd_num_boxes(h)
+    pb = np.empty(nb + 1, np.int64)
+    cb = np.empty(nb + 1, np.int64)
+    _check(lib().mpcd_box_offsets(h, _ptr(pb), _ptr(cb)), h)
+    return pb, cb
+
+
+def mpcd_get_tuning(h) -> Tuning:
+    t = Tuning()
+    _check(lib().mpcd_get_tuning(h, ctypes.byref(t)), h)
+    return t
+
+
+def mpcd_set_tuning(h, group_target=None, warps=None, resort_k=None):
+    t = mpcd_get_tuning(h)
+    if group_target is not None:
+        t.group_target = int(group_target)
+    if warps is not None:
+        t.warps = int(warps)
+    if resort_k is not None:
+        t.resort_k = int(resort_k)
+    return _check(lib().mpcd_set_tuning(h, ctypes.byref(t)), h)
+
+
+def mpcd_autotune(h, trial_steps: int = 5):
+    """Returns (best Tuning, best ms per step); the state is left unchanged."""
+    t = Tuning()
+    ms = ctypes.c_double()
+    _check(lib().mpcd_autotune(h, int(trial_steps), ctypes.byref(t), ctypes.byref(ms)), h)
+    return t, ms.value
 
 
 class Box:

@@ -46,7 +46,18 @@ struct mpcd_s {
   Scratch scr{};
   MixBufs mix{};
   MixScratch mscr{};
-  bool mixed_keys_valid = false;  // keys/ranks/counts of the next step exist (mixed form)
+  bool mixed_keys_valid = false;  // keys and counts of the next step exist (mixed form)
+  // mixed form: per-box tables (host copies and device arrays)
+  std::vector<Geom> boxes;
+  std::vector<int64_t> pbase;
+  std::vector<MixGroup> groups;
+  Geom* d_boxes = nullptr;
+  BoxShift* d_shifts = nullptr;
+  MixGroup* d_groups = nullptr;
+  int64_t* d_pbase = nullptr;
+  int64_t groups_cap = 0;
+  MixBatch mb{};
+  mpcd_tuning tune{};
   Ctl* ctl = nullptr;
   Ctl ctl_host{};  // host copy used to (re)initialise the device control block
   int red_blocks = 0;
@@ -249,9 +260,9 @@ int enqueue_step(mpcd_t* h, bool moments, int par = 0) {
                        [&] { launch_scatter_cursor(g.n, m.key[par], m.offset, m.cursor, m.perm, h->stream); })))
       return rc;
     if ((rc = run_slot(h, kSlotCollide,
-                       [&] { launch_collide_stream_mixed(g, h->mix, m, h->ctl, moments, h->stream); })))
+                       [&] { launch_collide_stream_mixed(h->mb, h->mix, m, h->ctl, moments, h->stream); })))
       return rc;
-    if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step_mixed(g, h->ctl, h->stream); }))) return rc;
+    if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step_mixed(h->mb, h->ctl, h->stream); }))) return rc;
     return MPCD_OK;
   }
   Scratch s = h->scr;
@@ -271,7 +282,7 @@ int enqueue_bin_mixed(mpcd_t* h) {
   const int par = h->cur;
   int rc;
   if ((rc = run_slot(h, kSlotZero, [&] { launch_zero_i32(m.count[par], g.ncell, h->stream); }))) return rc;
-  if ((rc = run_slot(h, kSlotStreamBin, [&] { launch_bin_mixed(g, h->mix, m, h->ctl, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotStreamBin, [&] { launch_bin_mixed(h->mb, h->mix, m, h->ctl, h->stream); }))) return rc;
   h->launches += 2;
   h->mixed_keys_valid = true;
   return MPCD_OK;
@@ -332,44 +343,146 @@ int guard(mpcd_t* h) {
   return MPCD_OK;
 }
 
-int create_common(const mpcd_params* p, mpcd_t** out) {
+// Mixed form: per-box grid shifts of steps t + 1 and t + 2 to the device.
+int upload_shifts(mpcd_t* h, int64_t t) {
+  std::vector<BoxShift> sh(h->boxes.size());
+  for (size_t b = 0; b < h->boxes.size(); ++b) mixed_box_shifts(h->boxes[b], t, &sh[b]);
+  MPCD_TRY(h, cudaMemcpyAsync(h->d_shifts, sh.data(), sizeof(BoxShift) * sh.size(), cudaMemcpyHostToDevice, h->stream));
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPCD_OK;
+}
+
+// Mixed form: the table of warp groups (consecutive cells of one box, about
+// tune.group_target particles each) for the current tuning.
+int build_groups(mpcd_t* h) {
+  std::vector<MixGroup> gr;
+  for (size_t b = 0; b < h->boxes.size(); ++b) {
+    const Geom& g = h->boxes[b];
+    const int gc = mixed_cells_per_group(g.ppc, h->tune.group_target);
+    for (int64_t c = 0; c < g.ncell; c += gc) {
+      MixGroup x;
+      x.c0 = g.cbase + c;
+      x.box = static_cast<int32_t>(b);
+      x.ncells = static_cast<int32_t>(std::min<int64_t>(gc, g.ncell - c));
+      gr.push_back(x);
+    }
+  }
+  if ((int64_t)gr.size() > h->groups_cap) {
+    if (h->d_groups) {
+      cudaFree(h->d_groups);
+      for (auto& a : h->allocations)
+        if (a == h->d_groups) a = nullptr;
+      h->d_groups = nullptr;
+    }
+    int rc = dalloc(h, &h->d_groups, (int64_t)gr.size());
+    if (rc) return rc;
+    h->groups_cap = (int64_t)gr.size();
+  }
+  if (!gr.empty())
+    MPCD_TRY(h, cudaMemcpyAsync(h->d_groups, gr.data(), sizeof(MixGroup) * gr.size(), cudaMemcpyHostToDevice, h->stream));
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  h->groups = gr;
+  h->mb.groups = h->d_groups;
+  h->mb.ngroups = static_cast<int32_t>(gr.size());
+  h->mb.warps = h->tune.warps;
+  drop_graph(h);  // the graphs hold the old table
+  return MPCD_OK;
+}
+
+int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   std::string why;
-  int rc = check_params(p, &why);
-  if (rc) return fail(nullptr, rc, why);
+  for (int32_t b = 0; b < nbox; ++b) {
+    int rc = check_params(&p[b], &why);
+    if (rc) return fail(nullptr, rc, nbox > 1 ? "box " + std::to_string(b) + ": " + why : why);
+  }
+  if (nbox > 1) {
+    for (int32_t b = 0; b < nbox; ++b) {
+      if (p[b].precision != MPCD_MIXED) return fail(nullptr, MPCD_ERR_ARG, "ensembles use the mixed form (MPCD_MIXED)");
+      if (p[b].walls_z != p[0].walls_z || p[b].thermostat != p[0].thermostat)
+        return fail(nullptr, MPCD_ERR_ARG, "all boxes of an ensemble must share walls_z and thermostat");
+    }
+  }
   mpcd_t* h = new mpcd_t();
   cudaError_t e = cudaGetDevice(&h->device);
   if (e != cudaSuccess) {
     delete h;
     return fail(nullptr, MPCD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
   }
-  h->geom = make_geom(p);
-  h->precision = p->precision;
+  h->precision = p[0].precision;
+  h->nbox = nbox;
+  h->tune.group_target = 192;
+  h->tune.warps = 4;
+  h->tune.resort_k = p[0].resort_k;
+  // per-box geometry; the handle's geom describes the whole concatenation for the kernels
+  // that run over all cells or particles (zeroing, scan, sort)
+  int64_t ctot = 0, ntot = 0;
+  bool force = false;
+  h->pbase.push_back(0);
+  for (int32_t b = 0; b < nbox; ++b) {
+    Geom g = make_geom(&p[b]);
+    g.cbase = ctot;
+    g.pbase = ntot;
+    ctot += g.ncell;
+    ntot += g.n;
+    force = force || g.force;
+    h->boxes.push_back(g);
+    h->pbase.push_back(ntot);
+  }
+  if (ctot > 2000000000LL || ntot > 2000000000LL) {
+    delete h;
+    return fail(nullptr, MPCD_ERR_ARG, "the ensemble has more than 2e9 cells or particles");
+  }
+  h->geom = h->boxes[0];
+  h->geom.n = ntot;
+  h->geom.ncell = ctot;
   for (int k = 0; k < kNumSlots; ++k) h->per_step[k] = kSlotLaunchesBase[k];
   if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotCollide] = 2;
-  h->n = h->geom.n;
-  h->ncell = h->geom.ncell;
+  h->n = ntot;
+  h->ncell = ctot;
   auto bail = [&](int code) {
     std::string msg = h->err;
     mpcd_destroy(h);
     *out = nullptr;
     return fail(nullptr, code, msg);
   };
+  int rc;
   if ((e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(h, e, "cudaStreamCreate"));
   h->stream = h->own_stream;
   const int64_t n = h->n, C = h->ncell;
   if (h->precision == MPCD_MIXED) {
     h->per_step[kSlotStreamBin] = 0;  // binning is fused into the collide kernel
+    h->per_step[kSlotZero] = 2;
+    h->per_step[kSlotCollide] = 1;
     for (int k = 0; k < 2; ++k) {
       if ((rc = dalloc(h, &h->mix.rec[k], n))) return bail(rc);
       if ((rc = dalloc(h, &h->mscr.key[k], n))) return bail(rc);
       if ((rc = dalloc(h, &h->mscr.count[k], C))) return bail(rc);
     }
     if ((rc = dalloc(h, &h->mscr.cursor, C))) return bail(rc);
-    h->per_step[kSlotZero] = 2;
     if ((rc = dalloc(h, &h->mscr.perm, n))) return bail(rc);
     if ((rc = dalloc(h, &h->mscr.offset, C + 1))) return bail(rc);
     if ((rc = dalloc(h, &h->mscr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_boxes, nbox))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_shifts, nbox))) return bail(rc);
+    if ((rc = dalloc(h, &h->d_pbase, (int64_t)nbox + 1))) return bail(rc);
+    if ((e = cudaMemcpyAsync(h->d_boxes, h->boxes.data(), sizeof(Geom) * h->boxes.size(), cudaMemcpyHostToDevice,
+                             h->stream)) != cudaSuccess)
+      return bail(cuda_fail(h, e, "cudaMemcpyAsync"));
+    if ((e = cudaMemcpyAsync(h->d_pbase, h->pbase.data(), sizeof(int64_t) * h->pbase.size(), cudaMemcpyHostToDevice,
+                             h->stream)) != cudaSuccess)
+      return bail(cuda_fail(h, e, "cudaMemcpyAsync"));
+    h->mb.boxes = h->d_boxes;
+    h->mb.shifts = h->d_shifts;
+    h->mb.pbase = h->d_pbase;
+    h->mb.nbox = nbox;
+    h->mb.n = n;
+    h->mb.ncell = C;
+    h->mb.walls = h->geom.walls;
+    h->mb.force = force ? 1 : 0;
+    h->mb.thermostat = h->geom.thermostat;
+    if ((rc = build_groups(h))) return bail(rc);
+    if ((rc = upload_shifts(h, 0))) return bail(rc);
   } else {
     for (int k = 0; k < 2; ++k) {
       for (int d = 0; d < 3; ++d) {
@@ -396,10 +509,11 @@ int create_common(const mpcd_params* p, mpcd_t** out) {
   set_shifts(h->geom, &h->ctl_host);
   if ((e = cudaMemcpyAsync(h->ctl, &h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
     return bail(cuda_fail(h, e, "cudaMemcpyAsync"));
-  if (h->precision == MPCD_MIXED)
-    launch_init_mixed(h->geom, h->mix, h->scr.red, h->red_blocks, h->ctl, h->stream);
-  else
+  if (h->precision == MPCD_MIXED) {
+    for (const Geom& g : h->boxes) launch_init_mixed_box(g, h->mix, h->scr.red, h->red_blocks, h->ctl, h->stream);
+  } else {
     launch_init_fp64(h->geom, h->f64, h->scr.red, h->red_blocks, h->ctl, h->stream);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(h, e, "init kernels"));
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "init sync"));
   *out = h;
@@ -413,14 +527,14 @@ extern "C" {
 int mpcd_create(const mpcd_params* p, mpcd_t** out) {
   if (!out) return fail(nullptr, MPCD_ERR_ARG, "out is NULL");
   *out = nullptr;
-  return create_common(p, out);
+  return create_common(p, 1, out);
 }
 
 int mpcd_batch_create(int32_t nbox, const mpcd_params* p, mpcd_t** out) {
   if (!out) return fail(nullptr, MPCD_ERR_ARG, "out is NULL");
   *out = nullptr;
   if (nbox < 1 || !p) return fail(nullptr, MPCD_ERR_ARG, "nbox must be >= 1 and params non-NULL");
-  return fail(nullptr, MPCD_ERR_ARG, "batched boxes are not built into this library yet");
+  return create_common(p, nbox, out);
 }
 
 int mpcd_destroy(mpcd_t* h) {
@@ -490,7 +604,7 @@ int mpcd_get_state_device(mpcd_t* h, double* r_dev, double* v_dev) {
   if (rc) return rc;
   if (!r_dev || !v_dev) return fail(h, MPCD_ERR_ARG, "NULL output");
   if (h->precision == MPCD_MIXED)
-    launch_get_state_mixed(h->geom, h->mix, h->cur, r_dev, v_dev, h->stream);
+    launch_get_state_mixed(h->mb, h->mix, h->cur, r_dev, v_dev, h->stream);
   else
     launch_get_state_fp64(h->geom, h->f64, h->cur, r_dev, v_dev, h->stream);
   MPCD_TRY(h, cudaGetLastError());
@@ -507,7 +621,7 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v) {
   MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 6 * (size_t)(h->n > 0 ? h->n : 1),
                               h->stream));
   if (h->precision == MPCD_MIXED)
-    launch_get_state_mixed(h->geom, h->mix, h->cur, scratch, scratch + 3 * h->n, h->stream);
+    launch_get_state_mixed(h->mb, h->mix, h->cur, scratch, scratch + 3 * h->n, h->stream);
   else
     launch_get_state_fp64(h->geom, h->f64, h->cur, scratch, scratch + 3 * h->n, h->stream);
   cudaError_t e = cudaGetLastError();
@@ -527,7 +641,7 @@ int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const doubl
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!r_dev || !v_dev || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
   if (h->precision == MPCD_MIXED)
-    launch_set_state_mixed(h->geom, h->mix, r_dev, v_dev, h->stream);
+    launch_set_state_mixed(h->mb, h->mix, r_dev, v_dev, h->stream);
   else
     launch_set_state_fp64(h->geom, h->f64, r_dev, v_dev, h->stream);
   MPCD_TRY(h, cudaGetLastError());
@@ -536,6 +650,8 @@ int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const doubl
   h->ctl_host.t = t;
   set_shifts(h->geom, &h->ctl_host);
   MPCD_TRY(h, cudaMemcpyAsync(h->ctl, &h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
+  if (h->precision == MPCD_MIXED)
+    if ((rc = upload_shifts(h, t))) return rc;
   h->launches += 1;
   h->t = t;
   h->cur = 0;
@@ -550,13 +666,20 @@ int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64
   if (rc) return rc;
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!r || !v || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
-  for (int64_t i = 0; i < n; ++i)
-    for (int d = 0; d < 3; ++d) {
-      const double x = r[3 * i + d];
-      if (!(x >= 0.0 && x < h->geom.B[d]))
-        return fail(h, MPCD_ERR_ARG, "position outside the box at particle " + std::to_string(i));
-      if (!std::isfinite(v[3 * i + d])) return fail(h, MPCD_ERR_ARG, "non-finite velocity at particle " + std::to_string(i));
-    }
+  const int nb = h->precision == MPCD_MIXED ? static_cast<int>(h->boxes.size()) : 1;
+  for (int b = 0; b < nb; ++b) {
+    const Geom& gb = h->precision == MPCD_MIXED ? h->boxes[(size_t)b] : h->geom;
+    const int64_t i0 = h->precision == MPCD_MIXED ? h->pbase[(size_t)b] : 0;
+    const int64_t i1 = h->precision == MPCD_MIXED ? h->pbase[(size_t)b + 1] : n;
+    for (int64_t i = i0; i < i1; ++i)
+      for (int d = 0; d < 3; ++d) {
+        const double x = r[3 * i + d];
+        if (!(x >= 0.0 && x < gb.B[d]))
+          return fail(h, MPCD_ERR_ARG, "position outside its box at particle " + std::to_string(i));
+        if (!std::isfinite(v[3 * i + d]))
+          return fail(h, MPCD_ERR_ARG, "non-finite velocity at particle " + std::to_string(i));
+      }
+  }
   double* scratch = nullptr;
   MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 6 * (size_t)(n > 0 ? n : 1), h->stream));
   cudaError_t e = cudaMemcpyAsync(scratch, r, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
@@ -593,8 +716,15 @@ int mpcd_cell_moments(mpcd_t* h, double* out, double* shift_out) {
   Ctl c{};
   MPCD_TRY(h, cudaMemcpyAsync(&c, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, h->stream));
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
-  if (shift_out)
-    for (int d = 0; d < 3; ++d) shift_out[d] = c.shift_last[d];
+  if (shift_out) {
+    if (h->precision == MPCD_MIXED) {
+      BoxShift b0{};
+      MPCD_TRY(h, cudaMemcpy(&b0, h->d_shifts, sizeof(BoxShift), cudaMemcpyDeviceToHost));
+      for (int d = 0; d < 3; ++d) shift_out[d] = b0.s_last[d];
+    } else {
+      for (int d = 0; d < 3; ++d) shift_out[d] = c.shift_last[d];
+    }
+  }
   return MPCD_OK;
 }
 
@@ -681,6 +811,91 @@ int mpcd_timing_read(mpcd_t* h, int32_t nmax, const char** names, double* ms, in
 }
 
 int64_t mpcd_launch_count(const mpcd_t* h) { return h ? h->launches : -1; }
+
+int mpcd_box_offsets(const mpcd_t* h, int64_t* particle_base, int64_t* cell_base) {
+  if (!h) return MPCD_ERR_ARG;
+  const size_t nb = h->precision == MPCD_MIXED ? h->boxes.size() : 1;
+  for (size_t b = 0; b <= nb; ++b) {
+    if (particle_base) particle_base[b] = b < nb ? (h->precision == MPCD_MIXED ? h->boxes[b].pbase : 0) : h->n;
+    if (cell_base) cell_base[b] = b < nb ? (h->precision == MPCD_MIXED ? h->boxes[b].cbase : 0) : h->ncell;
+  }
+  return MPCD_OK;
+}
+
+int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* best_ms) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (trial_steps < 1) return fail(h, MPCD_ERR_ARG, "trial_steps must be >= 1");
+  if (h->timing) return fail(h, MPCD_ERR_STATE, "disable timing before autotuning");
+  std::vector<mpcd_tuning> cand;
+  if (h->precision == MPCD_MIXED) {
+    for (int w : {2, 4})
+      for (int tg : {96, 128, 160, 192, 224}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, 0});
+  } else {
+    for (int k : {1, 2, 5, 10, 20, 50}) cand.push_back(mpcd_tuning{h->tune.group_target, h->tune.warps, k, 0});
+  }
+  // keep the state: by-id FP64 copies are exact for both forms
+  const int64_t t0 = h->t;
+  double* save = nullptr;
+  MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&save), sizeof(double) * 6 * (size_t)(h->n > 0 ? h->n : 1),
+                              h->stream));
+  if ((rc = mpcd_get_state_device(h, save, save + 3 * h->n))) return rc;
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  MPCD_TRY(h, cudaEventCreate(&ea));
+  MPCD_TRY(h, cudaEventCreate(&eb));
+  double best_t = 1e300;
+  mpcd_tuning choice = h->tune;
+  for (const mpcd_tuning& c : cand) {
+    if ((rc = mpcd_set_tuning(h, &c))) break;
+    if ((rc = mpcd_step(h, 2))) break;  // builds the graph, warms the caches
+    MPCD_TRY(h, cudaEventRecord(ea, h->stream));
+    if ((rc = mpcd_step(h, trial_steps))) break;
+    MPCD_TRY(h, cudaEventRecord(eb, h->stream));
+    MPCD_TRY(h, cudaEventSynchronize(eb));
+    float ms = 0.f;
+    MPCD_TRY(h, cudaEventElapsedTime(&ms, ea, eb));
+    const double per = (double)ms / trial_steps;
+    if (per < best_t) {
+      best_t = per;
+      choice = c;
+    }
+  }
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  if (!rc) rc = mpcd_set_tuning(h, &choice);
+  if (!rc) rc = mpcd_set_state_device(h, h->n, save, save + 3 * h->n, t0);
+  cudaFreeAsync(save, h->stream);
+  if (rc) return rc;
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  if (best) *best = choice;
+  if (best_ms) *best_ms = best_t;
+  return MPCD_OK;
+}
+
+int mpcd_get_tuning(const mpcd_t* h, mpcd_tuning* out) {
+  if (!h || !out) return MPCD_ERR_ARG;
+  *out = h->tune;
+  return MPCD_OK;
+}
+
+int mpcd_set_tuning(mpcd_t* h, const mpcd_tuning* t) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (!t || t->reserved != 0 || t->group_target < 32 || t->group_target > 224 || (t->warps != 2 && t->warps != 4) ||
+      t->resort_k < 0)
+    return fail(h, MPCD_ERR_ARG, "tuning out of range (group_target 32..224, warps 2 or 4, resort_k >= 0)");
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  const mpcd_tuning old = h->tune;
+  h->tune = *t;
+  if (h->precision == MPCD_MIXED) {
+    if (old.group_target != t->group_target || old.warps != t->warps) return build_groups(h);
+  } else if (old.resort_k != t->resort_k) {
+    // the re-sort schedule is part of the captured step and of the step-end kernel
+    h->geom.resort_k = t->resort_k;
+    drop_graph(h);
+  }
+  return MPCD_OK;
+}
 
 const char* mpcd_last_error(const mpcd_t* h) {
   if (h) return h->err.c_str();

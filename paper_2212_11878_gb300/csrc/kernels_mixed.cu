@@ -31,9 +31,7 @@ namespace mpcd {
 
 namespace {
 constexpr int kThreads = 256;
-constexpr int kMixWarps = 4;  // warps per block of the collide kernel (static smem < 48 KB)
-constexpr int kMixCap = 256;  // records one warp stages in shared memory
-constexpr int kMixTarget = 192;  // mean records per warp group the cell grouping aims for
+
 
 unsigned grid_for(int64_t n, int per_thread = 1) {
   int64_t blocks = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
@@ -412,13 +410,26 @@ __device__ __forceinline__ void store_rec(MixRec* __restrict__ p, const MixRec& 
 }
 
 // ----------------------------------------------------------------------- kernels ----
+// Box of particle i (pbase is sorted; nbox + 1 entries).
+__device__ __forceinline__ int box_of(const int64_t* __restrict__ pbase, int nbox, int64_t i) {
+  int lo = 0, hi = nbox;  // pbase[lo] <= i < pbase[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (pbase[mid] <= i) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 template <int WALLS, int FORCE>
-__global__ void __launch_bounds__(kThreads) k_bin_mixed(Geom g, MixBufs b, MixScratch s, Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kThreads) k_bin_mixed(MixBatch mb, MixBufs b, MixScratch s, Ctl* __restrict__ ctl) {
   const int cur = ctl->cur;
-  const float sf[3] = {ctl->sf[0], ctl->sf[1], ctl->sf[2]};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mb.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int bx = box_of(mb.pbase, mb.nbox, i);
+    const Geom& g = mb.boxes[bx];
+    const float sf[3] = {mb.shifts[bx].sf[0], mb.shifts[bx].sf[1], mb.shifts[bx].sf[2]};
     const MixRec r = load_rec(b.rec[cur] + i);
-    const int k = next_key<WALLS, FORCE>(g, r, sf);
+    const int k = static_cast<int>(g.cbase) + next_key<WALLS, FORCE>(g, r, sf);
     s.key[cur][i] = k;
     atomicAdd(&s.count[cur][k], 1);
   }
@@ -460,20 +471,29 @@ __device__ __forceinline__ MixRec stage_get(const MixStage& st, int e) {
   return r;
 }
 
-template <int WALLS, int FORCE, int THERMO, int MOMENTS>
-__global__ void __launch_bounds__(kMixWarps * 32) k_collide_stream_mixed(Geom g, MixBufs b, MixScratch s, int gcells,
-                                                                        Ctl* __restrict__ ctl) {
-  __shared__ MixStage stage[kMixWarps];
+// One warp per group of cells of one box (the group table never straddles boxes).  The
+// per-cell random axis is keyed on the cell's index inside its box, so a box advanced in
+// an ensemble reproduces the same box advanced alone.
+template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
+__global__ void __launch_bounds__(WARPS * 32) k_collide_stream_mixed(MixBatch mb, MixBufs b, MixScratch s,
+                                                                    Ctl* __restrict__ ctl) {
+  __shared__ MixStage stage[WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t gi = (int64_t)blockIdx.x * WARPS + warp;
+  if (gi >= mb.ngroups) return;
+  const MixGroup grp = mb.groups[gi];
+  const Geom& g = mb.boxes[grp.box];
+  const BoxShift& sh = mb.shifts[grp.box];
   const int64_t t1 = ctl->t + 1;
   const int cur = ctl->cur, nxt = cur ^ 1;
-  const float sf[3] = {ctl->sf_next[0], ctl->sf_next[1], ctl->sf_next[2]};  // grid of the next step
-  const double shz = ctl->shift[2];                                        // grid of this step
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t c0 = ((int64_t)blockIdx.x * kMixWarps + warp) * gcells;
-  if (c0 >= g.ncell) return;
-  const int64_t cend = (c0 + gcells < g.ncell) ? c0 + gcells : g.ncell;
+  const float sf[3] = {sh.sf_next[0], sh.sf_next[1], sh.sf_next[2]};  // grid of the next step
+  const double shz = sh.s[2];                                        // grid of this step
+  const int cbase = static_cast<int>(g.cbase);
+  const int64_t c0 = grp.c0;
+  const int64_t cend = c0 + grp.ncells;
   const int64_t c = c0 + lane;
-  const bool live = lane < gcells && c < cend;
+  const bool live = lane < grp.ncells;
+  const int64_t cl = c - cbase;  // cell index inside the box
   const int E0 = s.offset[c0];
   const int E1 = s.offset[cend];
   const int E = E1 - E0;
@@ -492,9 +512,9 @@ __global__ void __launch_bounds__(kMixWarps * 32) k_collide_stream_mixed(Geom g,
         stream_record<WALLS, FORCE>(g, r);
         dst[o + j] = r;
       }
-      mixed_collide_cell<WALLS, THERMO, MOMENTS>(g, dst + o, n, c, t1, shz, s.moments);
+      mixed_collide_cell<WALLS, THERMO, MOMENTS>(g, dst + o, n, cl, t1, shz, MOMENTS ? s.moments + 5 * cbase : nullptr);
       for (int j = 0; j < n; ++j) {
-        const int k = next_key<WALLS, FORCE>(g, dst[o + j], sf);
+        const int k = cbase + next_key<WALLS, FORCE>(g, dst[o + j], sf);
         knext[o + j] = k;
         atomicAdd(&cnext[k], 1);
       }
@@ -539,7 +559,7 @@ __global__ void __launch_bounds__(kMixWarps * 32) k_collide_stream_mixed(Geom g,
     const bool ok = cell_sums_mixed<MOMENTS>(v, n, S, E2);
     if (MOMENTS) write_moments_mixed(g, s.moments, c, n, S, E2);
     CellFrame f;
-    cell_prologue<WALLS>(g, S, n, c, t1, shz, f);
+    cell_prologue<WALLS>(g, S, n, cl, t1, shz, f);
 #pragma unroll
     for (int k = 0; k < 3; ++k) st.fr[k][lane] = f.u[k];
 #pragma unroll
@@ -580,7 +600,7 @@ __global__ void __launch_bounds__(kMixWarps * 32) k_collide_stream_mixed(Geom g,
       r.vy = __fadd_rn(st.fr[1][j], fmaf(df, r.vy, r.vy));
       r.vz = __fadd_rn(st.fr[2][j], fmaf(df, r.vz, r.vz));
     }
-    const int k = next_key<WALLS, FORCE>(g, r, sf);
+    const int k = cbase + next_key<WALLS, FORCE>(g, r, sf);
     store_rec(dst + E0 + e, r);
     knext[E0 + e] = k;
     atomicAdd(&cnext[k], 1);
@@ -602,14 +622,28 @@ __global__ void __launch_bounds__(kThreads) k_scatter_cursor(int64_t n, const in
   }
 }
 
-__global__ void k_end_step_mixed(Geom g, Ctl* ctl) {
-  for (int d = 0; d < 3; ++d) ctl->shift_last[d] = ctl->shift[d];
-  ctl->t += 1;
-  ctl->cur ^= 1;
-  set_shifts(g, ctl);
+__device__ __forceinline__ void box_shifts(const Geom& g, int64_t t, BoxShift& b) {
+  grid_shift(g.seed, t + 1, g.a, g.walls, b.s);
+  grid_shift(g.seed, t + 2, g.a, g.walls, b.s_next);
+  shift_in_cells(g, b.s, b.sf);
+  shift_in_cells(g, b.s_next, b.sf_next);
 }
 
-// ---- initial state, the same Philox draws as the FP64 form ----
+__global__ void k_end_step_mixed(MixBatch mb, Ctl* ctl) {
+  const int64_t t = ctl->t + 1;  // completed steps after this one
+  for (int bx = blockIdx.x * blockDim.x + threadIdx.x; bx < mb.nbox; bx += gridDim.x * blockDim.x) {
+    BoxShift& sh = mb.shifts[bx];
+    for (int d = 0; d < 3; ++d) sh.s_last[d] = sh.s[d];
+    box_shifts(mb.boxes[bx], t, sh);
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->t = t;
+    ctl->cur ^= 1;
+  }
+}
+
+// ---- initial state, the same Philox draws as the FP64 form (one box per launch) ----
 __device__ __forceinline__ void init_draw(const Geom& g, int64_t i, double r[3], double v[3]) {
   const double sigma = sqrt(g.kT / g.mass);
   const u64x4 w = draw(g.seed, static_cast<uint64_t>(i), 0, kTagInit);
@@ -702,26 +736,28 @@ __global__ void __launch_bounds__(kThreads) k_init_mixed_write(Geom g, MixBufs b
     v[0] -= m0;
     v[1] -= m1;
     v[2] -= m2;
-    store_rec(b.rec[0] + i, to_record(g, r, v, static_cast<int32_t>(i)));
+    store_rec(b.rec[0] + g.pbase + i, to_record(g, r, v, static_cast<int32_t>(g.pbase + i)));
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_set_state_mixed(Geom g, MixBufs b, const double* __restrict__ r,
+__global__ void __launch_bounds__(kThreads) k_set_state_mixed(MixBatch mb, MixBufs b, const double* __restrict__ r,
                                                               const double* __restrict__ v) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mb.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const Geom& g = mb.boxes[box_of(mb.pbase, mb.nbox, i)];
     const double ri[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
     const double vi[3] = {v[3 * i], v[3 * i + 1], v[3 * i + 2]};
     store_rec(b.rec[0] + i, to_record(g, ri, vi, static_cast<int32_t>(i)));
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_get_state_mixed(Geom g, const MixRec* __restrict__ rec, double* __restrict__ r,
-                                                              double* __restrict__ v) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(kThreads) k_get_state_mixed(MixBatch mb, const MixRec* __restrict__ rec,
+                                                              double* __restrict__ r, double* __restrict__ v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mb.n; i += (int64_t)gridDim.x * blockDim.x) {
     const MixRec q = load_rec(rec + i);
+    const int64_t p = q.id;
+    const Geom& g = mb.boxes[box_of(mb.pbase, mb.nbox, p)];
     int cc[3];
     unpack_cell(g, q.cell, cc);
-    const int64_t p = q.id;
     r[3 * p + 0] = ((double)cc[0] + (double)q.ox) * g.a;
     r[3 * p + 1] = ((double)cc[1] + (double)q.oy) * g.a;
     r[3 * p + 2] = ((double)cc[2] + (double)q.oz) * g.a;
@@ -732,65 +768,77 @@ __global__ void __launch_bounds__(kThreads) k_get_state_mixed(Geom g, const MixR
 }
 }  // namespace
 
-int mixed_cap(double ppc, int* cells_per_warp) {
-  // about kMixTarget records per warp on average, never more than 32 cells (one per lane)
-  int gc = ppc > 0.0 ? static_cast<int>(kMixTarget / ppc) : 32;
+int mixed_cells_per_group(double ppc, int target) {
+  int gc = ppc > 0.0 ? static_cast<int>(target / ppc) : 32;
   if (gc > 32) gc = 32;
   if (gc < 1) gc = 1;
-  *cells_per_warp = gc;
-  return kMixCap;
+  return gc;
 }
 
-void launch_init_mixed(const Geom& g, MixBufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st) {
+void mixed_box_shifts(const Geom& g, int64_t t, BoxShift* out) {
+  grid_shift(g.seed, t + 1, g.a, g.walls, out->s);
+  grid_shift(g.seed, t + 2, g.a, g.walls, out->s_next);
+  for (int d = 0; d < 3; ++d) out->s_last[d] = 0.0;
+  shift_in_cells(g, out->s, out->sf);
+  shift_in_cells(g, out->s_next, out->sf_next);
+}
+
+void launch_init_mixed_box(const Geom& g, MixBufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st) {
   k_init_mixed_sum<<<red_blocks, kThreads, 0, st>>>(g, red);
   k_init_mixed_mean<<<1, kThreads, 0, st>>>(red, red_blocks, g.n, ctl);
   k_init_mixed_write<<<grid_for(g.n), kThreads, 0, st>>>(g, b, ctl);
 }
 
-void launch_bin_mixed(const Geom& g, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st) {
-  if (g.walls)
-    k_bin_mixed<1, 1><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl);
-  else if (g.force)
-    k_bin_mixed<0, 1><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl);
+void launch_bin_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st) {
+  if (mb.walls)
+    k_bin_mixed<1, 1><<<grid_for(mb.n), kThreads, 0, st>>>(mb, b, s, ctl);
+  else if (mb.force)
+    k_bin_mixed<0, 1><<<grid_for(mb.n), kThreads, 0, st>>>(mb, b, s, ctl);
   else
-    k_bin_mixed<0, 0><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl);
+    k_bin_mixed<0, 0><<<grid_for(mb.n), kThreads, 0, st>>>(mb, b, s, ctl);
 }
 
-void launch_collide_stream_mixed(const Geom& g, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st) {
-  int gc = 32;
-  mixed_cap(g.ppc, &gc);
-  const int64_t groups = (g.ncell + gc - 1) / gc;
-  const unsigned grid = static_cast<unsigned>((groups + kMixWarps - 1) / kMixWarps);
-  const int sel = (g.walls ? 8 : (g.force ? 4 : 0)) | (g.thermostat ? 2 : 0) | (moments ? 1 : 0);
+template <int WARPS>
+void launch_collide_w(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st) {
+  const unsigned grid = static_cast<unsigned>((mb.ngroups + WARPS - 1) / WARPS);
+  if (grid == 0) return;
+  const int sel = (mb.walls ? 8 : (mb.force ? 4 : 0)) | (mb.thermostat ? 2 : 0) | (moments ? 1 : 0);
   switch (sel) {
-    case 0: k_collide_stream_mixed<0, 0, 0, 0><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 1: k_collide_stream_mixed<0, 0, 0, 1><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 2: k_collide_stream_mixed<0, 0, 1, 0><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 3: k_collide_stream_mixed<0, 0, 1, 1><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 4: k_collide_stream_mixed<0, 1, 0, 0><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 5: k_collide_stream_mixed<0, 1, 0, 1><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 6: k_collide_stream_mixed<0, 1, 1, 0><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 7: k_collide_stream_mixed<0, 1, 1, 1><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 8: k_collide_stream_mixed<1, 1, 0, 0><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 9: k_collide_stream_mixed<1, 1, 0, 1><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    case 10: k_collide_stream_mixed<1, 1, 1, 0><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
-    default: k_collide_stream_mixed<1, 1, 1, 1><<<grid, kMixWarps * 32, 0, st>>>(g, b, s, gc, ctl); break;
+    case 0: k_collide_stream_mixed<WARPS, 0, 0, 0, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 1: k_collide_stream_mixed<WARPS, 0, 0, 0, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 2: k_collide_stream_mixed<WARPS, 0, 0, 1, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 3: k_collide_stream_mixed<WARPS, 0, 0, 1, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 4: k_collide_stream_mixed<WARPS, 0, 1, 0, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 5: k_collide_stream_mixed<WARPS, 0, 1, 0, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 6: k_collide_stream_mixed<WARPS, 0, 1, 1, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 7: k_collide_stream_mixed<WARPS, 0, 1, 1, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 8: k_collide_stream_mixed<WARPS, 1, 1, 0, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 9: k_collide_stream_mixed<WARPS, 1, 1, 0, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    case 10: k_collide_stream_mixed<WARPS, 1, 1, 1, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+    default: k_collide_stream_mixed<WARPS, 1, 1, 1, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
   }
 }
 
-void launch_end_step_mixed(const Geom& g, Ctl* ctl, cudaStream_t st) { k_end_step_mixed<<<1, 1, 0, st>>>(g, ctl); }
+void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st) {
+  if (mb.warps == 2)
+    launch_collide_w<2>(mb, b, s, ctl, moments, st);
+  else
+    launch_collide_w<4>(mb, b, s, ctl, moments, st);
+}
+
+void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st) { k_end_step_mixed<<<1, 256, 0, st>>>(mb, ctl); }
 
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
                            cudaStream_t st) {
   k_scatter_cursor<<<grid_for(n, 2), kThreads, 0, st>>>(n, key, offset, cursor, perm);
 }
 
-void launch_get_state_mixed(const Geom& g, MixBufs b, int cur, double* r, double* v, cudaStream_t st) {
-  k_get_state_mixed<<<grid_for(g.n), kThreads, 0, st>>>(g, b.rec[cur], r, v);
+void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, double* v, cudaStream_t st) {
+  k_get_state_mixed<<<grid_for(mb.n), kThreads, 0, st>>>(mb, b.rec[cur], r, v);
 }
 
-void launch_set_state_mixed(const Geom& g, MixBufs b, const double* r, const double* v, cudaStream_t st) {
-  k_set_state_mixed<<<grid_for(g.n), kThreads, 0, st>>>(g, b, r, v);
+void launch_set_state_mixed(const MixBatch& mb, MixBufs b, const double* r, const double* v, cudaStream_t st) {
+  k_set_state_mixed<<<grid_for(mb.n), kThreads, 0, st>>>(mb, b, r, v);
 }
 
 }  // namespace mpcd

@@ -118,15 +118,47 @@ void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
 void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st);
 
-// ---- mixed form (kernels_mixed.cu) ----
-int mixed_cap(double ppc, int* cells_per_warp);  // staged records per warp; cells per warp group
-void launch_init_mixed(const Geom& g, MixBufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
-void launch_bin_mixed(const Geom& g, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st);
-void launch_collide_stream_mixed(const Geom& g, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st);
-void launch_end_step_mixed(const Geom& g, Ctl* ctl, cudaStream_t st);
+// ---- mixed form (kernels_mixed.cu); one box or an ensemble of independent boxes ----
+// A group of consecutive cells of one box, handled by one warp.
+struct MixGroup {
+  int64_t c0;      // first cell (global key)
+  int32_t box;
+  int32_t ncells;  // at most 32
+};
+
+// Grid shifts of one box (each box draws its own from its seed).
+struct BoxShift {
+  double s[3];       // step t + 1
+  double s_next[3];  // step t + 2
+  double s_last[3];  // step t
+  float sf[3];       // step t + 1, cell units
+  float sf_next[3];  // step t + 2, cell units
+};
+
+// Device tables of the mixed form.  Box b owns particles [pbase[b], pbase[b+1]) and cells
+// [boxes[b].cbase, boxes[b].cbase + boxes[b].ncell) of the concatenated arrays.
+struct MixBatch {
+  const Geom* boxes;
+  BoxShift* shifts;
+  const MixGroup* groups;
+  const int64_t* pbase;
+  int32_t nbox;
+  int32_t ngroups;
+  int64_t n;      // particles of all boxes
+  int64_t ncell;  // cells of all boxes
+  int32_t walls, force, thermostat, warps;  // uniform over boxes; warps per collide block
+};
+
+constexpr int kMixCap = 256;  // records one warp stages in shared memory
+int mixed_cells_per_group(double ppc, int target);  // cells per warp group for ~target records
+void mixed_box_shifts(const Geom& g, int64_t t, BoxShift* out);  // host: shifts of steps t+1, t+2
+void launch_init_mixed_box(const Geom& g, MixBufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
+void launch_bin_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st);
+void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st);
+void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st);
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
                            cudaStream_t st);
-void launch_get_state_mixed(const Geom& g, MixBufs b, int cur, double* r, double* v, cudaStream_t st);
-void launch_set_state_mixed(const Geom& g, MixBufs b, const double* r, const double* v, cudaStream_t st);
+void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, double* v, cudaStream_t st);
+void launch_set_state_mixed(const MixBatch& mb, MixBufs b, const double* r, const double* v, cudaStream_t st);
 
 }  // namespace mpcd

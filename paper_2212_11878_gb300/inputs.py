@@ -155,3 +155,21 @@ def batch_recipe(nbox: int = 256, meta_seed: int = BASE_SEED, side_choices=(8, 1
         rec.dt.append(float(rng.choice(dt_choices)))
         rec.seeds.append(int(meta_seed * 1000 + b))
     return rec
+
+
+# Ensembles: many independent periodic boxes advanced together (mixed form).
+BATCH_WORKLOADS = {
+    "batched_256": dict(nbox=256, meta_seed=BASE_SEED, side_choices=(8, 12, 16, 24, 32, 48, 64), ppc_range=(5, 20),
+                        alpha_range=(60.0, 150.0), dt_choices=(0.05, 0.1, 0.2), steps=1000,
+                        notes="256 uneven boxes, sides 8-64, 5-20 particles per cell, alpha 60-150 deg"),
+    "batched_32": dict(nbox=32, meta_seed=BASE_SEED + 7, side_choices=(8, 12, 16, 24), ppc_range=(5, 20),
+                       alpha_range=(60.0, 150.0), dt_choices=(0.05, 0.1, 0.2), steps=100,
+                       notes="small ensemble for tests and profiling"),
+}
+
+
+def batch_workload(name: str) -> BatchRecipe:
+    w = dict(BATCH_WORKLOADS[name])
+    for k in ("steps", "notes"):
+        w.pop(k)
+    return batch_recipe(**w)

@@ -52,6 +52,33 @@ def test_params_layout_matches_c(tmp_path):
                    P.reserved.offset]
 
 
+def test_tuning_layout_matches_c(tmp_path):
+    prog = tmp_path / "t.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpcd.h"\n'
+                    'int main(void){printf("%zu %zu %zu\\n", sizeof(mpcd_tuning), offsetof(mpcd_tuning, resort_k),'
+                    ' offsetof(mpcd_tuning, reserved)); return 0;}\n')
+    exe = tmp_path / "t"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    T = abi.Tuning
+    assert got == [__import__("ctypes").sizeof(T), T.resort_k.offset, T.reserved.offset]
+
+
+def test_ensemble_arguments_checked_on_host(libpath):
+    a = abi.make_params((4, 4, 4), precision="mixed")
+    b = abi.make_params((4, 4, 4), precision="fp64")
+    with pytest.raises(abi.MpcdError) as e:
+        abi.mpcd_batch_create([a, b])
+    assert e.value.code == abi.MPCD_ERR_ARG
+    c = abi.make_params((4, 4, 4), precision="mixed", thermostat=1)
+    with pytest.raises(abi.MpcdError):
+        abi.mpcd_batch_create([a, c])
+    bad = abi.make_params((0, 4, 4), precision="mixed")
+    with pytest.raises(abi.MpcdError) as e:
+        abi.mpcd_batch_create([a, bad])
+    assert "box 1" in str(e.value)
+
+
 def test_version_string(libpath):
     assert "sm_103a" in abi.mpcd_version()
 

@@ -1,0 +1,115 @@
+"""GPU checks of the ensemble form (many independent boxes per launch sequence) and of the
+autotuner.
+
+An ensemble runs one counting sort over the concatenated cell keys of all boxes; each box
+keeps its own parameters and random streams.  Because the per-cell sums are exact
+(order-independent), every box of an ensemble must reproduce the same box advanced alone
+bit for bit, and no tuning choice may change any result.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2212_11878_gb300 import abi, inputs
+
+pytestmark = pytest.mark.gpu
+
+BOXES = [
+    dict(L=(8, 8, 8), ppc=10, alpha_deg=130, dt=0.1, seed=101),
+    dict(L=(12, 12, 12), ppc=5, alpha_deg=60, dt=0.2, seed=102),
+    dict(L=(16, 16, 16), ppc=20, alpha_deg=150, dt=0.05, seed=103),
+    dict(L=(8, 12, 6), ppc=7, alpha_deg=95, dt=0.1, seed=104),
+    dict(L=(4, 4, 4), ppc=13, alpha_deg=110, dt=0.1, seed=105),
+]
+
+
+def box_params(kw):
+    return abi.make_params(precision="mixed", **kw)
+
+
+def test_each_box_equals_the_box_alone():
+    params = [box_params(k) for k in BOXES]
+    with abi.Box(batch=params) as ens:
+        assert abi.mpcd_num_boxes(ens.h) == len(BOXES)
+        pb, cb = abi.mpcd_box_offsets(ens.h)
+        assert pb[-1] == ens.n and cb[-1] == ens.ncell
+        ens.step(6)
+        r, v = ens.state()
+    for b, p in enumerate(params):
+        with abi.Box(p) as one:
+            assert one.n == pb[b + 1] - pb[b]
+            one.step(6)
+            r1, v1 = one.state()
+        assert np.array_equal(r[pb[b]:pb[b + 1]], r1), b
+        assert np.array_equal(v[pb[b]:pb[b + 1]], v1), b
+
+
+def test_ensemble_sort_and_conservation():
+    params = [box_params(k) for k in BOXES]
+    with abi.Box(batch=params) as ens:
+        pb, cb = abi.mpcd_box_offsets(ens.h)
+        r0, v0 = ens.state()
+        ens.step(1)
+        dbg = ens.debug_sort()
+        r, v = ens.state()
+    keys = np.empty(ens_n := len(dbg["keys"]), np.int64)
+    keys[dbg["ids"]] = dbg["keys"]
+    assert np.array_equal(dbg["counts"], np.bincount(dbg["keys"], minlength=cb[-1]))
+    assert np.array_equal(dbg["perm"], np.argsort(dbg["keys"], kind="stable"))
+    for b in range(len(BOXES)):
+        sl = slice(pb[b], pb[b + 1])
+        assert keys[sl].min() >= cb[b] and keys[sl].max() < cb[b + 1]       # particles stay in their box
+        box = np.array(BOXES[b]["L"], float)
+        assert np.all(r[sl] >= 0) and np.all(r[sl] < box)
+        P0, P1 = v0[sl].sum(axis=0), v[sl].sum(axis=0)
+        assert np.abs(P1 - P0).max() < 1e-4 * np.abs(v0[sl]).sum() / 3
+        E0, E1 = (v0[sl] ** 2).sum(), (v[sl] ** 2).sum()
+        assert abs(E1 / E0 - 1) < 1e-5
+
+
+def test_recipe_ensemble_runs():
+    rec = inputs.batch_recipe(nbox=24, side_choices=(8, 12, 16))
+    params = [abi.make_params((s, s, s), ppc=ppc, alpha_deg=al, dt=dt, seed=sd, precision="mixed")
+              for s, ppc, al, dt, sd in zip(rec.sides, rec.ppc, rec.alpha_deg, rec.dt, rec.seeds)]
+    with abi.Box(batch=params) as ens:
+        assert ens.n == rec.n_particles and ens.ncell == rec.cells
+        ens.step(20)
+        r, v = ens.state()
+    assert np.isfinite(v).all()
+    assert abs(np.mean(v ** 2) - 1.0) < 0.02
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_autotune_keeps_state_and_results(precision):
+    p = abi.make_params((24, 24, 24), precision=precision, seed=7, resort_k=10)
+    with abi.Box(p) as a, abi.Box(p) as b:
+        a.step(3)
+        b.step(3)
+        before = a.state()
+        best, ms = abi.mpcd_autotune(a.h, trial_steps=2)
+        assert ms > 0
+        after = a.state()
+        assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+        assert abi.mpcd_steps_done(a.h) == 3
+        assert abi.mpcd_get_tuning(a.h).as_dict() == best.as_dict()
+        a.step(4)
+        b.step(4)
+        ra, va = a.state()
+        rb, vb = b.state()
+    assert np.array_equal(ra, rb) and np.array_equal(va, vb)
+
+
+def test_tunings_give_identical_results():
+    p = abi.make_params((20, 20, 20), precision="mixed", seed=9)
+    outs = []
+    for tg, w in [(96, 2), (224, 4), (160, 2)]:
+        with abi.Box(p) as box:
+            abi.mpcd_set_tuning(box.h, group_target=tg, warps=w)
+            box.step(5)
+            outs.append(box.state())
+    for o in outs[1:]:
+        assert np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1])
+    with abi.Box(p) as box:
+        with pytest.raises(abi.MpcdError):
+            abi.mpcd_set_tuning(box.h, warps=3)
