@@ -451,6 +451,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->stream = h->own_stream;
   const int64_t n = h->n, C = h->ncell;
   if (h->precision == MPCD_MIXED) {
+    if ((e = prepare_collide_mixed()) != cudaSuccess) return bail(cuda_fail(h, e, "collide kernel setup"));
     h->per_step[kSlotStreamBin] = 0;  // binning is fused into the collide kernel
     h->per_step[kSlotZero] = 2;
     h->per_step[kSlotCollide] = 1;

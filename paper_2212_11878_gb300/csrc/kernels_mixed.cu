@@ -23,6 +23,8 @@
 // does not depend on the order in which the atomics delivered a cell's members and is a
 // function of the state alone.  No FP64 arithmetic runs per particle or per cell (except
 // for the virtual particles of wall cells).
+#include <mutex>
+
 #include "cellmath.cuh"
 #include "device_common.cuh"
 #include "mpcd_internal.h"
@@ -70,11 +72,34 @@ __device__ __forceinline__ void carry(float& x, int& c, int L, bool periodic) {
   }
 }
 
+// carry() for a periodic coordinate c in [0, L) and x in [-1, 2) (a move of at most one
+// cell): the same result without a branch.
+__device__ __forceinline__ void carry_near(float& x, int& c, int L) {
+  // k = +1 for x in [1, 2), -1 for x in [-1, 0), 0 otherwise; x - k is exact for k = +1 and
+  // rounds like x + 1 for k = -1 (both as in carry()); all selects, no branches
+  const int up = x >= 1.0f, dn = x < 0.0f;
+  const float y = __fsub_rn(x, up ? 1.0f : (dn ? -1.0f : 0.0f));
+  const int onto = y >= 1.0f;  // a value just below an integer rounded onto it
+  x = onto ? 0.0f : y;
+  c += up - dn + onto;
+  c += (c < 0) ? L : 0;
+  c -= (c >= L) ? L : 0;
+}
+
+__device__ __forceinline__ void carry_periodic(float& x, int& c, int L) {
+  if (x >= -1.0f && x < 2.0f)
+    carry_near(x, c, L);
+  else
+    carry(x, c, L, true);
+}
+
 // Ballistic move over dt in cell units (v in length/time), with the body force and, when
 // WALLS, bounce-back at z = 0 and z = Lz (velocity reversed at the crossing time).
-template <int WALLS, int FORCE>
+// NEAR: the caller has checked (moves_near) that no coordinate moves by a cell or more, so
+// the carry needs no test; the result is the same as without NEAR.
+template <int WALLS, int FORCE, int NEAR = 0>
 __device__ __forceinline__ void stream_mixed(const Geom& g, float f[3], int cc[3], float v[3]) {
-  if (!WALLS) {
+  if (!WALLS && NEAR) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (FORCE) {
@@ -83,7 +108,28 @@ __device__ __forceinline__ void stream_mixed(const Geom& g, float f[3], int cc[3
       } else {
         f[d] = fmaf(v[d], g.dta, f[d]);
       }
-      carry(f[d], cc[d], g.L[d], true);
+      carry_near(f[d], cc[d], g.L[d]);
+    }
+    return;
+  }
+  if (!WALLS) {
+    bool near = true;  // every coordinate moved by at most one cell
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (FORCE) {
+        f[d] = __fadd_rn(fmaf(v[d], g.dta, f[d]), g.ha[d]);
+        v[d] = __fadd_rn(v[d], g.gdt[d]);
+      } else {
+        f[d] = fmaf(v[d], g.dta, f[d]);
+      }
+      near = near && f[d] >= -1.0f && f[d] < 2.0f;
+    }
+    if (near) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) carry_near(f[d], cc[d], g.L[d]);
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) carry(f[d], cc[d], g.L[d], true);
     }
     return;
   }
@@ -109,7 +155,7 @@ __device__ __forceinline__ void stream_mixed(const Geom& g, float f[3], int cc[3
       const float gt = g.g[d] != 0.0 ? static_cast<float>(g.g[d]) : 0.0f;
       f[d] = fmaf(fmaf(0.5f * gt, tau, v[d]), tau * inv_a, f[d]);
       v[d] = fmaf(gt, tau, v[d]);
-      carry(f[d], cc[d], g.L[d], true);
+      carry_periodic(f[d], cc[d], g.L[d]);
     }
     if (wall == 0) {
       f[2] = fmaf(vz_c, tau, f[2]);
@@ -153,9 +199,9 @@ __device__ __forceinline__ int mixed_key(const Geom& g, const float f[3], const 
       c = c < 0 ? 0 : (c > g.L[2] ? g.L[2] : c);
     } else {
       const float x = __fsub_rn(f[d], sf[d]);
-      c += (x < 0.0f) ? -1 : (x >= 1.0f ? 1 : 0);
-      if (c < 0) c += g.L[d];
-      else if (c >= g.L[d]) c -= g.L[d];
+      c += static_cast<int>(x >= 1.0f) - static_cast<int>(x < 0.0f);
+      c += (c < 0) ? g.L[d] : 0;
+      c -= (c >= g.L[d]) ? g.L[d] : 0;
     }
     k[d] = c;
   }
@@ -165,9 +211,9 @@ __device__ __forceinline__ int mixed_key(const Geom& g, const float f[3], const 
 // Axis and rotation in FP32 from the same Philox draw as the FP64 form.
 __device__ __forceinline__ void frame_f32(const Geom& g, int64_t t1, int64_t cell, float R[9]) {
   const u64x4 w = draw(g.seed, static_cast<uint64_t>(t1), static_cast<uint64_t>(cell), kTagAxis);
-  const float z = fmaf(2.0f, static_cast<float>(w.x >> 40) * 0x1.0p-24f, -1.0f);
+  const float z = fmaf(2.0f, static_cast<float>(static_cast<uint32_t>(w.x >> 40)) * 0x1.0p-24f, -1.0f);
   float sp, cp;
-  sincospif(2.0f * (static_cast<float>(w.y >> 40) * 0x1.0p-24f), &sp, &cp);
+  sincospif(2.0f * (static_cast<float>(static_cast<uint32_t>(w.y >> 40)) * 0x1.0p-24f), &sp, &cp);
   const float rho = sqrtf((1.0f - z) * (1.0f + z));
   const float n0 = rho * cp, n1 = rho * sp, n2 = z;
   const float c = g.cos_af, s = g.sin_af, om = 1.0f - g.cos_af;
@@ -188,22 +234,64 @@ __device__ __forceinline__ void frame_f32(const Geom& g, int64_t t1, int64_t cel
 // r_t; their velocity slots receive the collided velocity.
 
 
-// Exact sum of FP32 values in fixed point with F fractional bits: x * 2^F (an exact FP32
-// product) is truncated to an int64 and added (exact when x's ulp is at least 2^-F).
-// Returns false, leaving the sum unchanged, if |x| >= 2^LIM.  Integer addition is
-// associative, so the total does not depend on the order of the terms.
-template <int F, int LIM>
-__device__ __forceinline__ bool fxf_add(long long& a, float x) {
-  if (!(fabsf(x) < static_cast<float>(1ull << (LIM + 24)) * 0x1.0p-24f)) return false;  // also rejects NaN
-  a += __float2ll_rz(x * static_cast<float>(1ull << (F > 62 ? 62 : F)) *
-                     (F > 62 ? static_cast<float>(1ull << (F - 62)) : 1.0f));
-  return true;
+// Exact sums of FP32 values on the fixed-point grid 2^-F.  A value is split into two int32
+// parts, x = (h 2^23 + lo) 2^-F to the nearest grid point: h = x 2^(F-23) rounded to an
+// integer and lo the remainder in units of 2^-F.  Both come from FP32 fused multiply-adds
+// whose result lands on the integer grid of the constant 1.5 * 2^23 (|h| <= 2^21, |lo| <=
+// 2^22), so the split costs a few FMA-pipe instructions (GB300's 64-bit conversions share its
+// narrow FP64 pipe).  Returns false, with both parts 0, for |x| >= 2^(44-F) or a non-finite
+// x.  Integer sums of the parts do not depend on the order of the terms; the sums of up to
+// 256 terms fit in int32.
+template <int F>
+__device__ __forceinline__ bool fix_split(float x, int& h, int& lo) {
+  static_assert(F >= 23 && F <= 44, "grid");
+  constexpr float kScale = static_cast<float>(1ull << (F - 23));
+  constexpr float kLimit = static_cast<float>(1ull << (44 - F));
+  constexpr float kRound = 12582912.0f;  // 1.5 * 2^23
+  const bool ok = fabsf(x) < kLimit;
+  const float t = fmaf(x, kScale, kRound);
+  const float rem = fmaf(x, kScale, -__fsub_rn(t, kRound));  // exact: x 2^(F-23) - h
+  const float t2 = fmaf(rem, 8388608.0f, kRound);
+  h = ok ? __float_as_int(t) - 0x4B400000 : 0;
+  lo = ok ? __float_as_int(t2) - 0x4B400000 : 0;
+  return ok;
 }
 
-// Velocities and squared lengths: 2^-36 grid, |x| < 2^14, up to 2^13 terms.
-__device__ __forceinline__ bool fx_v(long long& a, float x) { return fxf_add<36, 14>(a, x); }
-// Energy differences of order 1e-7: 2^-56 grid, |x| < 2^-2, up to 2^9 terms.
-__device__ __forceinline__ bool fx_de(long long& a, float x) { return fxf_add<56, -2>(a, x); }
+// The fixed-point value h 2^23 + lo of a split (or of sums of splits).
+__device__ __forceinline__ long long fix_join(int h, int lo) {
+  return static_cast<long long>(h) * 8388608LL + static_cast<long long>(lo);
+}
+
+// a += x on the grid 2^-F (int64 accumulator, for cells of any size).
+template <int F>
+__device__ __forceinline__ bool fx_add(long long& a, float x) {
+  int h, lo;
+  const bool ok = fix_split<F>(x, h, lo);
+  a += fix_join(h, lo);
+  return ok;
+}
+
+// Grids of the per-cell sums: velocities 2^-32 (|v| < 2^12), squared lengths 2^-30 (< 2^14),
+// energy differences 2^-44 (|x| < 1).
+constexpr int kFixV = 32, kFixV2 = 30, kFixDE = 44;
+
+// An int64 rounded to the nearest FP32 (ties to even), on the integer pipe; the same value
+// as __ll2float_rn.
+__device__ __forceinline__ float ll_to_float(long long s) {
+  const unsigned long long a = s < 0 ? 0ull - static_cast<unsigned long long>(s) : static_cast<unsigned long long>(s);
+  if (a == 0ull) return 0.0f;
+  const int lz = __clzll(static_cast<long long>(a));
+  const unsigned long long nrm = a << lz;                 // leading one at bit 63
+  unsigned mant = static_cast<unsigned>(nrm >> 40);      // 24 bits
+  const unsigned long long rem = nrm & 0xFFFFFFFFFFull;  // 40 bits below
+  if (rem > 0x8000000000ull || (rem == 0x8000000000ull && (mant & 1u))) ++mant;
+  unsigned ex = static_cast<unsigned>(63 - lz + 127);
+  if (mant == 0x1000000u) {
+    mant >>= 1;
+    ++ex;
+  }
+  return __uint_as_float((s < 0 ? 0x80000000u : 0u) | (ex << 23) | (mant & 0x7FFFFFu));
+}
 
 // Per-cell data the particle passes need.
 struct CellFrame {
@@ -214,18 +302,18 @@ struct CellFrame {
 };
 
 // The per-cell step before the rotation, from the exact momentum sums S (2^-36 fixed
-// point): centre-of-mass velocity (with the virtual particles of a cut wall cell), whether
-// the cell rotates, and its rotation.
+// point): centre-of-mass velocity (with the virtual particles of a cut wall cell) and
+// whether the cell rotates.  The rotation itself (frame_f32) needs no particle data.
 template <int WALLS>
-__device__ __forceinline__ void cell_prologue(const Geom& g, const long long S[3], int n, int64_t c, int64_t t1,
-                                              double shift_z, CellFrame& f) {
+__device__ __forceinline__ void cell_prologue_u(const Geom& g, const long long S[3], int n, int64_t c, int64_t t1,
+                                                double shift_z, CellFrame& f) {
   f.rot = 0;
   f.df = 0.0f;
   if (n == 0) return;
-  const float scale = 0x1.0p-36f / static_cast<float>(n);
-  f.u[0] = __ll2float_rn(S[0]) * scale;
-  f.u[1] = __ll2float_rn(S[1]) * scale;
-  f.u[2] = __ll2float_rn(S[2]) * scale;
+  const float scale = 0x1.0p-32f / static_cast<float>(n);
+  f.u[0] = ll_to_float(S[0]) * scale;
+  f.u[1] = ll_to_float(S[1]) * scale;
+  f.u[2] = ll_to_float(S[2]) * scale;
   bool virt = false;
   if (WALLS) {
     const int64_t layer = c / ((int64_t)g.L[0] * g.L[1]);
@@ -239,15 +327,20 @@ __device__ __forceinline__ void cell_prologue(const Geom& g, const long long S[3
       gauss_pair(w.z, w.w, g2, g3);
       const double sd = sqrt(Mv * g.kT);
       const double Mt = (double)n * m + Mv;
-      f.u[0] = static_cast<float>((m * __ll2double_rn(S[0]) * 0x1.0p-36 + sd * g0) / Mt);
-      f.u[1] = static_cast<float>((m * __ll2double_rn(S[1]) * 0x1.0p-36 + sd * g1) / Mt);
-      f.u[2] = static_cast<float>((m * __ll2double_rn(S[2]) * 0x1.0p-36 + sd * g2) / Mt);
+      f.u[0] = static_cast<float>((m * __ll2double_rn(S[0]) * 0x1.0p-32 + sd * g0) / Mt);
+      f.u[1] = static_cast<float>((m * __ll2double_rn(S[1]) * 0x1.0p-32 + sd * g1) / Mt);
+      f.u[2] = static_cast<float>((m * __ll2double_rn(S[2]) * 0x1.0p-32 + sd * g2) / Mt);
       virt = true;
     }
   }
-  if (n < 2 && !virt) return;
-  f.rot = 1;
-  frame_f32(g, t1, c, f.R);
+  f.rot = (n >= 2 || virt) ? 1 : 0;
+}
+
+template <int WALLS>
+__device__ __forceinline__ void cell_prologue(const Geom& g, const long long S[3], int n, int64_t c, int64_t t1,
+                                              double shift_z, CellFrame& f) {
+  cell_prologue_u<WALLS>(g, S, n, c, t1, shift_z, f);
+  if (f.rot) frame_f32(g, t1, c, f.R);
 }
 
 // w = R (v - u) for one particle, and |v - u|^2 - |w|^2.
@@ -269,25 +362,25 @@ __device__ __forceinline__ float sq3(const float w[3]) { return fmaf(w[0], w[0],
 // exactly; in FP32 the squared lengths drift by about 1e-7, so df = sum(|v-u|^2 - |w|^2) /
 // (2 sum |w|^2): the sum of the small differences is accurate on its own, and the cell's
 // relative kinetic energy is restored to FP32 rounding of the stored velocities.  With the
-// thermostat, df sets it to 3/2 (n - 1) kT instead.  dE: 2^-56 fixed point, Ea: 2^-36.
+// thermostat, df sets it to 3/2 (n - 1) kT instead.  dE: 2^-44 fixed point, Ea: 2^-30.
 template <int THERMO>
 __device__ __forceinline__ float cell_df(const Geom& g, int n, long long dE, long long Ea, bool ok) {
   if (!ok || Ea <= 0) return 0.0f;
-  const float ea = __ll2float_rn(Ea) * 0x1.0p-36f;
+  const float ea = ll_to_float(Ea) * 0x1.0p-30f;
   if (THERMO && n >= 2)
     return sqrtf(3.0f * static_cast<float>(n - 1) * static_cast<float>(g.kT) / (static_cast<float>(g.mass) * ea)) -
            1.0f;
-  return 0.5f * (__ll2float_rn(dE) * 0x1.0p-56f) / ea;
+  return 0.5f * (ll_to_float(dE) * 0x1.0p-44f) / ea;
 }
 
 __device__ __forceinline__ void write_moments_mixed(const Geom& g, double* moments, int64_t c, int n, const long long S[3],
                                                     long long E2) {
   double* mo = moments + 5 * c;
   mo[0] = static_cast<double>(n) * g.mass;
-  mo[1] = g.mass * __ll2double_rn(S[0]) * 0x1.0p-36;
-  mo[2] = g.mass * __ll2double_rn(S[1]) * 0x1.0p-36;
-  mo[3] = g.mass * __ll2double_rn(S[2]) * 0x1.0p-36;
-  mo[4] = 0.5 * g.mass * __ll2double_rn(E2) * 0x1.0p-36;
+  mo[1] = g.mass * __ll2double_rn(S[0]) * 0x1.0p-32;
+  mo[2] = g.mass * __ll2double_rn(S[1]) * 0x1.0p-32;
+  mo[3] = g.mass * __ll2double_rn(S[2]) * 0x1.0p-32;
+  mo[4] = 0.5 * g.mass * __ll2double_rn(E2) * 0x1.0p-30;
 }
 
 // Velocities of a cell's members: SoA arrays in shared memory (stride 1) or AoS records in
@@ -310,28 +403,15 @@ __device__ __forceinline__ bool cell_sums_mixed(const V3& v, int n, long long S[
   bool ok = n < 8192;
   for (int j = 0; j < n; ++j) {
     const float a = v.vx(j), b = v.vy(j), c = v.vz(j);
-    ok &= fx_v(S[0], a) & fx_v(S[1], b) & fx_v(S[2], c);
-    if (MOMENTS) ok &= fx_v(E2, fmaf(a, a, fmaf(b, b, __fmul_rn(c, c))));
+    ok &= fx_add<kFixV>(S[0], a) & fx_add<kFixV>(S[1], b) & fx_add<kFixV>(S[2], c);
+    if (MOMENTS) ok &= fx_add<kFixV2>(E2, fmaf(a, a, fmaf(b, b, __fmul_rn(c, c))));
   }
   return ok;
 }
 
-// Exact energy sums over a cell's rotated relative velocities w and their terms
-// |v - u|^2 - |w|^2, then the scale factor.
-template <int THERMO>
-__device__ __forceinline__ float cell_energy(const Geom& g, const V3& w, const float* term, int tstride, int n) {
-  long long dE = 0, Ea = 0;
-  bool oke = n < 512;
-  for (int j = 0; j < n; ++j) {
-    const float ww[3] = {w.vx(j), w.vy(j), w.vz(j)};
-    oke &= fx_de(dE, term[j * tstride]) & fx_v(Ea, sq3(ww));
-  }
-  return cell_df<THERMO>(g, n, dE, Ea, oke);
-}
-
 // The whole collision of one cell by one thread over AoS records rec[0..n-1] in global
-// memory (crowded cells).  Its energy sums are accumulated during the rotation instead of
-// from stored terms; being exact integer sums they equal the staged path's bit for bit.
+// memory (crowded cells).  Its sums accumulate the same fixed-point parts in int64, so they
+// equal the staged path's bit for bit.
 template <int WALLS, int THERMO, int MOMENTS>
 __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c, int64_t t1, double shift_z,
                                    double* moments) {
@@ -350,7 +430,7 @@ __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c,
     v.vx(j) = w[0];
     v.vy(j) = w[1];
     v.vz(j) = w[2];
-    oke &= fx_de(dE, term) & fx_v(Ea, sq3(w));
+    oke &= fx_add<kFixDE>(dE, term) & fx_add<kFixV2>(Ea, sq3(w));
   }
   const float df = cell_df<THERMO>(g, n, dE, Ea, oke);
   for (int j = 0; j < n; ++j) {
@@ -360,14 +440,24 @@ __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c,
   }
 }
 
+// True when streaming a particle with velocity v moves each in-cell offset f in [0, 1) by
+// less than 0.99 cells (with the body-force term): f + v dt / a then stays in (-1, 2) after
+// rounding, which is all that carry_near needs.
+template <int FORCE>
+__device__ __forceinline__ bool moves_near(const Geom& g, const MixRec& r) {
+  float m = fmaxf(fabsf(r.vx), fmaxf(fabsf(r.vy), fabsf(r.vz))) * g.dta;  // NaN: not near
+  if (FORCE) m += fmaxf(fabsf(g.ha[0]), fmaxf(fabsf(g.ha[1]), fabsf(g.ha[2])));
+  return m < 0.99f;
+}
+
 // Stream one record from r_{t-1} to r_t in place.
-template <int WALLS, int FORCE>
+template <int WALLS, int FORCE, int NEAR = 0>
 __device__ __forceinline__ void stream_record(const Geom& g, MixRec& r) {
   float f[3] = {r.ox, r.oy, r.oz};
   float v[3] = {r.vx, r.vy, r.vz};
   int cc[3];
   unpack_cell(g, r.cell, cc);
-  stream_mixed<WALLS, FORCE>(g, f, cc, v);
+  stream_mixed<WALLS, FORCE, NEAR>(g, f, cc, v);
   r.ox = f[0];
   r.oy = f[1];
   r.oz = f[2];
@@ -377,15 +467,29 @@ __device__ __forceinline__ void stream_record(const Geom& g, MixRec& r) {
   r.cell = pack_cell(g, cc);
 }
 
-// Key of a record's position after one more stream (the grid of the next step).
+// Out-of-line general forms, for the rare warps holding a particle that moves a cell or more
+// (records pass by value, so calling them stores nothing to memory).
 template <int WALLS, int FORCE>
+__device__ __noinline__ MixRec stream_record_general(const Geom* __restrict__ g, MixRec r) {
+  stream_record<WALLS, FORCE>(*g, r);
+  return r;
+}
+
+// Key of a record's position after one more stream (the grid of the next step).
+template <int WALLS, int FORCE, int NEAR = 0>
 __device__ __forceinline__ int next_key(const Geom& g, const MixRec& r, const float sf[3]) {
   float f[3] = {r.ox, r.oy, r.oz};
   float v[3] = {r.vx, r.vy, r.vz};
   int cc[3];
   unpack_cell(g, r.cell, cc);
-  stream_mixed<WALLS, FORCE>(g, f, cc, v);
+  stream_mixed<WALLS, FORCE, NEAR>(g, f, cc, v);
   return mixed_key<WALLS>(g, f, cc, sf);
+}
+
+template <int WALLS, int FORCE>
+__device__ __noinline__ int next_key_general(const Geom* __restrict__ g, MixRec r, float sf0, float sf1, float sf2) {
+  const float sf[3] = {sf0, sf1, sf2};
+  return next_key<WALLS, FORCE>(*g, r, sf);
 }
 
 __device__ __forceinline__ MixRec load_rec(const MixRec* __restrict__ p) {
@@ -435,175 +539,424 @@ __global__ void __launch_bounds__(kThreads) k_bin_mixed(MixBatch mb, MixBufs b, 
   }
 }
 
-// Shared-memory staging of one warp's records, structure of arrays: lanes that walk
-// different cells read different banks.
-struct MixStage {
-  float ox[kMixCap], oy[kMixCap], oz[kMixCap];
-  int32_t cell[kMixCap];
-  float vx[kMixCap], vy[kMixCap], vz[kMixCap];
-  int32_t id[kMixCap];
-  float term[kMixCap];  // |v-u|^2 - |w|^2 of each record
-  uint8_t seg[kMixCap]; // cell of each record within the group
-  float fr[14][32];     // per cell: u (3), R (9), df, rotate flag
+// ------------------------------------------------------------- collide + stream ----
+// Each warp runs a loop over groups of cells (groups w, w + W, w + 2W, ... for warp w of W).
+// Its records move HBM -> shared memory (cp.async, issued one group ahead) -> registers
+// (one record per lane and chunk of 32) -> HBM, so the gather of the next group is in flight
+// while the current group is computed.  Per-record work runs one lane per record; the
+// per-cell sums run one or two lanes per cell over the velocities in shared memory.
+constexpr int kPer = kMixCap / 32;  // records per lane
+
+template <int NQ>
+struct MixWarpStage {
+  MixRec rec[kMixCap];      // landing zone of the next group's records (as stored in HBM)
+  int2 q[NQ][kMixCap];      // fixed-point parts (h, lo) of each record's terms of the cell sums
+  alignas(16) float cf[32][16];  // per cell: u (3), df | R[0..3] | R[4..7] | R[8], rotate flag, 2 unused
+  uint8_t seg[kMixCap];     // cell of each record within the group
+  int32_t bad[2][32];       // per cell: a momentum / energy term outside its fixed-point range
 };
 
-__device__ __forceinline__ void stage_put(MixStage& st, int e, const MixRec& r) {
-  st.ox[e] = r.ox;
-  st.oy[e] = r.oy;
-  st.oz[e] = r.oz;
-  st.cell[e] = r.cell;
-  st.vx[e] = r.vx;
-  st.vy[e] = r.vy;
-  st.vz[e] = r.vz;
-  st.id[e] = r.id;
+// A group's cells and records; lo / n describe the cell that this lane works on in the
+// per-cell phases (lanes 2j and 2j + 1 share cell j when the group has at most 16 cells).
+struct Span {
+  int64_t c0;
+  int box, ncells, lsh;
+  int E0, E;  // first record (cell order), records
+  int lo, n;  // this lane's cell: first record relative to E0, members
+};
+
+__device__ __forceinline__ MixGroup group_desc(const MixBatch& mb, int64_t gi) {
+  if (gi < mb.ngroups) return mb.groups[gi];
+  MixGroup d;
+  d.c0 = 0;
+  d.box = 0;
+  d.ncells = 0;
+  return d;
 }
 
-__device__ __forceinline__ MixRec stage_get(const MixStage& st, int e) {
+__device__ __forceinline__ Span group_span(const int32_t* __restrict__ offset, const MixGroup& d, int lane) {
+  Span sp;
+  sp.c0 = d.c0;
+  sp.box = d.box;
+  sp.ncells = d.ncells;
+  sp.lsh = d.ncells <= 16 ? 1 : 0;
+  const int j = lane >> sp.lsh;
+  const int ja = j < d.ncells ? j : d.ncells;
+  const int jb = j < d.ncells ? j + 1 : d.ncells;
+  const int a = offset[d.c0 + ja], bnd = offset[d.c0 + jb];
+  sp.E0 = offset[d.c0];
+  sp.E = offset[d.c0 + d.ncells] - sp.E0;
+  sp.lo = a - sp.E0;
+  sp.n = bnd - a;
+  return sp;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(__cvta_generic_to_global(gmem)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// Start copying a group's records (slots pm) into the stage.
+template <typename Stage>
+__device__ __forceinline__ void gather_async(Stage& st, const MixRec* __restrict__ src, int E, const int pm[kPer],
+                                             int lane) {
+  if (E <= kMixCap) {
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int e = lane + 32 * i;
+      if (e < E) {
+        cp_async16(&st.rec[e], src + pm[i]);
+        cp_async16(reinterpret_cast<float4*>(&st.rec[e]) + 1, reinterpret_cast<const float4*>(src + pm[i]) + 1);
+      }
+    }
+  }
+  cp_async_commit();
+}
+
+__device__ __forceinline__ void load_perm(const int32_t* __restrict__ perm, const Span& sp, int pm[kPer], int lane) {
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int e = lane + 32 * i;
+    pm[i] = (sp.E <= kMixCap && e < sp.E) ? perm[sp.E0 + e] : 0;
+  }
+}
+
+__device__ __forceinline__ MixRec lds_rec(const MixRec* p) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  const float4 a = q[0], b = q[1];
   MixRec r;
-  r.ox = st.ox[e];
-  r.oy = st.oy[e];
-  r.oz = st.oz[e];
-  r.cell = st.cell[e];
-  r.vx = st.vx[e];
-  r.vy = st.vy[e];
-  r.vz = st.vz[e];
-  r.id = st.id[e];
+  r.ox = a.x;
+  r.oy = a.y;
+  r.oz = a.z;
+  r.cell = __float_as_int(a.w);
+  r.vx = b.x;
+  r.vy = b.y;
+  r.vz = b.z;
+  r.id = __float_as_int(b.w);
   return r;
 }
 
-// One warp per group of cells of one box (the group table never straddles boxes).  The
-// per-cell random axis is keyed on the cell's index inside its box, so a box advanced in
-// an ensemble reproduces the same box advanced alone.
-template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
-__global__ void __launch_bounds__(WARPS * 32) k_collide_stream_mixed(MixBatch mb, MixBufs b, MixScratch s,
-                                                                    Ctl* __restrict__ ctl) {
-  __shared__ MixStage stage[WARPS];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t gi = (int64_t)blockIdx.x * WARPS + warp;
-  if (gi >= mb.ngroups) return;
-  const MixGroup grp = mb.groups[gi];
-  const Geom& g = mb.boxes[grp.box];
-  const BoxShift& sh = mb.shifts[grp.box];
-  const int64_t t1 = ctl->t + 1;
-  const int cur = ctl->cur, nxt = cur ^ 1;
-  const float sf[3] = {sh.sf_next[0], sh.sf_next[1], sh.sf_next[2]};  // grid of the next step
-  const double shz = sh.s[2];                                        // grid of this step
+__device__ __forceinline__ long long shfl_xor_ll(long long x, int m) {
+  return __shfl_xor_sync(0xffffffffu, x, m);
+}
+
+// A group too large for the stage: one lane per cell, records in place in the destination.
+// (Arguments are plain values and pointers so that calling it stores nothing to the stack.)
+template <int WALLS, int FORCE, int THERMO, int MOMENTS>
+__device__ __noinline__ void collide_group_direct(const Geom* __restrict__ gp, const BoxShift* __restrict__ shp,
+                                                  int64_t c0, int ncells, const int32_t* __restrict__ offset,
+                                                  const int32_t* __restrict__ perm, double* moments,
+                                                  const MixRec* __restrict__ src, MixRec* __restrict__ dst,
+                                                  int32_t* __restrict__ knext, int32_t* __restrict__ cnext, int64_t t1,
+                                                  int lane) {
+  if (lane >= ncells) return;
+  const Geom& g = *gp;
+  const float sf[3] = {shp->sf_next[0], shp->sf_next[1], shp->sf_next[2]};
   const int cbase = static_cast<int>(g.cbase);
-  const int64_t c0 = grp.c0;
-  const int64_t cend = c0 + grp.ncells;
   const int64_t c = c0 + lane;
-  const bool live = lane < grp.ncells;
-  const int64_t cl = c - cbase;  // cell index inside the box
-  const int E0 = s.offset[c0];
-  const int E1 = s.offset[cend];
-  const int E = E1 - E0;
-  const MixRec* __restrict__ src = b.rec[cur];
-  MixRec* __restrict__ dst = b.rec[nxt];
-  int32_t* __restrict__ knext = s.key[nxt];
-  int32_t* __restrict__ cnext = s.count[nxt];
-  if (E > kMixCap) {
-    // too many records to stage: one cell per lane, in place in the destination buffer
-    if (live) {
-      const int o = s.offset[c];
-      const int n = s.offset[c + 1] - o;
-      const int32_t* pm = s.perm + o;
-      for (int j = 0; j < n; ++j) {
-        MixRec r = load_rec(src + pm[j]);
-        stream_record<WALLS, FORCE>(g, r);
-        dst[o + j] = r;
+  const int o = offset[c];
+  const int n = offset[c + 1] - o;
+  const int32_t* pm = perm + o;
+  for (int j = 0; j < n; ++j) {
+    MixRec r = load_rec(src + pm[j]);
+    stream_record<WALLS, FORCE>(g, r);
+    dst[o + j] = r;
+  }
+  mixed_collide_cell<WALLS, THERMO, MOMENTS>(g, dst + o, n, c - cbase, t1, shp->s[2],
+                                             MOMENTS ? moments + 5 * (int64_t)cbase : nullptr);
+  for (int j = 0; j < n; ++j) {
+    const int k = cbase + next_key<WALLS, FORCE>(g, dst[o + j], sf);
+    knext[o + j] = k;
+    atomicAdd(&cnext[k], 1);
+  }
+}
+
+// Phase 1 of a staged group (lane = record): stream to r_t and split each velocity into the
+// fixed-point parts of the momentum sums.  Returns the lane's records with a term out of
+// range (bit i: chunk i).  All chunks run; records past the end repeat the last one and
+// store nothing.
+template <int WALLS, int FORCE, int NEAR, int MOMENTS, typename Stage>
+__device__ __forceinline__ unsigned stream_split(const Geom& g, const Geom* __restrict__ gp, MixRec (&r)[kPer],
+                                                 Stage& st, int E, int lane) {
+  constexpr int NQ = 3 + MOMENTS;
+  unsigned badm = 0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int e = lane + 32 * i;
+    {
+      const bool valid = e < E;
+      if (NEAR)
+        stream_record<WALLS, FORCE, 1>(g, r[i]);
+      else
+        r[i] = stream_record_general<WALLS, FORCE>(gp, r[i]);
+      int h0, l0, h1, l1, h2, l2;
+      bool o = fix_split<kFixV>(r[i].vx, h0, l0) & fix_split<kFixV>(r[i].vy, h1, l1) &
+               fix_split<kFixV>(r[i].vz, h2, l2);
+      if (valid) {
+        st.q[0][e] = make_int2(h0, l0);
+        st.q[1][e] = make_int2(h1, l1);
+        st.q[2][e] = make_int2(h2, l2);
       }
-      mixed_collide_cell<WALLS, THERMO, MOMENTS>(g, dst + o, n, cl, t1, shz, MOMENTS ? s.moments + 5 * cbase : nullptr);
-      for (int j = 0; j < n; ++j) {
-        const int k = cbase + next_key<WALLS, FORCE>(g, dst[o + j], sf);
-        knext[o + j] = k;
+      if (MOMENTS) {
+        const float v2 = fmaf(r[i].vx, r[i].vx, fmaf(r[i].vy, r[i].vy, __fmul_rn(r[i].vz, r[i].vz)));
+        o &= fix_split<kFixV2>(v2, h0, l0);
+        if (valid) st.q[NQ - 1][e] = make_int2(h0, l0);
+      }
+      if (valid && !o) badm |= 1u << i;
+    }
+  }
+  return badm;
+}
+
+// Phase 5 tail (lane = record): keys of the next step, counts, write-out in cell order.
+template <int WALLS, int FORCE, int NEAR>
+__device__ __forceinline__ void key_store(const Geom& g, const Geom* __restrict__ gp, const MixRec (&r)[kPer],
+                                          const float sf[3], int E,
+                                          MixRec* __restrict__ dst, int32_t* __restrict__ knext,
+                                          int32_t* __restrict__ cnext, int cbase, int lane) {
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int e = lane + 32 * i;
+    {
+      const int k = cbase + (NEAR ? next_key<WALLS, FORCE, 1>(g, r[i], sf)
+                                  : next_key_general<WALLS, FORCE>(gp, r[i], sf[0], sf[1], sf[2]));
+      if (e < E) {
+        store_rec(dst + e, r[i]);
+        knext[e] = k;
         atomicAdd(&cnext[k], 1);
       }
     }
-    return;
   }
-  MixStage& st = stage[warp];
-  const int o = live ? s.offset[c] : E1;
-  const int n = live ? s.offset[c + 1] - o : 0;
-  const int lo = o - E0;
-  // 1. gather (a batch of loads in flight per lane) and stream to r_t (lane = record); tag
-  //    each staged record with its cell (lane = cell)
-  constexpr int kBatch = 4;
-  for (int base = 0; base < E; base += 32 * kBatch) {
-    int slot[kBatch];
+}
+
+// The per-cell random axis is keyed on the cell's index inside its box, so a box advanced in
+// an ensemble reproduces the same box advanced alone; every per-cell sum is an exact integer,
+// so neither the grouping nor the lanes per cell change any result.
+template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
+__global__ void __launch_bounds__(WARPS * 32) k_collide_stream_mixed(MixBatch mb, MixBufs b, MixScratch s,
+                                                                    Ctl* __restrict__ ctl) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int NQ = 3 + MOMENTS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  MixWarpStage<NQ>& st = reinterpret_cast<MixWarpStage<NQ>*>(smem_raw)[warp];
+  const int64_t W = (int64_t)gridDim.x * WARPS;
+  int64_t gi = (int64_t)blockIdx.x * WARPS + warp;
+  if (gi >= mb.ngroups) return;
+  const int64_t t1 = ctl->t + 1;
+  const int cur = ctl->cur, nxt = cur ^ 1;
+  const MixRec* __restrict__ src = b.rec[cur];
+  MixRec* __restrict__ dst = b.rec[nxt];
+  const int32_t* __restrict__ perm = s.perm;
+  const int32_t* __restrict__ offset = s.offset;
+  int32_t* __restrict__ knext = s.key[nxt];
+  int32_t* __restrict__ cnext = s.count[nxt];
+
+  // prologue: the first group's records into the stage, the second group's slots into registers
+  Span sp = group_span(offset, group_desc(mb, gi), lane);
+  int pm[kPer];
+  load_perm(perm, sp, pm, lane);
+  gather_async(st, src, sp.E, pm, lane);
+  Span sp1 = group_span(offset, group_desc(mb, gi + W), lane);
+  load_perm(perm, sp1, pm, lane);
+  cp_async_wait_all();
+  __syncwarp();
+
+  for (;;) {
+    const bool staged = sp.E <= kMixCap && sp.E > 0;  // empty groups take the per-cell path
+    MixRec r[kPer];
+    if (staged) {
+      // every lane takes kPer records; those past the end of the group repeat the last one,
+      // so all chunks run without branches and only their stores are predicated
 #pragma unroll
-    for (int k = 0; k < kBatch; ++k) {
-      const int e = base + lane + 32 * k;
-      slot[k] = e < E ? s.perm[E0 + e] : 0;
-    }
-    MixRec rec[kBatch];
-#pragma unroll
-    for (int k = 0; k < kBatch; ++k) {
-      const int e = base + lane + 32 * k;
-      if (e < E) rec[k] = load_rec(src + slot[k]);
-    }
-#pragma unroll
-    for (int k = 0; k < kBatch; ++k) {
-      const int e = base + lane + 32 * k;
-      if (e < E) {
-        stream_record<WALLS, FORCE>(g, rec[k]);
-        stage_put(st, e, rec[k]);
+      for (int i = 0; i < kPer; ++i) {
+        const int e = lane + 32 * i;
+        r[i] = lds_rec(&st.rec[e < sp.E ? e : sp.E - 1]);
       }
     }
-  }
-  for (int j = 0; j < n; ++j) st.seg[lo + j] = static_cast<uint8_t>(lane);
-  __syncwarp();
-  // 2. per cell (lane = cell): exact momentum sums, centre-of-mass velocity, frame
-  if (live) {
-    const V3 v{st.vx + lo, st.vy + lo, st.vz + lo, 1};
-    long long S[3], E2;
-    const bool ok = cell_sums_mixed<MOMENTS>(v, n, S, E2);
-    if (MOMENTS) write_moments_mixed(g, s.moments, c, n, S, E2);
-    CellFrame f;
-    cell_prologue<WALLS>(g, S, n, cl, t1, shz, f);
+    __syncwarp();
+    gather_async(st, src, sp1.E, pm, lane);               // group k + 1: HBM -> stage
+    const MixGroup d2 = group_desc(mb, gi + 2 * W);       // group k + 2: descriptor
+    Span sp2;
+    if (!staged) {
+      collide_group_direct<WALLS, FORCE, THERMO, MOMENTS>(mb.boxes + sp.box, mb.shifts + sp.box, sp.c0, sp.ncells,
+                                                          offset, perm, s.moments, src, dst, knext, cnext, t1, lane);
+      sp2 = group_span(offset, d2, lane);
+      load_perm(perm, sp2, pm, lane);
+    } else {
+      const Geom* gbox = mb.boxes + sp.box;
+      const Geom g = *gbox;  // a private copy: stores below cannot alias it
+      const BoxShift& sh = mb.shifts[sp.box];
+      const float sf[3] = {sh.sf_next[0], sh.sf_next[1], sh.sf_next[2]};  // grid of the next step
+      const double shz = sh.s[2];                                        // grid of this step
+      const int cbase = static_cast<int>(g.cbase);
+      const int E = sp.E, E0 = sp.E0;
+      const int lsh = sp.lsh, j = lane >> lsh, p = lane & lsh, step = 1 + lsh;
+      const bool cl_live = j < sp.ncells;
+      const int lo = sp.lo, n = sp.n;
+      const int64_t cl = sp.c0 + j - cbase;  // cell index inside the box
+
+      // 1. stream to r_t and split the velocities into fixed-point parts (lane = record);
+      //    tag records with their cell and draw the rotation (lane = cell)
+      bool near = !WALLS;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) st.fr[k][lane] = f.u[k];
+      for (int i = 0; i < kPer; ++i)
+        near = near & moves_near<FORCE>(g, r[i]);
+      unsigned badm = __all_sync(0xffffffffu, near) ? stream_split<WALLS, FORCE, 1, MOMENTS>(g, gbox, r, st, E, lane)
+                                                     : stream_split<WALLS, FORCE, 0, MOMENTS>(g, gbox, r, st, E, lane);
+      for (int k = p; k < n; k += step) st.seg[lo + k] = static_cast<uint8_t>(j);
+      st.bad[0][j] = 0;
+      st.bad[1][j] = 0;
+      float R8 = 0.0f;  // kept for the per-cell record written after the sums
+      if (cl_live && p == 0 && n >= 1) {
+        float R[9];
+        frame_f32(g, t1, cl, R);
+        float4* q = reinterpret_cast<float4*>(st.cf[j]);
+        q[1] = make_float4(R[0], R[1], R[2], R[3]);
+        q[2] = make_float4(R[4], R[5], R[6], R[7]);
+        R8 = R[8];
+      }
+      sp2 = group_span(offset, d2, lane);  // group k + 2: record range
+      __syncwarp();
+      if (__any_sync(0xffffffffu, badm != 0u)) {  // rare: mark the cells of out-of-range terms
 #pragma unroll
-    for (int k = 0; k < 9; ++k) st.fr[3 + k][lane] = f.R[k];
-    st.fr[13][lane] = (f.rot && ok) ? 1.0f : 0.0f;
-  }
-  __syncwarp();
-  // 3. rotate (lane = record): w = R (v - u) and the energy term of each particle
-  for (int e = lane; e < E; e += 32) {
-    const int j = st.seg[e];
-    if (st.fr[13][j] != 0.0f) {
-      CellFrame f;
+        for (int i = 0; i < kPer; ++i)
+          if ((badm >> i) & 1u) st.bad[0][st.seg[lane + 32 * i]] = 1;
+        __syncwarp();
+      }
+      // 2. per cell: exact momentum sums, centre-of-mass velocity, whether the cell rotates
+      long long S[3], E2 = 0;
+      {
+        int hs[NQ], ls[NQ];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) f.u[k] = st.fr[k][j];
+        for (int c = 0; c < NQ; ++c) hs[c] = ls[c] = 0;
+        for (int k = p; k < n; k += step) {
 #pragma unroll
-      for (int k = 0; k < 9; ++k) f.R[k] = st.fr[3 + k][j];
-      float w[3] = {st.vx[e], st.vy[e], st.vz[e]};
-      st.term[e] = rotate_relative(f, w);
-      st.vx[e] = w[0];
-      st.vy[e] = w[1];
-      st.vz[e] = w[2];
+          for (int c = 0; c < NQ; ++c) {
+            const int2 v = st.q[c][lo + k];
+            hs[c] += v.x;
+            ls[c] += v.y;
+          }
+        }
+        if (lsh) {
+#pragma unroll
+          for (int c = 0; c < NQ; ++c) {
+            hs[c] += __shfl_xor_sync(0xffffffffu, hs[c], 1);
+            ls[c] += __shfl_xor_sync(0xffffffffu, ls[c], 1);
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) S[c] = fix_join(hs[c], ls[c]);
+        if (MOMENTS) E2 = fix_join(hs[NQ - 1], ls[NQ - 1]);
+      }
+      if (cl_live && p == 0) {
+        const bool ok = st.bad[0][j] == 0;
+        if (MOMENTS) write_moments_mixed(g, s.moments, sp.c0 + j, n, S, E2);
+        CellFrame f;
+        cell_prologue_u<WALLS>(g, S, n, cl, t1, shz, f);
+        float4* q = reinterpret_cast<float4*>(st.cf[j]);
+        q[0] = make_float4(f.u[0], f.u[1], f.u[2], 0.0f);
+        q[3] = make_float4(R8, (f.rot && ok) ? 1.0f : 0.0f, 0.0f, 0.0f);
+      }
+      __syncwarp();
+      // 3. rotate (lane = record): w = R (v - u), and the fixed-point parts of the energy terms
+      badm = 0;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int e = lane + 32 * i;
+        {
+          const bool valid = e < E;
+          const float4* q = reinterpret_cast<const float4*>(st.cf[st.seg[valid ? e : E - 1]]);
+          const float4 q0 = q[0], q1 = q[1], q2 = q[2], q3 = q[3];
+          const bool rot = q3.y != 0.0f;
+          CellFrame f;
+          f.u[0] = q0.x;
+          f.u[1] = q0.y;
+          f.u[2] = q0.z;
+          f.R[0] = q1.x;
+          f.R[1] = q1.y;
+          f.R[2] = q1.z;
+          f.R[3] = q1.w;
+          f.R[4] = q2.x;
+          f.R[5] = q2.y;
+          f.R[6] = q2.z;
+          f.R[7] = q2.w;
+          f.R[8] = q3.x;
+          float w[3] = {r[i].vx, r[i].vy, r[i].vz};
+          const float term = rotate_relative(f, w);
+          r[i].vx = rot ? w[0] : r[i].vx;
+          r[i].vy = rot ? w[1] : r[i].vy;
+          r[i].vz = rot ? w[2] : r[i].vz;
+          int h0, l0, h1, l1;
+          const bool o = fix_split<kFixDE>(term, h0, l0) & fix_split<kFixV2>(sq3(w), h1, l1);
+          if (valid && rot) {
+            st.q[0][e] = make_int2(h0, l0);
+            st.q[1][e] = make_int2(h1, l1);
+            if (!o) badm |= 1u << i;
+          }
+        }
+      }
+      load_perm(perm, sp2, pm, lane);  // group k + 2: slots
+      __syncwarp();
+      if (__any_sync(0xffffffffu, badm != 0u)) {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i)
+          if ((badm >> i) & 1u) st.bad[1][st.seg[lane + 32 * i]] = 1;
+        __syncwarp();
+      }
+      // 4. per cell: exact energy sums, scale factor
+      {
+        const bool rot = cl_live && st.cf[j][13] != 0.0f;
+        int hd = 0, ld = 0, ha = 0, la = 0;
+        if (rot)
+          for (int k = p; k < n; k += step) {
+            const int2 d = st.q[0][lo + k], a = st.q[1][lo + k];
+            hd += d.x;
+            ld += d.y;
+            ha += a.x;
+            la += a.y;
+          }
+        if (lsh) {
+          hd += __shfl_xor_sync(0xffffffffu, hd, 1);
+          ld += __shfl_xor_sync(0xffffffffu, ld, 1);
+          ha += __shfl_xor_sync(0xffffffffu, ha, 1);
+          la += __shfl_xor_sync(0xffffffffu, la, 1);
+        }
+        if (rot && p == 0)
+          st.cf[j][3] = cell_df<THERMO>(g, n, fix_join(hd, ld), fix_join(ha, la), st.bad[1][j] == 0);
+      }
+      __syncwarp();
+      // 5. new velocities; keys and counts of the next step; write-out in cell order
+      near = !WALLS;
+#pragma unroll
+      for (int i = 0; i < kPer; ++i) {
+        const int e = lane + 32 * i;
+        {
+          const float* cf = st.cf[st.seg[e < E ? e : E - 1]];
+          const float4 q0 = *reinterpret_cast<const float4*>(cf);
+          const bool rot = cf[13] != 0.0f;
+          const float df = q0.w;
+          const float nx = __fadd_rn(q0.x, fmaf(df, r[i].vx, r[i].vx));
+          const float ny = __fadd_rn(q0.y, fmaf(df, r[i].vy, r[i].vy));
+          const float nz = __fadd_rn(q0.z, fmaf(df, r[i].vz, r[i].vz));
+          r[i].vx = rot ? nx : r[i].vx;
+          r[i].vy = rot ? ny : r[i].vy;
+          r[i].vz = rot ? nz : r[i].vz;
+          near = near & moves_near<FORCE>(g, r[i]);
+        }
+      }
+      if (__all_sync(0xffffffffu, near))
+        key_store<WALLS, FORCE, 1>(g, gbox, r, sf, E, dst + E0, knext + E0, cnext, cbase, lane);
+      else
+        key_store<WALLS, FORCE, 0>(g, gbox, r, sf, E, dst + E0, knext + E0, cnext, cbase, lane);
     }
-  }
-  __syncwarp();
-  // 4. per cell: exact energy sums, scale factor
-  if (live && st.fr[13][lane] != 0.0f) {
-    const V3 w{st.vx + lo, st.vy + lo, st.vz + lo, 1};
-    st.fr[12][lane] = cell_energy<THERMO>(g, w, st.term + lo, 1, n);
-  }
-  __syncwarp();
-  // 5. new velocities, keys and counts of the next step, write-out in cell order
-  for (int e = lane; e < E; e += 32) {
-    MixRec r = stage_get(st, e);
-    const int j = st.seg[e];
-    if (st.fr[13][j] != 0.0f) {
-      const float df = st.fr[12][j];
-      r.vx = __fadd_rn(st.fr[0][j], fmaf(df, r.vx, r.vx));
-      r.vy = __fadd_rn(st.fr[1][j], fmaf(df, r.vy, r.vy));
-      r.vz = __fadd_rn(st.fr[2][j], fmaf(df, r.vz, r.vz));
-    }
-    const int k = cbase + next_key<WALLS, FORCE>(g, r, sf);
-    store_rec(dst + E0 + e, r);
-    knext[E0 + e] = k;
-    atomicAdd(&cnext[k], 1);
+    cp_async_wait_all();  // group k + 1 has landed
+    __syncwarp();
+    gi += W;
+    if (gi >= mb.ngroups) break;
+    sp = sp1;
+    sp1 = sp2;
   }
 }
 
@@ -798,32 +1151,79 @@ void launch_bin_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cud
     k_bin_mixed<0, 0><<<grid_for(mb.n), kThreads, 0, st>>>(mb, b, s, ctl);
 }
 
-template <int WARPS>
-void launch_collide_w(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st) {
-  const unsigned grid = static_cast<unsigned>((mb.ngroups + WARPS - 1) / WARPS);
-  if (grid == 0) return;
-  const int sel = (mb.walls ? 8 : (mb.force ? 4 : 0)) | (mb.thermostat ? 2 : 0) | (moments ? 1 : 0);
-  switch (sel) {
-    case 0: k_collide_stream_mixed<WARPS, 0, 0, 0, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 1: k_collide_stream_mixed<WARPS, 0, 0, 0, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 2: k_collide_stream_mixed<WARPS, 0, 0, 1, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 3: k_collide_stream_mixed<WARPS, 0, 0, 1, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 4: k_collide_stream_mixed<WARPS, 0, 1, 0, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 5: k_collide_stream_mixed<WARPS, 0, 1, 0, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 6: k_collide_stream_mixed<WARPS, 0, 1, 1, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 7: k_collide_stream_mixed<WARPS, 0, 1, 1, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 8: k_collide_stream_mixed<WARPS, 1, 1, 0, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 9: k_collide_stream_mixed<WARPS, 1, 1, 0, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    case 10: k_collide_stream_mixed<WARPS, 1, 1, 1, 0><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
-    default: k_collide_stream_mixed<WARPS, 1, 1, 1, 1><<<grid, WARPS * 32, 0, st>>>(mb, b, s, ctl); break;
+namespace {
+// prepare: raise the kernel's dynamic shared-memory limit on the current device and record
+// how many of its blocks are resident at once (the persistent grid); runs outside capture.
+template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
+cudaError_t launch_collide_t(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st, bool prepare) {
+  auto kern = k_collide_stream_mixed<WARPS, WALLS, FORCE, THERMO, MOMENTS>;
+  const int smem = WARPS * static_cast<int>(sizeof(MixWarpStage<3 + MOMENTS>));
+  static int resident = 0;
+  if (prepare) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) resident = per_sm * sms;
+    return e;
   }
+  int64_t grid = (mb.ngroups + WARPS - 1) / WARPS;
+  if (grid == 0) return cudaSuccess;
+  if (resident > 0 && grid > resident) grid = resident;
+  kern<<<static_cast<unsigned>(grid), WARPS * 32, smem, st>>>(mb, b, s, ctl);
+  return cudaSuccess;
+}
+
+template <int WARPS>
+cudaError_t launch_collide_w(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st,
+                             bool prepare, int sel_override = -1) {
+  const int sel = sel_override >= 0 ? sel_override
+                                    : (mb.walls ? 8 : (mb.force ? 4 : 0)) | (mb.thermostat ? 2 : 0) | (moments ? 1 : 0);
+  switch (sel) {
+    case 0: return launch_collide_t<WARPS, 0, 0, 0, 0>(mb, b, s, ctl, st, prepare);
+    case 1: return launch_collide_t<WARPS, 0, 0, 0, 1>(mb, b, s, ctl, st, prepare);
+    case 2: return launch_collide_t<WARPS, 0, 0, 1, 0>(mb, b, s, ctl, st, prepare);
+    case 3: return launch_collide_t<WARPS, 0, 0, 1, 1>(mb, b, s, ctl, st, prepare);
+    case 4: return launch_collide_t<WARPS, 0, 1, 0, 0>(mb, b, s, ctl, st, prepare);
+    case 5: return launch_collide_t<WARPS, 0, 1, 0, 1>(mb, b, s, ctl, st, prepare);
+    case 6: return launch_collide_t<WARPS, 0, 1, 1, 0>(mb, b, s, ctl, st, prepare);
+    case 7: return launch_collide_t<WARPS, 0, 1, 1, 1>(mb, b, s, ctl, st, prepare);
+    case 8: return launch_collide_t<WARPS, 1, 1, 0, 0>(mb, b, s, ctl, st, prepare);
+    case 9: return launch_collide_t<WARPS, 1, 1, 0, 1>(mb, b, s, ctl, st, prepare);
+    case 10: return launch_collide_t<WARPS, 1, 1, 1, 0>(mb, b, s, ctl, st, prepare);
+    default: return launch_collide_t<WARPS, 1, 1, 1, 1>(mb, b, s, ctl, st, prepare);
+  }
+}
+
+}  // namespace
+
+cudaError_t prepare_collide_mixed() {
+  static std::mutex mu;
+  static uint64_t done = 0;  // devices prepared (bit per ordinal < 64)
+  std::lock_guard<std::mutex> lock(mu);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+  if (done & bit) return cudaSuccess;
+  MixBatch mb{};
+  MixBufs b{};
+  MixScratch s{};
+  for (int sel = 0; sel < 12 && e == cudaSuccess; ++sel) {
+    e = launch_collide_w<2>(mb, b, s, nullptr, false, nullptr, true, sel);
+    if (e == cudaSuccess) e = launch_collide_w<4>(mb, b, s, nullptr, false, nullptr, true, sel);
+  }
+  if (e == cudaSuccess) done |= bit;
+  return e;
 }
 
 void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st) {
   if (mb.warps == 2)
-    launch_collide_w<2>(mb, b, s, ctl, moments, st);
+    (void)launch_collide_w<2>(mb, b, s, ctl, moments, st, false);
   else
-    launch_collide_w<4>(mb, b, s, ctl, moments, st);
+    (void)launch_collide_w<4>(mb, b, s, ctl, moments, st, false);
 }
 
 void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st) { k_end_step_mixed<<<1, 256, 0, st>>>(mb, ctl); }

@@ -154,6 +154,9 @@ int mixed_cells_per_group(double ppc, int target);  // cells per warp group for 
 void mixed_box_shifts(const Geom& g, int64_t t, BoxShift* out);  // host: shifts of steps t+1, t+2
 void launch_init_mixed_box(const Geom& g, MixBufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
 void launch_bin_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st);
+// Set up the collide kernels on the current device (shared-memory limit, persistent grid);
+// call once per device before the first launch, outside stream capture.
+cudaError_t prepare_collide_mixed();
 void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st);
 void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st);
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,

@@ -68,12 +68,23 @@ def test_init_matches_oracle_to_fp32(orc):
 
 
 @pytest.mark.parametrize("case", [dict(L=(12, 10, 8)), dict(L=(9, 9, 9), a=0.5, dt=0.2),
-                                  dict(L=(8, 8, 8), g=(0.01, 0.02, -0.01)), dict(L=(8, 7, 6), ppc=25)])
+                                  dict(L=(8, 8, 8), g=(0.01, 0.02, -0.01)), dict(L=(8, 7, 6), ppc=25),
+                                  dict(L=(10, 9, 8), fast=0.02), dict(L=(9, 8, 7), g=(0.02, 0.0, 0.01), fast=0.01)])
 def test_one_step_against_fp64_oracle(orc, case):
+    """`fast`: that fraction of the particles moves 0.6 to 3 cells in the step, so that the
+    warps holding them take the general carry path instead of the one-cell one."""
+    case = dict(case)
+    fast = case.pop("fast", 0.0)
     p = mixed_params(seed=5, **case)
     L = tuple(p.L)
     n = int(round(p.ppc * np.prod(L)))
-    r0, v0 = quantize(*inputs.uniform_gaussian_state(L, n, 21, a=p.a), L, p.a)
+    r0, v0 = inputs.uniform_gaussian_state(L, n, 21, a=p.a)
+    if fast:
+        rng = np.random.default_rng(77)
+        ids = rng.choice(n, max(1, int(fast * n)), replace=False)
+        speed = rng.uniform(0.6, 3.0, ids.size) * p.a / p.dt
+        v0[ids] *= (speed / np.linalg.norm(v0[ids], axis=1))[:, None]
+    r0, v0 = quantize(r0, v0, L, p.a)
     with abi.Box(p) as box:
         box.set_state(r0, v0, 4)
         box.step(1)
