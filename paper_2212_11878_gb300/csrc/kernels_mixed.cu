@@ -554,6 +554,8 @@ struct MixWarpStage {
   alignas(16) float cf[32][16];  // per cell: u (3), df | R[0..3] | R[4..7] | R[8], rotate flag, 2 unused
   uint8_t seg[kMixCap];     // cell of each record within the group
   int32_t bad[2][32];       // per cell: a momentum / energy term outside its fixed-point range
+  Geom box[2];              // the box of the current / next group (copied with its records)
+  BoxShift shift[2];
 };
 
 // A group's cells and records; lo / n describe the cell that this lane works on in the
@@ -598,10 +600,18 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Start copying a group's records (slots pm) into the stage.
+// Start copying a group's records (slots pm) and its box's constants into the stage.
 template <typename Stage>
 __device__ __forceinline__ void gather_async(Stage& st, const MixRec* __restrict__ src, int E, const int pm[kPer],
-                                             int lane) {
+                                             const MixBatch& mb, int box, int slot, int lane) {
+  static_assert(sizeof(Geom) % 16 == 0 && sizeof(BoxShift) % 16 == 0, "16-byte pieces");
+  constexpr int kGeomPieces = sizeof(Geom) / 16, kShiftPieces = sizeof(BoxShift) / 16;
+  static_assert(kGeomPieces + kShiftPieces <= 32, "one piece per lane");
+  if (lane < kGeomPieces)
+    cp_async16(reinterpret_cast<float4*>(&st.box[slot]) + lane, reinterpret_cast<const float4*>(mb.boxes + box) + lane);
+  else if (lane < kGeomPieces + kShiftPieces)
+    cp_async16(reinterpret_cast<float4*>(&st.shift[slot]) + (lane - kGeomPieces),
+               reinterpret_cast<const float4*>(mb.shifts + box) + (lane - kGeomPieces));
   if (E <= kMixCap) {
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
@@ -735,7 +745,7 @@ __device__ __forceinline__ void key_store(const Geom& g, const Geom* __restrict_
 // an ensemble reproduces the same box advanced alone; every per-cell sum is an exact integer,
 // so neither the grouping nor the lanes per cell change any result.
 template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
-__global__ void __launch_bounds__(WARPS * 32) k_collide_stream_mixed(MixBatch mb, MixBufs b, MixScratch s,
+__global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed(MixBatch mb, MixBufs b, MixScratch s,
                                                                     Ctl* __restrict__ ctl) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   constexpr int NQ = 3 + MOMENTS;
@@ -757,7 +767,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_collide_stream_mixed(MixBatch mb
   Span sp = group_span(offset, group_desc(mb, gi), lane);
   int pm[kPer];
   load_perm(perm, sp, pm, lane);
-  gather_async(st, src, sp.E, pm, lane);
+  int slot = 0;  // stage slot of the current group's box constants
+  gather_async(st, src, sp.E, pm, mb, sp.box, slot, lane);
   Span sp1 = group_span(offset, group_desc(mb, gi + W), lane);
   load_perm(perm, sp1, pm, lane);
   cp_async_wait_all();
@@ -776,7 +787,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_collide_stream_mixed(MixBatch mb
       }
     }
     __syncwarp();
-    gather_async(st, src, sp1.E, pm, lane);               // group k + 1: HBM -> stage
+    gather_async(st, src, sp1.E, pm, mb, sp1.box, slot ^ 1, lane);  // group k + 1: HBM -> stage
     const MixGroup d2 = group_desc(mb, gi + 2 * W);       // group k + 2: descriptor
     Span sp2;
     if (!staged) {
@@ -786,8 +797,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_collide_stream_mixed(MixBatch mb
       load_perm(perm, sp2, pm, lane);
     } else {
       const Geom* gbox = mb.boxes + sp.box;
-      const Geom g = *gbox;  // a private copy: stores below cannot alias it
-      const BoxShift& sh = mb.shifts[sp.box];
+      const Geom& g = st.box[slot];  // box constants in shared memory
+      const BoxShift& sh = st.shift[slot];
       const float sf[3] = {sh.sf_next[0], sh.sf_next[1], sh.sf_next[2]};  // grid of the next step
       const double shz = sh.s[2];                                        // grid of this step
       const int cbase = static_cast<int>(g.cbase);
@@ -955,23 +966,47 @@ __global__ void __launch_bounds__(WARPS * 32) k_collide_stream_mixed(MixBatch mb
     __syncwarp();
     gi += W;
     if (gi >= mb.ngroups) break;
+    slot ^= 1;
     sp = sp1;
     sp1 = sp2;
   }
 }
 
+// perm[offset[key] + rank] = slot, the rank from a per-cell cursor.  Neighbouring slots mostly
+// share a key, so each warp groups equal keys (match.any) and one lane per group takes the
+// group's ranks with a single atomic.  The order inside a cell is whatever the atomics give;
+// every per-cell sum downstream is exact, so it does not matter.  A warp takes 4 chunks of
+// 32 consecutive slots per iteration, so that four load-atomic-store chains are in flight.
 __global__ void __launch_bounds__(kThreads) k_scatter_cursor(int64_t n, const int32_t* __restrict__ key,
                                                              const int32_t* __restrict__ offset, int32_t* __restrict__ cursor,
                                                              int32_t* __restrict__ perm) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += 2 * stride) {
-    const int64_t j = i + stride;
-    const int k0 = key[i];
-    const int k1 = j < n ? key[j] : 0;
-    const int p0 = offset[k0] + atomicAdd(&cursor[k0], 1);
-    const int p1 = j < n ? offset[k1] + atomicAdd(&cursor[k1], 1) : 0;
-    perm[p0] = static_cast<int32_t>(i);
-    if (j < n) perm[p1] = static_cast<int32_t>(j);
+  constexpr int kChunks = 4;
+  const int lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kChunks); base < n;
+       base += warps * 32 * kChunks) {  // warp-uniform
+    int k[kChunks];
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+      const int64_t i = base + 32 * c + lane;
+      k[c] = i < n ? key[i] : -1 - lane;  // distinct sentinels: lanes past the end stay alone
+    }
+    unsigned peers[kChunks];
+    int rank[kChunks], first[kChunks];
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+      peers[c] = __match_any_sync(0xffffffffu, k[c]);
+      rank[c] = __popc(peers[c] & below);
+      first[c] = 0;
+      if (k[c] >= 0 && rank[c] == 0) first[c] = atomicAdd(&cursor[k[c]], __popc(peers[c]));
+    }
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+      const int start = __shfl_sync(0xffffffffu, first[c], __ffs(peers[c]) - 1);
+      const int64_t i = base + 32 * c + lane;
+      if (k[c] >= 0) perm[offset[k[c]] + start + rank[c]] = static_cast<int32_t>(i);
+    }
   }
 }
 
@@ -1230,7 +1265,7 @@ void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st) { k_en
 
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
                            cudaStream_t st) {
-  k_scatter_cursor<<<grid_for(n, 2), kThreads, 0, st>>>(n, key, offset, cursor, perm);
+  k_scatter_cursor<<<grid_for(n, 4), kThreads, 0, st>>>(n, key, offset, cursor, perm);
 }
 
 void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, double* v, cudaStream_t st) {

@@ -7,8 +7,9 @@
 
 namespace mpcd {
 
-// One box as the kernels see it.  All values derived on the host from mpcd_params.
-struct Geom {
+// One box as the kernels see it.  All values derived on the host from mpcd_params.  (16-byte
+// aligned so that kernels can copy it into shared memory in 16-byte pieces.)
+struct alignas(16) Geom {
   int32_t L[3];
   int32_t walls;       // bounce-back walls in z
   int32_t thermostat;  // cell-level rescale of the relative kinetic energy
