@@ -12,6 +12,10 @@ With N > 1 (launched by torch.distributed.run) every rank advances its own indep
 replica box (the single-box path has no exchange step); `value` is the sum over ranks of
 updates divided by the slowest rank's time.
 
+Beside an FP64 run the same process times the mixed-precision form (256^3 cells, 167,772,160
+particles) and the 256-box ensemble the same way and reports them under `forms`, each with
+its speedup over the FP64 run (--no-forms skips them).
+
 --impl reference times the FP64 CPU oracle (the plain statement the library is checked
 against) on the same workload on the host cores, on rank 0 only.
 """
@@ -41,10 +45,16 @@ FP64_BYTES = {
     "stream_bin": (48.0 + 24.0 + 8.0, 4.0),
     "scan": (0.0, 12.0),
     "scatter": (12.0, 4.0),
-    "collide": (4.0 + 4.0 + 24.0 + 24.0, 8.0),
+    "collide": (4.0 + 24.0, 8.0 + 128.0),   # cell_frame: v through perm, offsets, 16-double frame
+    "rotate": (24.0 + 24.0 + 4.0 + 8.0, 0.0),  # v read + written, key, frame gather (amortised)
     "end_step": (0.0, 0.0),
 }
-FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # collide on re-sort steps also moves r and the ids
+FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # rotate on re-sort steps also moves r and the ids
+# FP64 instructions (DFMA, DADD, DMUL) per launch, as (per particle, per cell): the FP64 form
+# is bound by GB300's FP64 pipe (2 instructions per clock per SM), not by HBM.
+FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 73.0), "rotate": (9.0, 0.0)}
+SMS, FP64_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
+FP64_PEAK_GOPS = SMS * FP64_PER_CLK * SM_MAX_MHZ / 1e3   # 629.3 G FP64 instructions/s
 ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step
 # mixed form: 32-byte records; collide_stream gathers through perm, writes in cell order and
 # writes the next step's keys and ranks
@@ -57,6 +67,11 @@ MIXED_BYTES = {
     "end_step": (0.0, 0.0),
 }
 ALGO_STEP_BYTES_MIXED = 64.0
+# DRAM bytes (read + write) per particle of a kernel from one ncu capture of the current build,
+# scaled to a launch by the particle count; a kernel changed since its capture has none.
+NCU_TRAFFIC = {("mixed", "collide"): (71.62, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)")}
+# timed beside an FP64 run: the mixed form at 256^3 and the 256-box ensemble
+FORMS = ("mixed_L256", "batched_256")
 
 
 def parse():
@@ -69,6 +84,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip timing the mixed and ensemble forms")
+    ap.add_argument("--form-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -177,17 +194,105 @@ class EnsembleWorkload:
         self.seed = rec.seeds[0] if rec.nbox else 0
 
 
+def open_box(abi, inputs, name, rank):
+    """The box (or ensemble) of a named workload; rank r draws its own seeds."""
+    ensemble = name in inputs.BATCH_WORKLOADS
+    w = EnsembleWorkload(name, inputs.batch_workload(name)) if ensemble else inputs.WORKLOADS[name]
+    if ensemble:
+        plist = abi.params_from_recipe(w.rec)
+        for q in plist:
+            q.seed = q.seed + 1000003 * rank
+        return w, plist[0], abi.Box(batch=plist), True
+    p = abi.params_from_workload(w, seed=w.seed + rank)
+    return w, p, abi.Box(p), False
+
+
+def timed_steps(abi, torch, dist, box, stream, steps, world, sampler=None):
+    """K steps bracketed by barrier + synchronize, timed with CUDA events on the launching
+    stream (per-kernel events inside); returns (max-over-ranks ms, launches, kernel times,
+    clocks)."""
+    h = box.h
+    abi.mpcd_timing(h, True)
+    l0 = abi.mpcd_launch_count(h)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    box.step(steps)
+    e1.record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    launches = abi.mpcd_launch_count(h) - l0
+    ktimes = abi.mpcd_timing_read(h)
+    abi.mpcd_timing(h, False)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, launches, ktimes, clocks
+
+
+def kernel_table(p, mixed, n, C, ktimes, steps):
+    """Per-kernel device time per step, share, algorithmic HBM bytes and GB/s, and for the
+    FP64 kernels their FP64 instruction rate."""
+    kernels = {}
+    total_kernel_ms = sum(v[0] for v in ktimes.values()) or 1.0
+    model = MIXED_BYTES if mixed else FP64_BYTES
+    for name, (kms, cnt) in ktimes.items():
+        per_p, per_c = model.get(name, (0.0, 0.0))
+        bytes_step = per_p * n + per_c * C
+        if name == "rotate" and p.resort_k > 0 and not mixed:
+            bytes_step += FP64_RESORT_EXTRA * n / p.resort_k
+        ms_step = kms / steps
+        k = {"ms_per_step": ms_step, "launches": cnt, "share": kms / total_kernel_ms,
+             "algo_bytes_per_step": bytes_step, "gbs": bytes_step / (ms_step / 1e3) / 1e9 if kms > 0 else None,
+             "launches_per_step": cnt / steps}
+        if not mixed and name in FP64_OPS:
+            ops = FP64_OPS[name][0] * n + FP64_OPS[name][1] * C
+            k["fp64_ops_per_step"] = ops
+            k["fp64_gops"] = ops / (ms_step / 1e3) / 1e9 if kms > 0 else None
+        kernels[name] = k
+    return kernels
+
+
+def roofline_of(kernels, mixed, hbm_peak, peak_src, n):
+    """The dominant kernel against its bound: HBM bytes (mixed form) or the FP64 pipe (FP64
+    form: measured traffic stays far below HBM; the FP64 instruction count sets the floor)."""
+    if mixed:
+        dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+        d = kernels[dom]
+        per_launch = d["algo_bytes_per_step"] / max(d["launches_per_step"], 1.0)
+        tr = NCU_TRAFFIC.get(("mixed", dom))
+        return {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": d["gbs"] / hbm_peak, "traffic": tr[0] * n if tr else None,
+                "traffic_source": tr[1] if tr else None, "peak_source": peak_src + " (hbm_gbs)",
+                "algo_bytes_per_launch": per_launch}
+    fp64k = [k for k in kernels if "fp64_gops" in kernels[k]]
+    dom = max(fp64k, key=lambda k: kernels[k]["ms_per_step"])
+    d = kernels[dom]
+    return {"kernel": dom, "bound": "alu", "achieved": d["fp64_gops"], "peak": FP64_PEAK_GOPS,
+            "unit": "G FP64 instructions/s", "frac": d["fp64_gops"] / FP64_PEAK_GOPS, "traffic": None,
+            "peak_source": "derived: %d SMs x %d FP64 instructions/clock x %.0f MHz" % (SMS, FP64_PER_CLK, SM_MAX_MHZ),
+            "algo_fp64_ops_per_launch": d["fp64_ops_per_step"] / max(d["launches_per_step"], 1.0),
+            "hbm_gbs": d["gbs"], "hbm_frac": d["gbs"] / hbm_peak}
+
+
 def main():
     args = parse()
     from paper_2212_11878_gb300 import inputs
     ensemble = args.workload in inputs.BATCH_WORKLOADS
-    w = (EnsembleWorkload(args.workload, inputs.batch_workload(args.workload)) if ensemble
-         else inputs.WORKLOADS[args.workload])
     if args.impl == "reference":
         if ensemble:
             print(json.dumps({"impl": "reference", "unavailable": "the CPU oracle times single-box workloads"}))
             return
-        run_reference(args, w)
+        run_reference(args, inputs.WORKLOADS[args.workload])
         return
 
     import torch
@@ -201,52 +306,26 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    hbm_peak = hbm_peak or 6800.0
+
     stream = torch.cuda.Stream()
-    if ensemble:
-        plist = abi.params_from_recipe(w.rec)
-        for q in plist:
-            q.seed = q.seed + 1000003 * rank
-        box = abi.Box(batch=plist)
-        p = plist[0]
-    else:
-        p = abi.params_from_workload(w, seed=w.seed + rank)
-        box = abi.Box(p)
+    w, p, box, ensemble = open_box(abi, inputs, args.workload, rank)
     h = box.h
     abi.mpcd_set_stream(h, stream.cuda_stream)
     n = box.n
+    mixed = p.precision == abi.MPCD_MIXED
 
     box.step(args.warmup)
     box.sync()
-
     props = torch.cuda.get_device_properties(local)
     bus = getattr(props, "pci_bus_id", None)
     sampler = ClockSampler(bus if isinstance(bus, str) else None)
-
-    abi.mpcd_timing(h, True)
-    l0 = abi.mpcd_launch_count(h)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    box.step(args.steps)
-    e1.record(stream)
-    stream.synchronize()
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    launches = abi.mpcd_launch_count(h) - l0
-    ktimes = abi.mpcd_timing_read(h)
-    abi.mpcd_timing(h, False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    total_updates = n * args.steps * world
-    value = total_updates / (ms / 1e3)
+    ms, launches, ktimes, clocks = timed_steps(abi, torch, dist, box, stream, args.steps, world, sampler)
+    value = n * args.steps * world / (ms / 1e3)
 
     # --- end to end through the host-buffer API: upload, one step, download ---
     r_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
@@ -267,46 +346,43 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_value = n * args.e2e_steps * world / e2e_s
+    C = box.ncell
+    kernels = kernel_table(p, mixed, n, C, ktimes, args.steps)
+    box.close()
+    del r_h, v_h
+
+    # --- the mixed-precision and ensemble forms, timed the same way, against this FP64 run ---
+    forms = {}
+    if not mixed and not args.no_forms:
+        for name in FORMS:
+            fw, fp, fbox, fens = open_box(abi, inputs, name, rank)
+            abi.mpcd_set_stream(fbox.h, stream.cuda_stream)
+            fbox.step(args.warmup)
+            fbox.sync()
+            fms, fl, fkt, _ = timed_steps(abi, torch, dist, fbox, stream, args.form_steps, world)
+            fn = fbox.n
+            fval = fn * args.form_steps * world / (fms / 1e3)
+            fk = kernel_table(fp, True, fn, fbox.ncell, fkt, args.form_steps)
+            forms[name] = {"value": fval, "unit": UNIT, "steps": args.form_steps, "ms_per_step": fms / args.form_steps,
+                           "particles": fn, "cells": fbox.ncell, "boxes": fw.rec.nbox if fens else 1,
+                           "speedup_vs_fp64": fval / value, "gpu_launches": fl,
+                           "hbm_roofline_frac_step": fval / world * ALGO_STEP_BYTES_MIXED / 1e9 / hbm_peak,
+                           "roofline": roofline_of(fk, True, hbm_peak, peak_src, fn),
+                           "kernels": {k: {"ms_per_step": v["ms_per_step"], "share": v["share"], "gbs": v["gbs"]}
+                                       for k, v in fk.items()}}
+            launches += fl
+            fbox.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not ensemble:
         cpu = cpu_oracle_run(w, args.cpu_steps, "cpu_baseline")
 
     if rank == 0:
-        import json as _json
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-        hbm_peak = peaks.get("hbm_gbs")
-        peak_src = "measured" if hbm_peak else "fallback"
-        hbm_peak = hbm_peak or 6800.0
-        C = box.ncell
-        kernels = {}
-        total_kernel_ms = sum(v[0] for v in ktimes.values())
-        mixed = p.precision == abi.MPCD_MIXED
-        model = MIXED_BYTES if mixed else FP64_BYTES
-        for name, (kms, cnt) in ktimes.items():
-            per_p, per_c = model.get(name, (0.0, 0.0))
-            # bytes per launch of this slot (a slot may hold several kernel launches)
-            slot_launches = cnt / args.steps
-            bytes_step = per_p * n + per_c * C
-            if name == "collide" and p.resort_k > 0 and not mixed:
-                bytes_step += FP64_RESORT_EXTRA * n / p.resort_k
-            kernels[name] = {"ms_per_step": kms / args.steps, "launches": cnt, "share": kms / total_kernel_ms,
-                             "algo_bytes_per_step": bytes_step,
-                             "gbs": bytes_step / (kms / args.steps / 1e3) / 1e9 if kms > 0 else None,
-                             "launches_per_step": slot_launches}
-        dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
-        d = kernels[dom]
-        achieved = d["gbs"]
-        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                    "algo_bytes_per_launch": d["algo_bytes_per_step"]}
         ms_step = ms / args.steps
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if p.precision == abi.MPCD_FP64 else "f32",
-            "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if mixed else "f64", "data": "synthetic",
             "config": {"workload": w.name, "L": list(w.L) if not ensemble else None,
                        "boxes": w.rec.nbox if ensemble else 1, "particles": n, "cells": C, "ppc": w.ppc,
                        "precision": w.precision, "resort_k": w.resort_k, "alpha_deg": w.alpha_deg, "dt": w.dt,
@@ -314,8 +390,9 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "hbm_roofline_frac_step": value / world * (ALGO_STEP_BYTES_MIXED if mixed else ALGO_STEP_BYTES_FP64) / 1e9
             / hbm_peak,
-            "roofline": roofline,
+            "roofline": roofline_of(kernels, mixed, hbm_peak, peak_src, n),
             "kernels": kernels,
+            "forms": forms or None,
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 48, "d2h_bytes_per_step": n * 48,
@@ -323,7 +400,6 @@ def main():
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))
-    box.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -19,10 +19,10 @@ using namespace mpcd;
 
 namespace {
 
-enum KernelSlot { kSlotZero = 0, kSlotStreamBin, kSlotScan, kSlotScatter, kSlotCollide, kSlotEndStep, kNumSlots };
-const char* kSlotNames[kNumSlots] = {"zero_counts", "stream_bin", "scan", "scatter", "collide", "end_step"};
+enum KernelSlot { kSlotZero = 0, kSlotStreamBin, kSlotScan, kSlotScatter, kSlotCollide, kSlotRotate, kSlotEndStep, kNumSlots };
+const char* kSlotNames[kNumSlots] = {"zero_counts", "stream_bin", "scan", "scatter", "collide", "rotate", "end_step"};
 // kernels launched per slot per step (collide: two for periodic boxes without thermostat)
-const int kSlotLaunchesBase[kNumSlots] = {1, 1, 3, 1, 1, 1};
+const int kSlotLaunchesBase[kNumSlots] = {1, 1, 3, 1, 1, 0, 1};
 
 std::mutex g_err_mu;
 std::string g_create_err;
@@ -271,6 +271,8 @@ int enqueue_step(mpcd_t* h, bool moments, int par = 0) {
   if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(s.count, s.offset, s.partial, g.ncell, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotScatter, [&] { launch_scatter(g, s, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotCollide, [&] { launch_collide_fp64(g, h->f64, s, h->ctl, moments, h->stream); }))) return rc;
+  if (fp64_dense_collide(g, s))
+    if ((rc = run_slot(h, kSlotRotate, [&] { launch_rotate_fp64(g, h->f64, s, h->ctl, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step(g, h->ctl, h->stream); }))) return rc;
   return MPCD_OK;
 }
@@ -436,7 +438,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->geom.n = ntot;
   h->geom.ncell = ctot;
   for (int k = 0; k < kNumSlots; ++k) h->per_step[k] = kSlotLaunchesBase[k];
-  if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotCollide] = 2;
+  if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotRotate] = 1;  // cell_frame + rotate
   h->n = ntot;
   h->ncell = ctot;
   auto bail = [&](int code) {
@@ -455,6 +457,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     h->per_step[kSlotStreamBin] = 0;  // binning is fused into the collide kernel
     h->per_step[kSlotZero] = 2;
     h->per_step[kSlotCollide] = 1;
+    h->per_step[kSlotRotate] = 0;
     for (int k = 0; k < 2; ++k) {
       if ((rc = dalloc(h, &h->mix.rec[k], n))) return bail(rc);
       if ((rc = dalloc(h, &h->mscr.key[k], n))) return bail(rc);

@@ -395,19 +395,35 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
   rec[6] = make_double2(1.0, 0.0);
 }
 
-__device__ __forceinline__ void rotate_slot(const Geom& g, const Fp64Bufs& b, const Scratch& s, int64_t i, int cur,
-                                            bool resort) {
+// One storage slot of k_rotate: its velocity and its cell's frame record, all loaded
+// before any of them is used (the frame whether or not the cell rotates: one round trip
+// after the key instead of two).
+struct RotSlot {
+  int64_t i;
+  double v[3];
+  double2 f[7];
+};
+
+__device__ __forceinline__ void rotate_load(const Fp64Bufs& b, const Scratch& s, int64_t i, int cur, RotSlot& q) {
+  q.i = i;
   const int c = s.key[i];
-  double v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
+  q.v[0] = b.v[cur][0][i];
+  q.v[1] = b.v[cur][1][i];
+  q.v[2] = b.v[cur][2][i];
   const double2* __restrict__ rec = reinterpret_cast<const double2*>(s.frame + kFrameStride * (int64_t)c);
-  const double2 f6 = rec[6];
-  const bool rot = f6.x != 0.0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) q.f[k] = rec[k];
+}
+
+__device__ __forceinline__ void rotate_finish(const Fp64Bufs& b, const Scratch& s, RotSlot& q, int cur, bool resort) {
+  const bool rot = q.f[6].x != 0.0;
+  double v0 = q.v[0], v1 = q.v[1], v2 = q.v[2];
   if (rot) {
-    const double2 f0 = rec[0], f1 = rec[1], f2 = rec[2], f3 = rec[3], f4 = rec[4], f5 = rec[5];
-    const double R[9] = {f0.x, f0.y, f1.x, f1.y, f2.x, f2.y, f3.x, f3.y, f4.x};
-    const double bv[3] = {f4.y, f5.x, f5.y};
+    const double R[9] = {q.f[0].x, q.f[0].y, q.f[1].x, q.f[1].y, q.f[2].x, q.f[2].y, q.f[3].x, q.f[3].y, q.f[4].x};
+    const double bv[3] = {q.f[4].y, q.f[5].x, q.f[5].y};
     apply_frame(R, bv, v0, v1, v2);
   }
+  const int64_t i = q.i;
   if (resort) {
     const int ob = cur ^ 1;
     const int dst = s.inv[i];
@@ -429,8 +445,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scra
   const int64_t t1 = ctl->t + 1;
   const int cur = ctl->cur;
   const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x)
-    rotate_slot(g, b, s, i, cur, resort);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+    RotSlot q;
+    rotate_load(b, s, i, cur, q);
+    rotate_finish(b, s, q, cur, resort);
+  }
 }
 
 // Put every cell's perm entries in storage order (the linked-cell list's order); run on
@@ -580,8 +599,10 @@ void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl,
   }
 }
 
+bool fp64_dense_collide(const Geom& g, const Scratch& s) { return !g.walls && !g.thermostat && s.frame && s.inv; }
+
 void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st) {
-  if (g.walls || g.thermostat || !s.frame || !s.inv) {
+  if (!fp64_dense_collide(g, s)) {
     launch_collide_fp64_generic(g, b, s, ctl, moments, st);
     return;
   }
@@ -590,6 +611,9 @@ void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool mo
     k_cell_frame<1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl);
   else
     k_cell_frame<0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl);
+}
+
+void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st) {
   k_rotate<<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl);
 }
 

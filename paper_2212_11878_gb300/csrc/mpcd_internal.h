@@ -109,9 +109,11 @@ void launch_scan(const int32_t* count, int32_t* offset, int32_t* partial, int64_
 void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
 void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
 void launch_scatter(const Geom& g, Scratch s, cudaStream_t st);
-// periodic boxes without thermostat: cell_frame + rotate (needs s.frame, s.rotflag);
-// otherwise one thread per cell
+// periodic boxes without thermostat (fp64_dense_collide): cell_frame here, then
+// launch_rotate_fp64; otherwise one thread per cell here and no rotate launch
+bool fp64_dense_collide(const Geom& g, const Scratch& s);
 void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st);
+void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
 // one thread per cell for every box kind (no frame buffer needed)
 void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st);
 void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st);

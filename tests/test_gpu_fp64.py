@@ -136,7 +136,7 @@ def test_graph_and_timed_paths_agree():
             outs.append(box.state())
             if timed:
                 t = abi.mpcd_timing_read(box.h)
-                assert t["collide"][1] == 14 and t["scan"][1] == 21   # cell_frame + rotate per step
+                assert t["collide"][1] == 7 and t["rotate"][1] == 7 and t["scan"][1] == 21
                 assert all(ms >= 0 for ms, _ in t.values())
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
