@@ -196,21 +196,22 @@ class EnsembleWorkload:
 
 def open_box(abi, inputs, name, rank):
     """The box (or ensemble) of a named workload; rank r draws its own seeds."""
+    from paper_2212_11878_gb300 import replicas
     ensemble = name in inputs.BATCH_WORKLOADS
     w = EnsembleWorkload(name, inputs.batch_workload(name)) if ensemble else inputs.WORKLOADS[name]
     if ensemble:
         plist = abi.params_from_recipe(w.rec)
         for q in plist:
-            q.seed = q.seed + 1000003 * rank
+            q.seed = replicas.ensemble_seed(q.seed, rank)
         return w, plist[0], abi.Box(batch=plist), True
-    p = abi.params_from_workload(w, seed=w.seed + rank)
+    p = abi.params_from_workload(w, seed=replicas.box_seed(w.seed, rank))
     return w, p, abi.Box(p), False
 
 
 def timed_steps(abi, torch, dist, box, stream, steps, world, sampler=None):
     """K steps bracketed by barrier + synchronize, timed with CUDA events on the launching
-    stream (per-kernel events inside); returns (max-over-ranks ms, launches, kernel times,
-    clocks)."""
+    stream (per-kernel events inside); returns (updates/s of all ranks over the slowest
+    rank's time, that time in ms, launches, kernel times, clocks)."""
     h = box.h
     abi.mpcd_timing(h, True)
     l0 = abi.mpcd_launch_count(h)
@@ -231,12 +232,11 @@ def timed_steps(abi, torch, dist, box, stream, steps, world, sampler=None):
     launches = abi.mpcd_launch_count(h) - l0
     ktimes = abi.mpcd_timing_read(h)
     abi.mpcd_timing(h, False)
+    from paper_2212_11878_gb300 import replicas
+    value, ms, _ = replicas.job_throughput(box.n * steps, ms, dist if world > 1 else None, device="cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    return ms, launches, ktimes, clocks
+    return value, ms, launches, ktimes, clocks
 
 
 def kernel_table(p, mixed, n, C, ktimes, steps):
@@ -324,8 +324,7 @@ def main():
     props = torch.cuda.get_device_properties(local)
     bus = getattr(props, "pci_bus_id", None)
     sampler = ClockSampler(bus if isinstance(bus, str) else None)
-    ms, launches, ktimes, clocks = timed_steps(abi, torch, dist, box, stream, args.steps, world, sampler)
-    value = n * args.steps * world / (ms / 1e3)
+    value, ms, launches, ktimes, clocks = timed_steps(abi, torch, dist, box, stream, args.steps, world, sampler)
 
     # --- end to end through the host-buffer API: upload, one step, download ---
     r_h = torch.empty((n, 3), dtype=torch.float64, pin_memory=True)
@@ -341,11 +340,8 @@ def main():
         abi.mpcd_step(h, 1)
         abi.mpcd_get_state(h, r_np, v_np)
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = n * args.e2e_steps * world / e2e_s
+    from paper_2212_11878_gb300 import replicas
+    e2e_value, _, _ = replicas.job_throughput(n * args.e2e_steps, e2e_s * 1e3, dist if world > 1 else None, device="cuda")
     C = box.ncell
     kernels = kernel_table(p, mixed, n, C, ktimes, args.steps)
     box.close()
@@ -359,9 +355,8 @@ def main():
             abi.mpcd_set_stream(fbox.h, stream.cuda_stream)
             fbox.step(args.warmup)
             fbox.sync()
-            fms, fl, fkt, _ = timed_steps(abi, torch, dist, fbox, stream, args.form_steps, world)
+            fval, fms, fl, fkt, _ = timed_steps(abi, torch, dist, fbox, stream, args.form_steps, world)
             fn = fbox.n
-            fval = fn * args.form_steps * world / (fms / 1e3)
             fk = kernel_table(fp, True, fn, fbox.ncell, fkt, args.form_steps)
             forms[name] = {"value": fval, "unit": UNIT, "steps": args.form_steps, "ms_per_step": fms / args.form_steps,
                            "particles": fn, "cells": fbox.ncell, "boxes": fw.rec.nbox if fens else 1,

@@ -208,13 +208,26 @@ __device__ __forceinline__ int mixed_key(const Geom& g, const float f[3], const 
   return k[0] + g.L[0] * (k[1] + g.L[1] * k[2]);
 }
 
-// Axis and rotation in FP32 from the same Philox draw as the FP64 form.
+// A 53-bit integer 0 <= m < 2^53 times 2^-53, rounded to FP32 from its two halves (no 64-bit
+// conversion, which would use the FP64 pipe).
+__device__ __forceinline__ float u53_f32(uint64_t m) {
+  const float hi = static_cast<float>(static_cast<uint32_t>(m >> 21));           // exact below 2^24, else RN
+  const float lo = static_cast<float>(static_cast<uint32_t>(m & 0x1FFFFFull));   // exact
+  return fmaf(hi, 0x1.0p-32f, lo * 0x1.0p-53f);
+}
+
+// Axis and rotation in FP32 from the same Philox draw as the FP64 form: U = U53(w0), the
+// axis z = 2U - 1 = U - (1 - U) and rho = sqrt(1 - z^2) = 2 sqrt(U (1 - U)), with U and
+// 1 - U each taken from the 53-bit integer, so that rho keeps full FP32 accuracy near the
+// poles (1 - z from a rounded z would lose it); phi = 2 pi U53(w1).
 __device__ __forceinline__ void frame_f32(const Geom& g, int64_t t1, int64_t cell, float R[9]) {
   const u64x4 w = draw(g.seed, static_cast<uint64_t>(t1), static_cast<uint64_t>(cell), kTagAxis);
-  const float z = fmaf(2.0f, static_cast<float>(static_cast<uint32_t>(w.x >> 40)) * 0x1.0p-24f, -1.0f);
+  const uint64_t mz = w.x >> 11;
+  const float U = u53_f32(mz), Uc = mz ? u53_f32((1ull << 53) - mz) : 1.0f;  // U in [0, 1), 1 - U in (0, 1]
+  const float z = __fsub_rn(U, Uc);
   float sp, cp;
-  sincospif(2.0f * (static_cast<float>(static_cast<uint32_t>(w.y >> 40)) * 0x1.0p-24f), &sp, &cp);
-  const float rho = sqrtf((1.0f - z) * (1.0f + z));
+  sincospif(2.0f * u53_f32(w.y >> 11), &sp, &cp);
+  const float rho = 2.0f * sqrtf(U * Uc);
   const float n0 = rho * cp, n1 = rho * sp, n2 = z;
   const float c = g.cos_af, s = g.sin_af, om = 1.0f - g.cos_af;
   const float wx = om * n0, wy = om * n1, wz = om * n2;
