@@ -412,7 +412,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   }
   h->precision = p[0].precision;
   h->nbox = nbox;
-  h->tune.group_target = 192;
+  h->tune.group_target = 144;
   h->tune.warps = 4;
   h->tune.resort_k = p[0].resort_k;
   // per-box geometry; the handle's geom describes the whole concatenation for the kernels
@@ -834,7 +834,7 @@ int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* bes
   std::vector<mpcd_tuning> cand;
   if (h->precision == MPCD_MIXED) {
     for (int w : {2, 4})
-      for (int tg : {96, 128, 160, 192, 224}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, 0});
+      for (int tg : {96, 112, 128, 144, 160}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, 0});
   } else {
     for (int k : {1, 2, 5, 10, 20, 50}) cand.push_back(mpcd_tuning{h->tune.group_target, h->tune.warps, k, 0});
   }

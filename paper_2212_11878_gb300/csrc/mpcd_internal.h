@@ -152,7 +152,7 @@ struct MixBatch {
   int32_t walls, force, thermostat, warps;  // uniform over boxes; warps per collide block
 };
 
-constexpr int kMixCap = 256;  // records one warp stages in shared memory
+constexpr int kMixCap = 192;  // records one warp stages (larger groups take the per-cell path)
 int mixed_cells_per_group(double ppc, int target);  // cells per warp group for ~target records
 void mixed_box_shifts(const Geom& g, int64_t t, BoxShift* out);  // host: shifts of steps t+1, t+2
 void launch_init_mixed_box(const Geom& g, MixBufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
