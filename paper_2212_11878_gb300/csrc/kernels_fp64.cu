@@ -108,9 +108,15 @@ __device__ __forceinline__ int move_and_key(const Geom& g, double r[3], double v
         r[d] = fma(v[d], g.dt, r[d]);
       }
     }
-    r[0] = wrap_box(r[0], g.B[0], __double_as_longlong(g.B[0]));
-    r[1] = wrap_box(r[1], g.B[1], __double_as_longlong(g.B[1]));
-    r[2] = wrap_box(r[2], g.B[2], __double_as_longlong(g.B[2]));
+    // all three in [0, B) (as unsigned bit patterns: negative values and -0.0 compare
+    // high) in one test; otherwise the per-coordinate wrap
+    const unsigned long long b0 = __double_as_longlong(g.B[0]), b1 = __double_as_longlong(g.B[1]),
+                             b2 = __double_as_longlong(g.B[2]);
+    if (!(dbits(r[0]) < b0 && dbits(r[1]) < b1 && dbits(r[2]) < b2)) {
+      r[0] = wrap_box(r[0], g.B[0], b0);
+      r[1] = wrap_box(r[1], g.B[1], b1);
+      r[2] = wrap_box(r[2], g.B[2], b2);
+    }
   }
   const int cx = cell_coord<POW2A>(r[0], sh[0], g, 0);
   const int cy = cell_coord<POW2A>(r[1], sh[1], g, 1);
@@ -416,7 +422,7 @@ __device__ __forceinline__ void rotate_load(const Fp64Bufs& b, const Scratch& s,
 }
 
 __device__ __forceinline__ void rotate_finish(const Fp64Bufs& b, const Scratch& s, RotSlot& q, int cur, bool resort) {
-  const bool rot = q.f[6].x != 0.0;
+  const bool rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1.0 or 0.0, tested as bits
   double v0 = q.v[0], v1 = q.v[1], v2 = q.v[2];
   if (rot) {
     const double R[9] = {q.f[0].x, q.f[0].y, q.f[1].x, q.f[1].y, q.f[2].x, q.f[2].y, q.f[3].x, q.f[3].y, q.f[4].x};
