@@ -270,7 +270,7 @@ __device__ __forceinline__ void write_moments(const Geom& g, Scratch& s, int64_t
 }
 
 // The whole collision of one cell by one thread (the shape of Listing 4): used for walls
-// and the thermostat, and by the dense kernel for groups of cells too large to stage.
+// and the thermostat, and by the allocation-free step.
 template <int WALLS, int THERMO, int MOMENTS>
 __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& s, int64_t c, int64_t t1, int cur,
                                      bool resort, double shift_z) {
