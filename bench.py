@@ -69,7 +69,8 @@ MIXED_BYTES = {
 ALGO_STEP_BYTES_MIXED = 64.0
 # DRAM bytes (read + write) per particle of a kernel from one ncu capture of the current build,
 # scaled to a launch by the particle count; a kernel changed since its capture has none.
-NCU_TRAFFIC = {("mixed", "collide"): (71.48, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)")}
+NCU_TRAFFIC = {("mixed", "collide"): (71.48, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)"),
+               ("fp64", "rotate"): (78.47, "profiles/fp64_L128_kernels_full.md (sorted regime, non-re-sort step)")}
 # timed beside an FP64 run: the mixed form at 256^3 and the 256-box ensemble
 FORMS = ("mixed_L256", "batched_256")
 
@@ -277,8 +278,10 @@ def roofline_of(kernels, mixed, hbm_peak, peak_src, n):
     fp64k = [k for k in kernels if "fp64_gops" in kernels[k]]
     dom = max(fp64k, key=lambda k: kernels[k]["ms_per_step"])
     d = kernels[dom]
+    tr = NCU_TRAFFIC.get(("fp64", dom))
     return {"kernel": dom, "bound": "alu", "achieved": d["fp64_gops"], "peak": FP64_PEAK_GOPS,
-            "unit": "G FP64 instructions/s", "frac": d["fp64_gops"] / FP64_PEAK_GOPS, "traffic": None,
+            "unit": "G FP64 instructions/s", "frac": d["fp64_gops"] / FP64_PEAK_GOPS,
+            "traffic": tr[0] * n if tr else None, "traffic_source": tr[1] if tr else None,
             "peak_source": "derived: %d SMs x %d FP64 instructions/clock x %.0f MHz" % (SMS, FP64_PER_CLK, SM_MAX_MHZ),
             "algo_fp64_ops_per_launch": d["fp64_ops_per_step"] / max(d["launches_per_step"], 1.0),
             "hbm_gbs": d["gbs"], "hbm_frac": d["gbs"] / hbm_peak}
