@@ -1,0 +1,71 @@
+"""The full channel-flow workload: 256x64x64 cells, walls in z, 20 particles per cell
+(20,971,520 particles), g = 1e-3 along x, thermostat, mixed form; 20,000 steps from rest,
+with the velocity profile averaged over steps 10,001-20,000 in 64 z-bins.
+
+Opt-in (about a minute on one GB300): set MPCD_LONG=1.  The profile comes from the per-cell
+moments of one step in fifty (each cut-cell layer's mean velocity, binned by the centre of
+its part of the channel), not from reading the particles back.
+
+Closed form: v_x(z) = g z (H - z) / (2 nu), with the SRD kinematic viscosity nu = nu_kin +
+nu_coll (mean-field formulas of Kikuchi et al. and Gompper et al.); for n = 20, alpha = 130
+deg, dt = 0.1: nu = 0.910, v_max = 0.563.  From rest, the slowest mode of the start-up
+decays as exp(-(pi/H)^2 nu t).  Averaged over t = 1000..2000 it leaves the centre about 4.7%
+below v_max, so the fitted viscosity is expected about 4.9% above nu.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2212_11878_gb300 import abi, inputs
+from test_gpu_mixed_accuracy import report
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not os.environ.get("MPCD_LONG"), reason="long run: set MPCD_LONG=1")]
+
+
+def test_poiseuille_full_channel():
+    w = inputs.WORKLOADS["poiseuille_256x64x64"]
+    p = abi.params_from_workload(w)
+    Lx, Ly, H = w.L
+    g, n_bar, dt, alpha = w.g[0], w.ppc, w.dt, math.radians(w.alpha_deg)
+    nu_kin = dt / 2 * (5 * n_bar / ((n_bar - 1 + math.exp(-n_bar)) * (2 - math.cos(alpha) - math.cos(2 * alpha))) - 1)
+    nu_col = (n_bar - 1 + math.exp(-n_bar)) / n_bar * (1 - math.cos(alpha)) / (18 * dt)
+    nu = nu_kin + nu_col
+    vmax = g * H * H / (8 * nu)
+    k = (math.pi / H) ** 2 * nu
+    t0, t1 = (w.steps // 2) * dt, w.steps * dt
+    deficit = 32 / math.pi ** 3 * (math.exp(-k * t0) - math.exp(-k * t1)) / (k * (t1 - t0))
+    nb = H
+    px = np.zeros(nb)
+    mass = np.zeros(nb)
+    with abi.Box(p) as box:
+        box.step(w.steps // 2)
+        for _ in range(w.steps // 2 // 50):
+            box.step(49)
+            abi.mpcd_record_moments(box.h, True)
+            box.step(1)
+            mom, s = box.moments()
+            abi.mpcd_record_moments(box.h, False)
+            layers = mom.reshape(H + 1, Ly, Lx, 5).sum(axis=(1, 2))
+            lo = np.clip(np.arange(H + 1) - 1 + s[2], 0, H)
+            hi = np.clip(np.arange(H + 1) + s[2], 0, H)
+            b = np.minimum((0.5 * (lo + hi)).astype(int), nb - 1)
+            np.add.at(px, b, layers[:, 1])
+            np.add.at(mass, b, layers[:, 0])
+    prof = px / mass
+    z = np.arange(nb) + 0.5
+    A = np.stack([np.ones(nb), z, z * z], axis=1)
+    coef, *_ = np.linalg.lstsq(A, prof, rcond=None)
+    fit_center = coef[0] + coef[1] * H / 2 + coef[2] * H * H / 4
+    out = {"nu_theory": nu, "vmax_theory": vmax, "expected_center_deficit": deficit,
+           "nu_fit_over_theory": float(-g / (2 * coef[2]) / nu),
+           "center_over_vmax": float(fit_center / vmax),
+           "wall_velocity_over_vmax": float(coef[0] / vmax),
+           "rms_vs_parabola_over_vmax": float(np.sqrt(((prof - g / (2 * nu) * z * (H - z) * (1 - deficit)) ** 2).mean())
+                                              / vmax)}
+    report("poiseuille_256x64x64_full", out)
+    assert abs(out["center_over_vmax"] - (1 - deficit)) < 0.05
+    assert abs(out["nu_fit_over_theory"] - 1 / (1 - deficit)) < 0.08
+    assert abs(out["wall_velocity_over_vmax"]) < 0.05
