@@ -165,17 +165,44 @@ def cpu_oracle_run(w, steps, sample_note):
                 sample_note, steps, w.n_particles, dt)}
 
 
+REF_SAMPLE_L = 32         # reference arm: one oracle step per timed step on a 32^3 sub-box
+REF_TIME_LIMIT_S = 150.0  # ... and at most this much timed CPU work in all
+
+
 def run_reference(args, w):
+    """The reference arm: the FP64 oracle as it stands, single thread, on the host cores.  Each
+    step is a bounded sample of the workload: one oracle step of a sub-box of side 32 (or
+    the box itself if smaller) with the workload's density and parameters; the timed steps
+    stop early once REF_TIME_LIMIT_S of CPU time is spent (stated in `sample`)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    res = cpu_oracle_run(w, max(1, args.steps), "reference arm")
-    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": args.gpus,
+    from oracle import oracle as orc
+    L = tuple(min(int(x), REF_SAMPLE_L) for x in w.L)
+    n = int(round(w.ppc * L[0] * L[1] * L[2]))
+    p = orc.make_params(L, a=w.a, dt=w.dt, alpha_deg=w.alpha_deg, kT=w.kT, mass=w.mass, ppc=w.ppc, seed=w.seed,
+                        resort_k=w.resort_k, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat)
+    r, v = orc.init(p, n)
+    st = orc.State(r, v)
+    for _ in range(max(1, args.warmup)):
+        orc.step(p, st)
+    done, t_cpu = 0, 0.0
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        orc.step(p, st)
+        t_cpu += time.perf_counter() - t0
+        done += 1
+        if t_cpu > REF_TIME_LIMIT_S:
+            break
+    value = n * done / t_cpu
+    sample = ("%d oracle steps (of %d asked; %d warm-up) of a %dx%dx%d sub-box, %d particles, same density and "
+              "parameters as %s; %.1f s single thread" % (done, args.steps, args.warmup, L[0], L[1], L[2], n, w.name, t_cpu))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "L": list(w.L), "particles": w.n_particles, "precision": w.precision},
-            "cpu_baseline": res,
-            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
