@@ -161,7 +161,7 @@ int mpcd_set_tuning(mpcd_t* h, const mpcd_tuning* t);
 
 /* Autotuner: times each candidate tuning on the handle's own box(es) for trial_steps steps
  * (CUDA events on the handle's stream), keeps the fastest and restores the state, so the
- * simulation is unchanged.  Candidates: group_target in {96, 112, 128, 144, 160} x warps
+ * simulation is unchanged.  Candidates: group_target in {128, 144, 160, 168, 176} x warps
  * in {2, 4} for the mixed form; resort_k in {1, 2, 5, 10, 20, 50} for the FP64 form.
  * *best receives the choice and *best_ms its time per step (either may be NULL). */
 int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* best_ms);

@@ -3,6 +3,7 @@
 // event timing and error reporting.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -50,10 +51,10 @@ struct mpcd_s {
   // mixed form: per-box tables (host copies and device arrays)
   std::vector<Geom> boxes;
   std::vector<int64_t> pbase;
-  std::vector<MixGroup> groups;
   Geom* d_boxes = nullptr;
   BoxShift* d_shifts = nullptr;
-  MixGroup* d_groups = nullptr;
+  MixGroup* d_groups = nullptr;       // rewritten every step by k_group_bounds
+  MixGroupSpec* d_gspec = nullptr;    // fixed part of the group table
   int64_t* d_pbase = nullptr;
   int64_t groups_cap = 0;
   MixBatch mb{};
@@ -256,8 +257,10 @@ int enqueue_step(mpcd_t* h, bool moments, int par = 0) {
       return rc;
     if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(m.count[par], m.offset, m.partial, g.ncell, h->stream); })))
       return rc;
-    if ((rc = run_slot(h, kSlotScatter,
-                       [&] { launch_scatter_cursor(g.n, m.key[par], m.offset, m.cursor, m.perm, h->stream); })))
+    if ((rc = run_slot(h, kSlotScatter, [&] {
+           launch_scatter_cursor(g.n, m.key[par], m.offset, m.cursor, m.perm, h->stream);
+           launch_group_bounds(h->mb, h->d_gspec, m.offset, h->d_groups, h->stream);
+         })))
       return rc;
     if ((rc = run_slot(h, kSlotCollide,
                        [&] { launch_collide_stream_mixed(h->mb, h->mix, m, h->ctl, moments, h->stream); })))
@@ -357,35 +360,44 @@ int upload_shifts(mpcd_t* h, int64_t t) {
 // Mixed form: the table of warp groups (consecutive cells of one box, about
 // tune.group_target particles each) for the current tuning.
 int build_groups(mpcd_t* h) {
-  std::vector<MixGroup> gr;
+  // the fixed part of the group table: per box, ceil(N_b / T_b) groups of T_b records, with
+  // T_b the target (at most 24 cells' worth on average, so groups rarely exceed 32 cells);
+  // k_group_bounds places their cell boundaries every step
+  std::vector<MixGroupSpec> spec;
   for (size_t b = 0; b < h->boxes.size(); ++b) {
     const Geom& g = h->boxes[b];
-    const int gc = mixed_cells_per_group(g.ppc, h->tune.group_target);
-    for (int64_t c = 0; c < g.ncell; c += gc) {
-      MixGroup x;
-      x.c0 = g.cbase + c;
+    const int64_t nb = h->pbase[b + 1] - h->pbase[b];
+    const int64_t tb = std::max<int64_t>(16, std::min<int64_t>(h->tune.group_target, (int64_t)(24.0 * g.ppc)));
+    const int64_t ng = std::max<int64_t>(1, (nb + tb - 1) / tb);
+    for (int64_t k = 0; k < ng; ++k) {
+      MixGroupSpec x;
+      x.rec0 = h->pbase[b] + k * tb;
+      x.rec1 = k + 1 < ng ? h->pbase[b] + (k + 1) * tb : -1;
       x.box = static_cast<int32_t>(b);
-      x.ncells = static_cast<int32_t>(std::min<int64_t>(gc, g.ncell - c));
-      gr.push_back(x);
+      x.pad = 0;
+      spec.push_back(x);
     }
   }
-  if ((int64_t)gr.size() > h->groups_cap) {
-    if (h->d_groups) {
-      cudaFree(h->d_groups);
-      for (auto& a : h->allocations)
-        if (a == h->d_groups) a = nullptr;
-      h->d_groups = nullptr;
+  if ((int64_t)spec.size() > 2000000000LL) return fail(h, MPCD_ERR_ARG, "too many cell groups");
+  if ((int64_t)spec.size() > h->groups_cap) {
+    for (void* p : {static_cast<void*>(h->d_groups), static_cast<void*>(h->d_gspec)}) {
+      if (!p) continue;
+      cudaFree(p);
+      for (auto& q : h->allocations)
+        if (q == p) q = nullptr;
     }
-    int rc = dalloc(h, &h->d_groups, (int64_t)gr.size());
+    h->d_groups = nullptr;
+    h->d_gspec = nullptr;
+    int rc = dalloc(h, &h->d_groups, (int64_t)spec.size());
+    if (!rc) rc = dalloc(h, &h->d_gspec, (int64_t)spec.size());
     if (rc) return rc;
-    h->groups_cap = (int64_t)gr.size();
+    h->groups_cap = (int64_t)spec.size();
   }
-  if (!gr.empty())
-    MPCD_TRY(h, cudaMemcpyAsync(h->d_groups, gr.data(), sizeof(MixGroup) * gr.size(), cudaMemcpyHostToDevice, h->stream));
+  MPCD_TRY(h, cudaMemcpyAsync(h->d_gspec, spec.data(), sizeof(MixGroupSpec) * spec.size(), cudaMemcpyHostToDevice,
+                              h->stream));
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
-  h->groups = gr;
   h->mb.groups = h->d_groups;
-  h->mb.ngroups = static_cast<int32_t>(gr.size());
+  h->mb.ngroups = static_cast<int32_t>(spec.size());
   h->mb.warps = h->tune.warps;
   drop_graph(h);  // the graphs hold the old table
   return MPCD_OK;
@@ -412,7 +424,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   }
   h->precision = p[0].precision;
   h->nbox = nbox;
-  h->tune.group_target = 144;
+  h->tune.group_target = 168;
   h->tune.warps = 4;
   h->tune.resort_k = p[0].resort_k;
   // per-box geometry; the handle's geom describes the whole concatenation for the kernels
@@ -456,6 +468,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     if ((e = prepare_collide_mixed()) != cudaSuccess) return bail(cuda_fail(h, e, "collide kernel setup"));
     h->per_step[kSlotStreamBin] = 0;  // binning is fused into the collide kernel
     h->per_step[kSlotZero] = 2;
+    h->per_step[kSlotScatter] = 2;  // scatter + group bounds
     h->per_step[kSlotCollide] = 1;
     h->per_step[kSlotRotate] = 0;
     for (int k = 0; k < 2; ++k) {
@@ -834,7 +847,7 @@ int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* bes
   std::vector<mpcd_tuning> cand;
   if (h->precision == MPCD_MIXED) {
     for (int w : {2, 4})
-      for (int tg : {96, 112, 128, 144, 160}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, 0});
+      for (int tg : {128, 144, 160, 168, 176}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, 0});
   } else {
     for (int k : {1, 2, 5, 10, 20, 50}) cand.push_back(mpcd_tuning{h->tune.group_target, h->tune.warps, k, 0});
   }

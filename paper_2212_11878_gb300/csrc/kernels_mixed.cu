@@ -580,6 +580,9 @@ struct Span {
   int lo, n;  // this lane's cell: first record relative to E0, members
 };
 
+// Whether a group goes through the shared-memory stage.
+__device__ __forceinline__ bool stages(const Span& sp) { return sp.E > 0 && sp.E <= kMixCap && sp.ncells <= 32; }
+
 __device__ __forceinline__ MixGroup group_desc(const MixBatch& mb, int64_t gi) {
   if (gi < mb.ngroups) return mb.groups[gi];
   MixGroup d;
@@ -615,8 +618,9 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // Start copying a group's records (slots pm) and its box's constants into the stage.
 template <typename Stage>
-__device__ __forceinline__ void gather_async(Stage& st, const MixRec* __restrict__ src, int E, const int pm[kPer],
-                                             const MixBatch& mb, int box, int slot, int lane) {
+__device__ __forceinline__ void gather_async(Stage& st, const MixRec* __restrict__ src, const Span& sp, const int pm[kPer],
+                                             const MixBatch& mb, int slot, int lane) {
+  const int E = sp.E, box = sp.box;
   static_assert(sizeof(Geom) % 16 == 0 && sizeof(BoxShift) % 16 == 0, "16-byte pieces");
   constexpr int kGeomPieces = sizeof(Geom) / 16, kShiftPieces = sizeof(BoxShift) / 16;
   static_assert(kGeomPieces + kShiftPieces <= 32, "one piece per lane");
@@ -625,7 +629,7 @@ __device__ __forceinline__ void gather_async(Stage& st, const MixRec* __restrict
   else if (lane < kGeomPieces + kShiftPieces)
     cp_async16(reinterpret_cast<float4*>(&st.shift[slot]) + (lane - kGeomPieces),
                reinterpret_cast<const float4*>(mb.shifts + box) + (lane - kGeomPieces));
-  if (E <= kMixCap) {
+  if (stages(sp)) {
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
       const int e = lane + 32 * i;
@@ -642,7 +646,7 @@ __device__ __forceinline__ void load_perm(const int32_t* __restrict__ perm, cons
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     const int e = lane + 32 * i;
-    pm[i] = (sp.E <= kMixCap && e < sp.E) ? perm[sp.E0 + e] : 0;
+    pm[i] = (stages(sp) && e < sp.E) ? perm[sp.E0 + e] : 0;
   }
 }
 
@@ -665,7 +669,8 @@ __device__ __forceinline__ long long shfl_xor_ll(long long x, int m) {
   return __shfl_xor_sync(0xffffffffu, x, m);
 }
 
-// A group too large for the stage: one lane per cell, records in place in the destination.
+// A group too large for the stage (more than kMixCap records or 32 cells): one lane per
+// cell, in passes of 32 cells, records in place in the destination.
 // (Arguments are plain values and pointers so that calling it stores nothing to the stack.)
 template <int WALLS, int FORCE, int THERMO, int MOMENTS>
 __device__ __noinline__ void collide_group_direct(const Geom* __restrict__ gp, const BoxShift* __restrict__ shp,
@@ -674,25 +679,25 @@ __device__ __noinline__ void collide_group_direct(const Geom* __restrict__ gp, c
                                                   const MixRec* __restrict__ src, MixRec* __restrict__ dst,
                                                   int32_t* __restrict__ knext, int32_t* __restrict__ cnext, int64_t t1,
                                                   int lane) {
-  if (lane >= ncells) return;
   const Geom& g = *gp;
   const float sf[3] = {shp->sf_next[0], shp->sf_next[1], shp->sf_next[2]};
   const int cbase = static_cast<int>(g.cbase);
-  const int64_t c = c0 + lane;
-  const int o = offset[c];
-  const int n = offset[c + 1] - o;
-  const int32_t* pm = perm + o;
-  for (int j = 0; j < n; ++j) {
-    MixRec r = load_rec(src + pm[j]);
-    stream_record<WALLS, FORCE>(g, r);
-    dst[o + j] = r;
-  }
-  mixed_collide_cell<WALLS, THERMO, MOMENTS>(g, dst + o, n, c - cbase, t1, shp->s[2],
-                                             MOMENTS ? moments + 5 * (int64_t)cbase : nullptr);
-  for (int j = 0; j < n; ++j) {
-    const int k = cbase + next_key<WALLS, FORCE>(g, dst[o + j], sf);
-    knext[o + j] = k;
-    atomicAdd(&cnext[k], 1);
+  for (int64_t c = c0 + lane; c < c0 + ncells; c += 32) {
+    const int o = offset[c];
+    const int n = offset[c + 1] - o;
+    const int32_t* pm = perm + o;
+    for (int j = 0; j < n; ++j) {
+      MixRec r = load_rec(src + pm[j]);
+      stream_record<WALLS, FORCE>(g, r);
+      dst[o + j] = r;
+    }
+    mixed_collide_cell<WALLS, THERMO, MOMENTS>(g, dst + o, n, c - cbase, t1, shp->s[2],
+                                               MOMENTS ? moments + 5 * (int64_t)cbase : nullptr);
+    for (int j = 0; j < n; ++j) {
+      const int k = cbase + next_key<WALLS, FORCE>(g, dst[o + j], sf);
+      knext[o + j] = k;
+      atomicAdd(&cnext[k], 1);
+    }
   }
 }
 
@@ -781,14 +786,14 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
   int pm[kPer];
   load_perm(perm, sp, pm, lane);
   int slot = 0;  // stage slot of the current group's box constants
-  gather_async(st, src, sp.E, pm, mb, sp.box, slot, lane);
+  gather_async(st, src, sp, pm, mb, slot, lane);
   Span sp1 = group_span(offset, group_desc(mb, gi + W), lane);
   load_perm(perm, sp1, pm, lane);
   cp_async_wait_all();
   __syncwarp();
 
   for (;;) {
-    const bool staged = sp.E <= kMixCap && sp.E > 0;  // empty groups take the per-cell path
+    const bool staged = stages(sp);  // empty and oversized groups take the per-cell path
     MixRec r[kPer];
     if (staged) {
       // every lane takes kPer records; those past the end of the group repeat the last one,
@@ -800,7 +805,7 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
       }
     }
     __syncwarp();
-    gather_async(st, src, sp1.E, pm, mb, sp1.box, slot ^ 1, lane);  // group k + 1: HBM -> stage
+    gather_async(st, src, sp1, pm, mb, slot ^ 1, lane);  // group k + 1: HBM -> stage
     const MixGroup d2 = group_desc(mb, gi + 2 * W);       // group k + 2: descriptor
     Span sp2;
     if (!staged) {
@@ -1023,6 +1028,38 @@ __global__ void __launch_bounds__(kThreads) k_scatter_cursor(int64_t n, const in
   }
 }
 
+// First cell c in [lo, hi] with offset[c] >= rec (offset[hi] is the box's end).
+__device__ __forceinline__ int64_t first_cell(const int32_t* __restrict__ offset, int64_t lo, int64_t hi, int64_t rec) {
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (offset[mid] >= rec)
+      hi = mid;
+    else
+      lo = mid + 1;
+  }
+  return lo;
+}
+
+// Group g of a box starts at the first cell whose records start at or after its rec0, and
+// ends where the next group starts (the last one at the box's end): the groups tile the box
+// and each holds about the target number of records, within one cell's worth.
+__global__ void __launch_bounds__(kThreads) k_group_bounds(int64_t ngroups, const Geom* __restrict__ boxes,
+                                                           const MixGroupSpec* __restrict__ spec,
+                                                           const int32_t* __restrict__ offset,
+                                                           MixGroup* __restrict__ groups) {
+  for (int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; gi < ngroups; gi += (int64_t)gridDim.x * blockDim.x) {
+    const MixGroupSpec q = spec[gi];
+    const int64_t cb = boxes[q.box].cbase, ce = cb + boxes[q.box].ncell;
+    const int64_t c0 = first_cell(offset, cb, ce, q.rec0);
+    const int64_t c1 = q.rec1 < 0 ? ce : first_cell(offset, cb, ce, q.rec1);
+    MixGroup d;
+    d.c0 = c0;
+    d.box = q.box;
+    d.ncells = static_cast<int32_t>(c1 - c0);
+    groups[gi] = d;
+  }
+}
+
 __device__ __forceinline__ void box_shifts(const Geom& g, int64_t t, BoxShift& b) {
   grid_shift(g.seed, t + 1, g.a, g.walls, b.s);
   grid_shift(g.seed, t + 2, g.a, g.walls, b.s_next);
@@ -1169,13 +1206,6 @@ __global__ void __launch_bounds__(kThreads) k_get_state_mixed(MixBatch mb, const
 }
 }  // namespace
 
-int mixed_cells_per_group(double ppc, int target) {
-  int gc = ppc > 0.0 ? static_cast<int>(target / ppc) : 32;
-  if (gc > 32) gc = 32;
-  if (gc < 1) gc = 1;
-  return gc;
-}
-
 void mixed_box_shifts(const Geom& g, int64_t t, BoxShift* out) {
   grid_shift(g.seed, t + 1, g.a, g.walls, out->s);
   grid_shift(g.seed, t + 2, g.a, g.walls, out->s_next);
@@ -1279,6 +1309,12 @@ void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st) { k_en
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
                            cudaStream_t st) {
   k_scatter_cursor<<<grid_for(n, 4), kThreads, 0, st>>>(n, key, offset, cursor, perm);
+}
+
+void launch_group_bounds(const MixBatch& mb, const MixGroupSpec* spec, const int32_t* offset, MixGroup* groups,
+                         cudaStream_t st) {
+  if (mb.ngroups > 0)
+    k_group_bounds<<<grid_for(mb.ngroups), kThreads, 0, st>>>(mb.ngroups, mb.boxes, spec, offset, groups);
 }
 
 void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, double* v, cudaStream_t st) {

@@ -122,11 +122,21 @@ void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double
 void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st);
 
 // ---- mixed form (kernels_mixed.cu); one box or an ensemble of independent boxes ----
-// A group of consecutive cells of one box, handled by one warp.
+// A group of consecutive cells of one box, handled by one warp; rewritten every step
+// (k_group_bounds) so that each group holds about the target number of records.
 struct MixGroup {
   int64_t c0;      // first cell (global key)
   int32_t box;
-  int32_t ncells;  // at most 32
+  int32_t ncells;  // groups of more than 32 cells take the per-cell path
+};
+
+// The fixed part of a group: it starts at the first cell of its box whose record offset
+// reaches rec0 (the box's first group starts at the box's first cell).
+struct MixGroupSpec {
+  int64_t rec0;   // first record of the group's range (global, cell order)
+  int64_t rec1;   // first record of the next group of the box, or -1 for the box's last group
+  int32_t box;
+  int32_t pad;
 };
 
 // Grid shifts of one box (each box draws its own from its seed).
@@ -153,7 +163,6 @@ struct MixBatch {
 };
 
 constexpr int kMixCap = 192;  // records one warp stages (larger groups take the per-cell path)
-int mixed_cells_per_group(double ppc, int target);  // cells per warp group for ~target records
 void mixed_box_shifts(const Geom& g, int64_t t, BoxShift* out);  // host: shifts of steps t+1, t+2
 void launch_init_mixed_box(const Geom& g, MixBufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
 void launch_bin_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st);
@@ -164,6 +173,9 @@ void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ct
 void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st);
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
                            cudaStream_t st);
+// Rewrite the group table from this step's offsets.
+void launch_group_bounds(const MixBatch& mb, const MixGroupSpec* spec, const int32_t* offset, MixGroup* groups,
+                         cudaStream_t st);
 void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, double* v, cudaStream_t st);
 void launch_set_state_mixed(const MixBatch& mb, MixBufs b, const double* r, const double* v, cudaStream_t st);
 
