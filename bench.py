@@ -395,7 +395,6 @@ def main():
                            "roofline": roofline_of(fk, True, hbm_peak, peak_src, fn),
                            "kernels": {k: {"ms_per_step": v["ms_per_step"], "share": v["share"], "gbs": v["gbs"]}
                                        for k, v in fk.items()}}
-            launches += fl
             fbox.close()
 
     cpu = None
