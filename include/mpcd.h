@@ -109,12 +109,14 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v);
 
 /* Replace the state from host arrays r[n*3], v[n*3] (particle-id order) and set the step
  * counter to t (the next step is t + 1).  n must equal mpcd_num_particles.  Positions must
- * lie in the box ([0, L a) per axis); MPCD_ERR_ARG otherwise.  Synchronises. */
+ * lie in their box ([0, L a) per axis) and velocities be finite; otherwise MPCD_ERR_ARG
+ * (the message names the first offending particle) and the state is unchanged.  The check
+ * runs on the device.  Synchronises. */
 int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64_t t);
 
-/* Same as mpcd_get_state / mpcd_set_state with device arrays; enqueued on the handle's
- * stream without a host synchronisation.  The device variant of set_state does not check
- * that positions lie in the box. */
+/* Same as mpcd_get_state / mpcd_set_state with device arrays.  get_state_device is enqueued
+ * on the handle's stream without a host synchronisation; set_state_device checks the state
+ * as mpcd_set_state does, which synchronises once. */
 int mpcd_get_state_device(mpcd_t* h, double* r_dev, double* v_dev);
 int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const double* v_dev, int64_t t);
 

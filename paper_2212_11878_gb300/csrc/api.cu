@@ -60,6 +60,7 @@ struct mpcd_s {
   MixBatch mb{};
   mpcd_tuning tune{};
   Ctl* ctl = nullptr;
+  unsigned long long* d_bad = nullptr;  // first invalid particle found by the state check
   Ctl ctl_host{};  // host copy used to (re)initialise the device control block
   int red_blocks = 0;
   std::vector<void*> allocations;
@@ -520,6 +521,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     }
   }
   if ((rc = dalloc(h, &h->ctl, 1))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_bad, 1))) return bail(rc);
   h->red_blocks = 152 * 4;
   if ((rc = dalloc(h, &h->scr.red, 3 * (int64_t)h->red_blocks))) return bail(rc);
   h->ctl_host = Ctl{};
@@ -652,11 +654,26 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v) {
   return MPCD_OK;
 }
 
+// Reject a state with a position outside its box or a non-finite velocity before any of it
+// is applied (checked on the device; synchronises).
+int check_state(mpcd_t* h, const double* r_dev, const double* v_dev) {
+  MPCD_TRY(h, cudaMemsetAsync(h->d_bad, 0xFF, sizeof(unsigned long long), h->stream));
+  launch_check_state(h->precision == MPCD_MIXED ? &h->mb : nullptr, h->geom, h->n, r_dev, v_dev, h->d_bad, h->stream);
+  MPCD_TRY(h, cudaGetLastError());
+  unsigned long long bad = 0;
+  MPCD_TRY(h, cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  if (bad != ~0ull)
+    return fail(h, MPCD_ERR_ARG, "position outside its box or non-finite velocity at particle " + std::to_string(bad));
+  return MPCD_OK;
+}
+
 int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const double* v_dev, int64_t t) {
   int rc = guard(h);
   if (rc) return rc;
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!r_dev || !v_dev || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
+  if ((rc = check_state(h, r_dev, v_dev))) return rc;
   if (h->precision == MPCD_MIXED)
     launch_set_state_mixed(h->mb, h->mix, r_dev, v_dev, h->stream);
   else
@@ -683,21 +700,7 @@ int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64
   if (rc) return rc;
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!r || !v || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
-  const int nb = h->precision == MPCD_MIXED ? static_cast<int>(h->boxes.size()) : 1;
-  for (int b = 0; b < nb; ++b) {
-    const Geom& gb = h->precision == MPCD_MIXED ? h->boxes[(size_t)b] : h->geom;
-    const int64_t i0 = h->precision == MPCD_MIXED ? h->pbase[(size_t)b] : 0;
-    const int64_t i1 = h->precision == MPCD_MIXED ? h->pbase[(size_t)b + 1] : n;
-    for (int64_t i = i0; i < i1; ++i)
-      for (int d = 0; d < 3; ++d) {
-        const double x = r[3 * i + d];
-        if (!(x >= 0.0 && x < gb.B[d]))
-          return fail(h, MPCD_ERR_ARG, "position outside its box at particle " + std::to_string(i));
-        if (!std::isfinite(v[3 * i + d]))
-          return fail(h, MPCD_ERR_ARG, "non-finite velocity at particle " + std::to_string(i));
-      }
-  }
-  double* scratch = nullptr;
+  double* scratch = nullptr;  // the state is uploaded, then checked and applied on the device
   MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 6 * (size_t)(n > 0 ? n : 1), h->stream));
   cudaError_t e = cudaMemcpyAsync(scratch, r, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + 3 * n, v, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);

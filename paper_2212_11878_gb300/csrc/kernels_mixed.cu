@@ -1106,6 +1106,14 @@ __device__ __forceinline__ MixRec to_record(const Geom& g, const double r[3], co
     const double q = g.pow2a ? r[d] * g.inv_a : r[d] / g.a;
     double fl = floor(q);
     float x = static_cast<float>(q - fl);
+    if (!(fl >= 0.0 && fl < static_cast<double>(g.L[d]))) {
+      // outside the box (the state entry points reject such input): fold into range, so
+      // that no cell index can leave the key space
+      const double Ld = static_cast<double>(g.L[d]);
+      fl = (fl == fl && fabs(fl) < 9.0e15) ? fl - Ld * floor(fl / Ld) : 0.0;
+      if (!(fl >= 0.0 && fl < Ld)) fl = 0.0;
+      if (!(x >= 0.0f && x < 1.0f)) x = 0.0f;
+    }
     int c = static_cast<int>(fl);
     if (x >= 1.0f) {
       x = 0.0f;
@@ -1176,6 +1184,30 @@ __global__ void __launch_bounds__(kThreads) k_init_mixed_write(Geom g, MixBufs b
     v[2] -= m2;
     store_rec(b.rec[0] + g.pbase + i, to_record(g, r, v, static_cast<int32_t>(g.pbase + i)));
   }
+}
+
+// Validation of a state on the device: the smallest index i with a position outside
+// [0, B_d) of its box or a non-finite velocity goes to *bad (left as is when all are valid).
+__device__ __forceinline__ bool state_ok(const double* r, const double* v, const double B[3]) {
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ok = ok && r[d] >= 0.0 && r[d] < B[d] && isfinite(v[d]);
+  return ok;
+}
+
+__global__ void __launch_bounds__(kThreads) k_check_state_batch(MixBatch mb, const double* __restrict__ r,
+                                                                const double* __restrict__ v,
+                                                                unsigned long long* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < mb.n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!state_ok(r + 3 * i, v + 3 * i, mb.boxes[box_of(mb.pbase, mb.nbox, i)].B))
+      atomicMin(bad, static_cast<unsigned long long>(i));
+}
+
+__global__ void __launch_bounds__(kThreads) k_check_state_box(int64_t n, Geom g, const double* __restrict__ r,
+                                                              const double* __restrict__ v,
+                                                              unsigned long long* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!state_ok(r + 3 * i, v + 3 * i, g.B)) atomicMin(bad, static_cast<unsigned long long>(i));
 }
 
 __global__ void __launch_bounds__(kThreads) k_set_state_mixed(MixBatch mb, MixBufs b, const double* __restrict__ r,
@@ -1319,6 +1351,14 @@ void launch_group_bounds(const MixBatch& mb, const MixGroupSpec* spec, const int
 
 void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, double* v, cudaStream_t st) {
   k_get_state_mixed<<<grid_for(mb.n), kThreads, 0, st>>>(mb, b.rec[cur], r, v);
+}
+
+void launch_check_state(const MixBatch* mb, const Geom& g, int64_t n, const double* r, const double* v,
+                        unsigned long long* bad, cudaStream_t st) {
+  if (mb)
+    k_check_state_batch<<<grid_for(n), kThreads, 0, st>>>(*mb, r, v, bad);
+  else
+    k_check_state_box<<<grid_for(n), kThreads, 0, st>>>(n, g, r, v, bad);
 }
 
 void launch_set_state_mixed(const MixBatch& mb, MixBufs b, const double* r, const double* v, cudaStream_t st) {

@@ -178,5 +178,9 @@ void launch_group_bounds(const MixBatch& mb, const MixGroupSpec* spec, const int
                          cudaStream_t st);
 void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, double* v, cudaStream_t st);
 void launch_set_state_mixed(const MixBatch& mb, MixBufs b, const double* r, const double* v, cudaStream_t st);
+// First invalid particle of a state (position outside its box, non-finite velocity) into
+// *bad, which the caller sets to ~0 first: per box of *mb, or for the single box g if mb is NULL.
+void launch_check_state(const MixBatch* mb, const Geom& g, int64_t n, const double* r, const double* v,
+                        unsigned long long* bad, cudaStream_t st);
 
 }  // namespace mpcd

@@ -249,3 +249,32 @@ def test_poiseuille_channel_mixed():
     assert abs(nu_fit / nu - 1) < 0.15, (nu_fit, nu)
     vmax = g * H * H / (8 * nu)
     assert abs(coef[0]) < 0.2 * vmax and abs(-coef[1] / (2 * coef[2]) - H / 2) < 0.05 * H
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_set_state_rejects_invalid_input(precision):
+    """Positions outside the box and non-finite velocities are rejected on both entry points,
+    naming the first offending particle, and leave the state as it was."""
+    import torch
+    L = (6, 5, 4)
+    p = abi.make_params(L, precision=precision, seed=3)
+    with abi.Box(p) as box:
+        r0, v0 = box.state()
+        for k, (dr, dv) in enumerate([((7, 0), None), ((-1e-9, 2), None), ((float("nan"), 1), None),
+                                      (None, (float("inf"), 0)), ((1e300, 2), None)]):
+            r, v = r0.copy(), v0.copy()
+            i = 11 + k
+            if dr:
+                r[i, dr[1]] = dr[0] if dr[0] != 7 else 7.0 * L[0]
+            if dv:
+                v[i, dv[1]] = dv[0]
+            with pytest.raises(abi.MpcdError, match="particle %d" % i):
+                box.set_state(r, v, 0)
+            if torch.cuda.is_available():
+                rd = torch.from_numpy(r).cuda()
+                vd = torch.from_numpy(v).cuda()
+                torch.cuda.synchronize()
+                with pytest.raises(abi.MpcdError, match="particle %d" % i):
+                    abi.mpcd_set_state_device(box.h, rd, vd, 0)
+            r1, v1 = box.state()
+            assert np.array_equal(r1, r0) and np.array_equal(v1, v0)
