@@ -665,10 +665,6 @@ __device__ __forceinline__ MixRec lds_rec(const MixRec* p) {
   return r;
 }
 
-__device__ __forceinline__ long long shfl_xor_ll(long long x, int m) {
-  return __shfl_xor_sync(0xffffffffu, x, m);
-}
-
 // A group too large for the stage (more than kMixCap records or 32 cells): one lane per
 // cell, in passes of 32 cells, records in place in the destination.
 // (Arguments are plain values and pointers so that calling it stores nothing to the stack.)
