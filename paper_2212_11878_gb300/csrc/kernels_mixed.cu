@@ -811,7 +811,7 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
       load_perm(perm, sp2, pm, lane);
     } else {
       const Geom* gbox = mb.boxes + sp.box;
-      const Geom& g = st.box[slot];  // box constants in shared memory
+      const Geom g = st.box[slot];  // a register copy: the stores below cannot alias it
       const BoxShift& sh = st.shift[slot];
       const float sf[3] = {sh.sf_next[0], sh.sf_next[1], sh.sf_next[2]};  // grid of the next step
       const double shz = sh.s[2];                                        // grid of this step
