@@ -650,9 +650,14 @@ __device__ __forceinline__ void load_perm(const int32_t* __restrict__ perm, cons
   }
 }
 
-__device__ __forceinline__ MixRec lds_rec(const MixRec* p) {
+// A staged record from shared memory.  Lanes with bit 2 set read the second 16-byte half
+// first, so that the eight lanes of each quarter-warp cover all 32 banks (the 32-byte record
+// stride would otherwise put lanes l and l + 4 on the same banks).
+__device__ __forceinline__ MixRec lds_rec(const MixRec* p, int lane) {
   const float4* q = reinterpret_cast<const float4*>(p);
-  const float4 a = q[0], b = q[1];
+  const int h = (lane >> 2) & 1;
+  const float4 x = q[h], y = q[h ^ 1];
+  const float4 a = h ? y : x, b = h ? x : y;
   MixRec r;
   r.ox = a.x;
   r.oy = a.y;
@@ -797,7 +802,7 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
 #pragma unroll
       for (int i = 0; i < kPer; ++i) {
         const int e = lane + 32 * i;
-        r[i] = lds_rec(&st.rec[e < sp.E ? e : sp.E - 1]);
+        r[i] = lds_rec(&st.rec[e < sp.E ? e : sp.E - 1], lane);
       }
     }
     __syncwarp();
