@@ -994,12 +994,12 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
 // perm[offset[key] + rank] = slot, the rank from a per-cell cursor.  Neighbouring slots mostly
 // share a key, so each warp groups equal keys (match.any) and one lane per group takes the
 // group's ranks with a single atomic.  The order inside a cell is whatever the atomics give;
-// every per-cell sum downstream is exact, so it does not matter.  A warp takes 4 chunks of
-// 32 consecutive slots per iteration, so that four load-atomic-store chains are in flight.
+// every per-cell sum downstream is exact, so it does not matter.  A warp takes 8 chunks of
+// 32 consecutive slots per iteration, so that eight load-atomic-store chains are in flight.
 __global__ void __launch_bounds__(kThreads) k_scatter_cursor(int64_t n, const int32_t* __restrict__ key,
                                                              const int32_t* __restrict__ offset, int32_t* __restrict__ cursor,
                                                              int32_t* __restrict__ perm) {
-  constexpr int kChunks = 4;
+  constexpr int kChunks = 8;
   const int lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -1341,7 +1341,7 @@ void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st) { k_en
 
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
                            cudaStream_t st) {
-  k_scatter_cursor<<<grid_for(n, 4), kThreads, 0, st>>>(n, key, offset, cursor, perm);
+  k_scatter_cursor<<<grid_for(n, 8), kThreads, 0, st>>>(n, key, offset, cursor, perm);
 }
 
 void launch_group_bounds(const MixBatch& mb, const MixGroupSpec* spec, const int32_t* offset, MixGroup* groups,
