@@ -65,10 +65,6 @@ __device__ __forceinline__ bool fx_add(Fx128& a, double x) {
   return true;
 }
 
-__device__ __forceinline__ double pow2i(int k) {  // 2^k for -1022 <= k <= 1023
-  return __longlong_as_double(static_cast<long long>(k + 1023) << 52);
-}
-
 // The accumulated value rounded once to FP64 (round to nearest even).
 __device__ __forceinline__ double fx_value(const Fx128& a) {
   unsigned long long lo = a.lo, hi = a.hi;
@@ -91,8 +87,19 @@ __device__ __forceinline__ double fx_value(const Fx128& a) {
     top = lo << lz;
     k = -lz;
   }
-  const double d = __dmul_rn(__ull2double_rn(top), pow2i(k - 80));
-  return neg ? -d : d;
+  // top * 2^(k - 80) with top rounded to 53 bits (nearest, ties to even), assembled from its
+  // fields: the same bits as converting top and scaling by 2^(k - 80), without the two
+  // instructions on GB300's narrow FP64 pipe
+  unsigned long long m = top >> 11;
+  const unsigned rem = static_cast<unsigned>(top & 0x7FFull);
+  if (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ++m;
+  unsigned long long e = static_cast<unsigned long long>(1006 + k);  // top in [2^63, 2^64)
+  if (m >> 53) {
+    m >>= 1;
+    ++e;
+  }
+  const unsigned long long bits = (e << 52) | (m & 0x000FFFFFFFFFFFFFull) | (neg ? 0x8000000000000000ull : 0ull);
+  return __longlong_as_double(static_cast<long long>(bits));
 }
 
 // 1/n for the common occupancies (constant-folded, correctly rounded); others divide.

@@ -51,7 +51,17 @@ __host__ __device__ __forceinline__ u64x4 draw(uint64_t seed, uint64_t a, uint64
 
 // The top 53 bits of w as k * 2^-53, uniform on [0, 1); exact in FP64.
 __host__ __device__ __forceinline__ double unit53(uint64_t w) {
+#ifdef __CUDA_ARCH__
+  // the same value assembled from its fields (no 64-bit conversion on the narrow FP64 pipe):
+  // m = w >> 11 < 2^53 is exact in FP64, and m 2^-53 = 1.f 2^(10 - clz(m))
+  const uint64_t m = w >> 11;
+  if (m == 0) return 0.0;
+  const int lz = __clzll(static_cast<long long>(m));  // 11 .. 63
+  const uint64_t mant = m << (lz - 11);                // leading one at bit 52
+  return __longlong_as_double(static_cast<long long>((static_cast<uint64_t>(1033 - lz) << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
+#else
   return static_cast<double>(w >> 11) * 0x1.0p-53;
+#endif
 }
 
 // Grid shift of step t: uniform in [-a/2, a/2) per axis; with walls the z component is
