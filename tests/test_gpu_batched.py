@@ -45,6 +45,34 @@ def test_each_box_equals_the_box_alone():
         assert np.array_equal(v[pb[b]:pb[b + 1]], v1), b
 
 
+WALL_BOXES = [
+    dict(L=(6, 6, 8), ppc=10, alpha_deg=130, dt=0.1, seed=201, g=(0.01, 0.0, 0.0)),
+    dict(L=(8, 4, 10), ppc=15, alpha_deg=100, dt=0.05, seed=202, g=(0.005, 0.002, 0.0)),
+    dict(L=(5, 7, 6), ppc=6, alpha_deg=150, dt=0.2, seed=203, g=(0.0, 0.0, 0.0)),
+]
+SPARSE_BOXES = [  # groups span more than 32 cells here and take the per-cell path
+    dict(L=(20, 20, 20), ppc=0.8, alpha_deg=130, dt=0.1, seed=301),
+    dict(L=(16, 12, 10), ppc=2, alpha_deg=90, dt=0.2, seed=302),
+    dict(L=(6, 6, 6), ppc=12, alpha_deg=120, dt=0.1, seed=303),
+]
+
+
+@pytest.mark.parametrize("boxes,extra", [(WALL_BOXES, dict(walls_z=1, thermostat=1)), (SPARSE_BOXES, {})],
+                         ids=["walls_force_thermostat", "sparse"])
+def test_each_box_equals_the_box_alone_other_kinds(boxes, extra):
+    params = [abi.make_params(precision="mixed", **k, **extra) for k in boxes]
+    with abi.Box(batch=params) as ens:
+        pb, _ = abi.mpcd_box_offsets(ens.h)
+        ens.step(8)
+        r, v = ens.state()
+    for b, p in enumerate(params):
+        with abi.Box(p) as one:
+            one.step(8)
+            r1, v1 = one.state()
+        assert np.array_equal(r[pb[b]:pb[b + 1]], r1), b
+        assert np.array_equal(v[pb[b]:pb[b + 1]], v1), b
+
+
 def test_ensemble_sort_and_conservation():
     params = [box_params(k) for k in BOXES]
     with abi.Box(batch=params) as ens:
