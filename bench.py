@@ -52,7 +52,7 @@ FP64_BYTES = {
 FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # rotate on re-sort steps also moves r and the ids
 # FP64 instructions (DFMA, DADD, DMUL) per launch, as (per particle, per cell): the FP64 form
 # is bound by GB300's FP64 pipe (2 instructions per clock per SM), not by HBM.
-FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 73.0), "rotate": (9.0, 0.0)}
+FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 71.0), "rotate": (9.0, 0.0)}
 SMS, FP64_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_GOPS = SMS * FP64_PER_CLK * SM_MAX_MHZ / 1e3   # 629.3 G FP64 instructions/s
 ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step
