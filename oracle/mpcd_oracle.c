@@ -127,6 +127,32 @@ void orc_axis(const orc_params* p, int64_t t, int64_t cell, double n[3]) {
   n[2] = z;
 }
 
+/* Marsaglia and Tsang, "A simple method for generating gamma variables", ACM TOMS 26(3),
+ * 2000: for shape a >= 1 put d = a - 1/3 and c = 1/sqrt(9 d); draw x standard normal and
+ * u uniform on (0, 1]; with t = 1 + c x > 0 and v = t^3, d v is accepted when
+ * u < 1 - 0.0331 x^4 (the squeeze) or log u < x^2/2 + d (1 - v + log v); else draw again.
+ * Attempt k takes its three uniforms from Philox counter (t, cell, THERMO, k): the normal
+ * from words 0 and 1 by Box-Muller (the cosine branch), u from word 2. */
+double orc_mbs_gamma(const orc_params* p, int64_t t, int64_t cell, double shape) {
+  double d = shape - 1.0 / 3.0;
+  double c = 1.0 / sqrt(9.0 * d);
+  for (uint64_t k = 0; k < 64; ++k) {
+    uint64_t ctr[4] = {(uint64_t)t, (uint64_t)cell, ORC_TAG_THERMO, k};
+    uint64_t key[2] = {p->seed, 0};
+    uint64_t w[4];
+    orc_philox(ctr, key, w);
+    double x = sqrt(-2.0 * log(1.0 - orc_u53(w[0]))) * cos(2.0 * ORC_PI * orc_u53(w[1]));
+    double tt = 1.0 + c * x;
+    if (tt <= 0.0) continue;
+    double v = tt * tt * tt;
+    double u = 1.0 - orc_u53(w[2]);
+    double x2 = x * x;
+    if (u < 1.0 - 0.0331 * (x2 * x2)) return d * v;
+    if (log(u) < 0.5 * x2 + d * (1.0 - v + log(v))) return d * v;
+  }
+  return d;
+}
+
 void orc_rotate(const double n[3], double alpha, const double u[3], double v[3]) {
   double d[3], cr[3], out[3];
   for (int k = 0; k < 3; ++k) d[k] = v[k] - u[k];               /* relative velocity */
@@ -314,14 +340,16 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
 
     if (p->thermostat && nc >= 2) {
       /* R14: rescale the relative velocities so the cell's relative kinetic energy is
-       * (3/2)(n_c - 1) kT. */
+       * (3/2)(n_c - 1) kT; R16 (MBS): kT times a Gamma(3/2 (n_c - 1)) draw instead. */
+      double target = p->thermostat == 2 ? p->kT * orc_mbs_gamma(p, t, c, 1.5 * (double)(nc - 1))
+                                         : 1.5 * (double)(nc - 1) * p->kT;
       double K = 0.0;
       for (int32_t j = off[c]; j < off[c + 1]; ++j) {
         const double* vi = &v[3 * (int64_t)perm[j]];
         for (int d = 0; d < 3; ++d) K += 0.5 * m * (vi[d] - u[d]) * (vi[d] - u[d]);
       }
       if (K > 0.0) {
-        double f = sqrt(1.5 * (double)(nc - 1) * p->kT / K);
+        double f = sqrt(target / K);
         for (int32_t j = off[c]; j < off[c + 1]; ++j) {
           double* vi = &v[3 * (int64_t)perm[j]];
           for (int d = 0; d < 3; ++d) vi[d] = u[d] + f * (vi[d] - u[d]);

@@ -105,6 +105,8 @@ def lib():
             L.orc_cell_key.restype = ctypes.c_int64
             L.orc_axis.argtypes = [pp, ctypes.c_int64, ctypes.c_int64, dp]
             L.orc_axis.restype = None
+            L.orc_mbs_gamma.argtypes = [pp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double]
+            L.orc_mbs_gamma.restype = ctypes.c_double
             L.orc_rotate.argtypes = [dp, ctypes.c_double, dp, dp]
             L.orc_rotate.restype = None
             L.orc_init.argtypes = [pp, ctypes.c_int64, dp, dp]
@@ -159,6 +161,11 @@ def axis(p: Params, t: int, cell: int) -> np.ndarray:
     n = np.zeros(3)
     lib().orc_axis(ctypes.byref(p), int(t), int(cell), _dp(n))
     return n
+
+
+def mbs_gamma(p: Params, t: int, cell: int, shape: float) -> float:
+    """Gamma(shape, 1) draw of the MBS thermostat for cell `cell` in step t (R16)."""
+    return lib().orc_mbs_gamma(ctypes.byref(p), int(t), int(cell), float(shape))
 
 
 def rotate(n, alpha: float, u, v) -> np.ndarray:

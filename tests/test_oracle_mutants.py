@@ -32,6 +32,13 @@ MUTANTS = [
     ("axis not uniform", "double z = 2.0 * orc_u53(w[0]) - 1.0;", "double z = orc_u53(w[0]);", "axis_uniform"),
     ("wall bounce keeps velocity", "for (int d = 0; d < 3; ++d) v[d] = -v[d];",
      "for (int d = 2; d < 3; ++d) v[d] = -v[d];", "bounce_back"),
+    ("gamma shift d without the 1/3", "double d = shape - 1.0 / 3.0;", "double d = shape;", "mbs"),
+    ("gamma cube dropped", "double v = tt * tt * tt;", "double v = tt * tt;", "mbs"),
+    ("gamma squeeze too loose", "if (u < 1.0 - 0.0331 * (x2 * x2)) return d * v;",
+     "if (u < 1.0 - 0.00331 * (x2 * x2)) return d * v;", "mbs"),
+    ("MBS shape from n_c instead of n_c - 1", "orc_mbs_gamma(p, t, c, 1.5 * (double)(nc - 1))",
+     "orc_mbs_gamma(p, t, c, 1.5 * (double)nc)", "mbs"),
+    ("MBS target without kT", "? p->kT * orc_mbs_gamma(", "? orc_mbs_gamma(", "mbs"),
 ]
 
 
@@ -48,7 +55,7 @@ def test_pins_catch_mutant(tmp_path, name, old, new, select):
     env = dict(os.environ, ORACLE_LIB=str(lib))
     tests = [os.path.join(ROOT, "tests", f) for f in
              ("test_oracle_philox.py", "test_oracle_geometry.py", "test_oracle_rotation.py",
-              "test_oracle_step.py", "test_oracle_walls.py")]
+              "test_oracle_step.py", "test_oracle_walls.py", "test_oracle_thermostat.py")]
     res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                           "-k", select + " and not poiseuille and not relaxes"] + tests,
                          cwd=ROOT, env=env, capture_output=True, text=True)
