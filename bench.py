@@ -71,8 +71,9 @@ ALGO_STEP_BYTES_MIXED = 64.0
 # scaled to a launch by the particle count; a kernel changed since its capture has none.
 NCU_TRAFFIC = {("mixed", "collide"): (71.96, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)"),
                ("fp64", "rotate"): (78.47, "profiles/fp64_L128_kernels_full.md (sorted regime, non-re-sort step)")}
-# timed beside an FP64 run: the mixed form at 256^3 and the 256-box ensemble
-FORMS = ("mixed_L256", "batched_256")
+# timed beside an FP64 run: the mixed form at 256^3, the 256-box ensemble and the walled
+# channel with each cell thermostat
+FORMS = ("mixed_L256", "batched_256", "poiseuille_256x64x64", "poiseuille_256x64x64_mbs")
 
 
 def parse():
@@ -290,14 +291,16 @@ def kernel_table(p, mixed, n, C, ktimes, steps):
     return kernels
 
 
-def roofline_of(kernels, mixed, hbm_peak, peak_src, n):
+def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True):
     """The dominant kernel against its bound: HBM bytes (mixed form) or the FP64 pipe (FP64
-    form: measured traffic stays far below HBM; the FP64 instruction count sets the floor)."""
+    form: measured traffic stays far below HBM; the FP64 instruction count sets the floor).
+    `captured`: the kernel variant is the one the ncu traffic figure was taken on (periodic,
+    no force, no thermostat); other variants report no traffic."""
     if mixed:
         dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
         d = kernels[dom]
         per_launch = d["algo_bytes_per_step"] / max(d["launches_per_step"], 1.0)
-        tr = NCU_TRAFFIC.get(("mixed", dom))
+        tr = NCU_TRAFFIC.get(("mixed", dom)) if captured else None
         return {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": d["gbs"] / hbm_peak, "traffic": tr[0] * n if tr else None,
                 "traffic_source": tr[1] if tr else None, "peak_source": peak_src + " (hbm_gbs)",
@@ -388,11 +391,12 @@ def main():
             fval, fms, fl, fkt, _ = timed_steps(abi, torch, dist, fbox, stream, args.form_steps, world)
             fn = fbox.n
             fk = kernel_table(fp, True, fn, fbox.ncell, fkt, args.form_steps)
+            captured = not (getattr(fw, "walls_z", 0) or getattr(fw, "thermostat", 0) or any(getattr(fw, "g", (0.0,))))
             forms[name] = {"value": fval, "unit": UNIT, "steps": args.form_steps, "ms_per_step": fms / args.form_steps,
                            "particles": fn, "cells": fbox.ncell, "boxes": fw.rec.nbox if fens else 1,
                            "speedup_vs_fp64": fval / value, "gpu_launches": fl,
                            "hbm_roofline_frac_step": fval / world * ALGO_STEP_BYTES_MIXED / 1e9 / hbm_peak,
-                           "roofline": roofline_of(fk, True, hbm_peak, peak_src, fn),
+                           "roofline": roofline_of(fk, True, hbm_peak, peak_src, fn, captured=captured),
                            "kernels": {k: {"ms_per_step": v["ms_per_step"], "share": v["share"], "gbs": v["gbs"]}
                                        for k, v in fk.items()}}
             fbox.close()

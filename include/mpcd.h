@@ -61,7 +61,11 @@ typedef struct {
   uint64_t seed;      /* Philox4x64-10 key word 0 for every random draw of this box         */
   int32_t walls_z;    /* 0: periodic in z; 1: bounce-back walls at z = 0 and z = L[2] a,    */
                       /*   virtual particles in cut cells (Lz + 1 cell layers)               */
-  int32_t thermostat; /* 1: rescale each cell's relative kinetic energy to 3/2 (n-1) kT     */
+  int32_t thermostat; /* 0: none; after each collision, rescale each cell's relative kinetic */
+                      /*   energy (n >= 2 real particles) to 1: 3/2 (n-1) kT, or 2: kT G    */
+                      /*   with G ~ Gamma(3/2 (n-1)) drawn per (step, cell) (Maxwell-       */
+                      /*   Boltzmann scaling, Huang et al. 2010; Philox counter             */
+                      /*   (t, cell, 3, attempt), Marsaglia-Tsang).  Other values: ERR_ARG  */
   int32_t resort_k;   /* physically re-order storage by cell every k steps (0: never)       */
   int32_t reserved;   /* must be 0                                                          */
 } mpcd_params;
@@ -151,7 +155,8 @@ int mpcd_timing_read(mpcd_t* h, int32_t nmax, const char** names, double* ms, in
 /* Launch and layout parameters that do not change results (the cell sums are exact, so
  * the order in which particles are stored or visited never matters). */
 typedef struct {
-  int32_t group_target; /* mixed form: mean particles per warp's group of cells (32..224) */
+  int32_t group_target; /* mixed form: mean particles per warp's group of cells (32..224); */
+                        /*   per box at most 24 ppc and 192 - ceil(ppc + 4 sqrt(ppc))     */
   int32_t warps;        /* mixed form: warps per collide block (2 or 4) */
   int32_t resort_k;     /* FP64 form: physical re-sort period in steps (0: never) */
   int32_t reserved;     /* must be 0 */

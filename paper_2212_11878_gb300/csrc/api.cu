@@ -136,7 +136,7 @@ int check_params(const mpcd_params* p, std::string* why) {
     if (!std::isfinite(p->g[d])) return *why = "g must be finite", MPCD_ERR_ARG;
   if (p->walls_z != 0 && p->walls_z != 1) return *why = "walls_z must be 0 or 1", MPCD_ERR_ARG;
   if (p->walls_z && p->g[2] != 0.0) return *why = "g[2] must be 0 with walls in z", MPCD_ERR_ARG;
-  if (p->thermostat != 0 && p->thermostat != 1) return *why = "thermostat must be 0 or 1", MPCD_ERR_ARG;
+  if (p->thermostat < 0 || p->thermostat > 2) return *why = "thermostat must be 0, 1 or 2", MPCD_ERR_ARG;
   if (p->resort_k < 0) return *why = "resort_k must be >= 0", MPCD_ERR_ARG;
   if (p->reserved != 0) return *why = "reserved must be 0", MPCD_ERR_ARG;
   if (p->precision == MPCD_MIXED) {
@@ -362,13 +362,18 @@ int upload_shifts(mpcd_t* h, int64_t t) {
 // tune.group_target particles each) for the current tuning.
 int build_groups(mpcd_t* h) {
   // the fixed part of the group table: per box, ceil(N_b / T_b) groups of T_b records, with
-  // T_b the target (at most 24 cells' worth on average, so groups rarely exceed 32 cells);
-  // k_group_bounds places their cell boundaries every step
+  // T_b the target, at most 24 cells' worth on average (so groups rarely exceed 32 cells) and
+  // at most the stage's kMixCap records less a high quantile of one cell's occupancy
+  // (ppc + 4 sqrt(ppc)): a group overshoots its target by up to one cell, and a group past
+  // kMixCap takes the slower per-cell path.  k_group_bounds places the cell boundaries
+  // every step.
   std::vector<MixGroupSpec> spec;
   for (size_t b = 0; b < h->boxes.size(); ++b) {
     const Geom& g = h->boxes[b];
     const int64_t nb = h->pbase[b + 1] - h->pbase[b];
-    const int64_t tb = std::max<int64_t>(16, std::min<int64_t>(h->tune.group_target, (int64_t)(24.0 * g.ppc)));
+    const int64_t room = kMixCap - static_cast<int64_t>(std::ceil(g.ppc + 4.0 * std::sqrt(g.ppc)));
+    const int64_t tb = std::max<int64_t>(
+        16, std::min<int64_t>({static_cast<int64_t>(h->tune.group_target), static_cast<int64_t>(24.0 * g.ppc), room}));
     const int64_t ng = std::max<int64_t>(1, (nb + tb - 1) / tb);
     for (int64_t k = 0; k < ng; ++k) {
       MixGroupSpec x;

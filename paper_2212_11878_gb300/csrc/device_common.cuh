@@ -1,8 +1,9 @@
 // device_common.cuh -- device helpers shared by the libmpcd kernels: the counter-based
 // Philox4x64-10 generator, exact uniform doubles, the random rotation axis and Box-Muller.
 //
-// Random numbers (axis, shift, initial state, wall particles) all come from Philox4x64-10
-// (Salmon et al., SC'11) keyed by (seed, 0) with counter (a, b, tag, 0), so that every draw
+// Random numbers (axis, shift, initial state, wall particles, thermostat) all come from
+// Philox4x64-10 (Salmon et al., SC'11) keyed by (seed, 0) with counter (a, b, tag, 0) -- the
+// thermostat's rejection loop counts its attempts in the last word -- so that every draw
 // is a pure function of (seed, step, cell) and independent of launch order (the paper's
 // random axis per cell, Sec. 2; random grid shift, Sec. 2 and Listing 1's offset).
 #pragma once
@@ -95,6 +96,33 @@ __device__ __forceinline__ void gauss_pair(uint64_t w0, uint64_t w1, double& g0,
   sincospi(2.0 * unit53(w1), &s, &c);
   g0 = rad * c;
   g1 = rad * s;
+}
+
+// Gamma(shape, 1) variate of a cell for the Maxwell-Boltzmann-scaling thermostat, shape >= 1,
+// by Marsaglia and Tsang's method (ACM TOMS 26(3), 2000): with d = shape - 1/3 and
+// c = 1/sqrt(9 d), attempt k takes a standard normal x (Box-Muller, cosine branch, from words
+// 0 and 1 of Philox counter (t, cell, THERMO, k)) and u in (0, 1] (word 2); with
+// tt = 1 + c x > 0 and v = tt^3 it returns d v when u < 1 - 0.0331 x^4 or
+// log u < x^2 / 2 + d (1 - v + log v).  Every product and sum is rounded on its own (no
+// contraction), so the accept decisions are those of the same arithmetic on the host.  After
+// 64 rejected attempts (probability below 1e-80) it returns d.
+static __device__ __noinline__ double mbs_gamma(uint64_t seed, int64_t t, int64_t cell, double shape) {
+  const double d = __dsub_rn(shape, 1.0 / 3.0);
+  const double c = 1.0 / sqrt(__dmul_rn(9.0, d));
+  for (uint64_t k = 0; k < 64; ++k) {
+    const u64x4 w = philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(cell), kTagThermo, k, seed, 0);
+    const double rad = sqrt(__dmul_rn(-2.0, log(1.0 - unit53(w.x))));
+    const double x = __dmul_rn(rad, cospi(2.0 * unit53(w.y)));
+    const double tt = __dadd_rn(1.0, __dmul_rn(c, x));
+    if (tt <= 0.0) continue;
+    const double v = __dmul_rn(__dmul_rn(tt, tt), tt);
+    const double u = 1.0 - unit53(w.z);
+    const double x2 = __dmul_rn(x, x);
+    if (u < __dsub_rn(1.0, __dmul_rn(0.0331, __dmul_rn(x2, x2)))) return __dmul_rn(d, v);
+    if (log(u) < __dadd_rn(__dmul_rn(0.5, x2), __dmul_rn(d, __dadd_rn(__dsub_rn(1.0, v), log(v)))))
+      return __dmul_rn(d, v);
+  }
+  return d;
 }
 #endif
 

@@ -316,7 +316,12 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
       const double d0 = v0 - u0, d1 = v1 - u1, d2 = v2 - u2;
       K += 0.5 * g.mass * fma(d0, d0, fma(d1, d1, d2 * d2));
     }
-    if (K > 0.0) f = sqrt(1.5 * (double)(n - 1) * g.kT / K);
+    if (K > 0.0) {
+      // R14: relative kinetic energy 3/2 (n - 1) kT; MBS: kT times a Gamma(3/2 (n - 1)) draw
+      const double target = g.thermostat == 2 ? g.kT * mbs_gamma(g.seed, t1, c, 1.5 * (double)(n - 1))
+                                              : 1.5 * (double)(n - 1) * g.kT;
+      f = sqrt(target / K);
+    }
   }
   for (int j = 0; j < n; ++j) {
     const int i = pm[j];

@@ -95,10 +95,26 @@ __device__ __forceinline__ void carry_periodic(float& x, int& c, int L) {
 
 // Ballistic move over dt in cell units (v in length/time), with the body force and, when
 // WALLS, bounce-back at z = 0 and z = Lz (velocity reversed at the crossing time).
-// NEAR: the caller has checked (moves_near) that no coordinate moves by a cell or more, so
-// the carry needs no test; the result is the same as without NEAR.
+// NEAR: the caller has checked (moves_near) that no coordinate moves by a cell or more and,
+// with walls, (stays_inside) that the particle reaches no wall within dt, so the carry needs
+// no test and there is no bounce; the result is the same as without NEAR.
 template <int WALLS, int FORCE, int NEAR = 0>
 __device__ __forceinline__ void stream_mixed(const Geom& g, float f[3], int cc[3], float v[3]) {
+  if (WALLS && NEAR) {
+    // the first pass of the bounce loop below when it finds no wall: tau = dt
+    const float inv_a = static_cast<float>(g.inv_a);
+    const float tau = static_cast<float>(g.dt);
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const float gt = g.g[d] != 0.0 ? static_cast<float>(g.g[d]) : 0.0f;
+      f[d] = fmaf(fmaf(0.5f * gt, tau, v[d]), tau * inv_a, f[d]);
+      v[d] = fmaf(gt, tau, v[d]);
+      carry_near(f[d], cc[d], g.L[d]);
+    }
+    f[2] = fmaf(v[2] * inv_a, tau, f[2]);
+    carry_near(f[2], cc[2], g.L[2]);  // stays in [0, Lz): the wrap never applies
+    return;
+  }
   if (!WALLS && NEAR) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -214,6 +230,29 @@ __device__ __forceinline__ float u53_f32(uint64_t m) {
   const float hi = static_cast<float>(static_cast<uint32_t>(m >> 21));           // exact below 2^24, else RN
   const float lo = static_cast<float>(static_cast<uint32_t>(m & 0x1FFFFFull));   // exact
   return fmaf(hi, 0x1.0p-32f, lo * 0x1.0p-53f);
+}
+
+// Gamma(shape, 1) variate of the Maxwell-Boltzmann-scaling thermostat in FP32: the same
+// Marsaglia-Tsang steps and Philox counters (t, cell, THERMO, k) as the FP64 form, with the
+// uniforms rounded from their 53-bit integers.  Not inlined: it runs once per cell, only in
+// the kernels instantiated for this thermostat (THERMO = 2).
+__device__ __noinline__ float mbs_gamma_f32(uint64_t seed, int64_t t, int64_t cell, float shape) {
+  const float d = shape - (1.0f / 3.0f);
+  const float c = rsqrtf(9.0f * d);
+  for (uint64_t k = 0; k < 64; ++k) {
+    const u64x4 w = philox4x64_10(static_cast<uint64_t>(t), static_cast<uint64_t>(cell), kTagThermo, k, seed, 0);
+    const uint64_t m0 = w.x >> 11, m2 = w.z >> 11;
+    const float u1 = m0 ? u53_f32((1ull << 53) - m0) : 1.0f;  // (0, 1]
+    const float x = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u53_f32(w.y >> 11));
+    const float tt = fmaf(c, x, 1.0f);
+    if (tt <= 0.0f) continue;
+    const float v = tt * tt * tt;
+    const float u = m2 ? u53_f32((1ull << 53) - m2) : 1.0f;
+    const float x2 = x * x;
+    if (u < 1.0f - 0.0331f * (x2 * x2)) return d * v;
+    if (logf(u) < 0.5f * x2 + d * ((1.0f - v) + logf(v))) return d * v;
+  }
+  return d;
 }
 
 // Axis and rotation in FP32 from the same Philox draw as the FP64 form: U = U53(w0), the
@@ -375,14 +414,19 @@ __device__ __forceinline__ float sq3(const float w[3]) { return fmaf(w[0], w[0],
 // exactly; in FP32 the squared lengths drift by about 1e-7, so df = sum(|v-u|^2 - |w|^2) /
 // (2 sum |w|^2): the sum of the small differences is accurate on its own, and the cell's
 // relative kinetic energy is restored to FP32 rounding of the stored velocities.  With the
-// thermostat, df sets it to 3/2 (n - 1) kT instead.  dE: 2^-44 fixed point, Ea: 2^-30.
+// thermostat, df sets it to 3/2 (n - 1) kT instead, or with the Maxwell-Boltzmann-scaling
+// thermostat to kT times a Gamma(3/2 (n - 1)) draw for (step t1, cell).  dE: 2^-44 fixed
+// point, Ea: 2^-30.
 template <int THERMO>
-__device__ __forceinline__ float cell_df(const Geom& g, int n, long long dE, long long Ea, bool ok) {
+__device__ __forceinline__ float cell_df(const Geom& g, int n, long long dE, long long Ea, bool ok, int64_t t1,
+                                         int64_t cell) {
   if (!ok || Ea <= 0) return 0.0f;
   const float ea = ll_to_float(Ea) * 0x1.0p-30f;
-  if (THERMO && n >= 2)
-    return sqrtf(3.0f * static_cast<float>(n - 1) * static_cast<float>(g.kT) / (static_cast<float>(g.mass) * ea)) -
-           1.0f;
+  if (THERMO && n >= 2) {
+    const float dof = THERMO == 2 ? 2.0f * mbs_gamma_f32(g.seed, t1, cell, 1.5f * static_cast<float>(n - 1))
+                                  : 3.0f * static_cast<float>(n - 1);
+    return sqrtf(dof * static_cast<float>(g.kT) / (static_cast<float>(g.mass) * ea)) - 1.0f;
+  }
   return 0.5f * (ll_to_float(dE) * 0x1.0p-44f) / ea;
 }
 
@@ -445,7 +489,7 @@ __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c,
     v.vz(j) = w[2];
     oke &= fx_add<kFixDE>(dE, term) & fx_add<kFixV2>(Ea, sq3(w));
   }
-  const float df = cell_df<THERMO>(g, n, dE, Ea, oke);
+  const float df = cell_df<THERMO>(g, n, dE, Ea, oke, t1, c);
   for (int j = 0; j < n; ++j) {
     v.vx(j) = __fadd_rn(f.u[0], fmaf(df, v.vx(j), v.vx(j)));
     v.vy(j) = __fadd_rn(f.u[1], fmaf(df, v.vy(j), v.vy(j)));
@@ -461,6 +505,15 @@ __device__ __forceinline__ bool moves_near(const Geom& g, const MixRec& r) {
   float m = fmaxf(fabsf(r.vx), fmaxf(fabsf(r.vy), fabsf(r.vz))) * g.dta;  // NaN: not near
   if (FORCE) m += fmaxf(fabsf(g.ha[0]), fmaxf(fabsf(g.ha[1]), fabsf(g.ha[2])));
   return m < 0.99f;
+}
+
+// With walls: true when streaming the record over dt > 0 reaches neither wall, by the same
+// test as the first pass of the bounce loop in stream_mixed (NaN: false).
+__device__ __forceinline__ bool stays_inside(const Geom& g, const MixRec& r) {
+  const int cz = r.cell >> (g.bits[0] + g.bits[1]);
+  const float tau = static_cast<float>(g.dt);
+  const float zrel = fmaf(r.vz * static_cast<float>(g.inv_a), tau, r.oz);
+  return tau > 0.0f && zrel >= -static_cast<float>(cz) && zrel < static_cast<float>(g.L[2] - cz);
 }
 
 // Stream one record from r_{t-1} to r_t in place.
@@ -572,7 +625,8 @@ struct MixWarpStage {
 };
 
 // A group's cells and records; lo / n describe the cell that this lane works on in the
-// per-cell phases (lanes 2j and 2j + 1 share cell j when the group has at most 16 cells).
+// per-cell phases: lanes 4j .. 4j + 3 share cell j when the group has at most 8 cells, lanes
+// 2j and 2j + 1 when it has at most 16, else lane j alone.
 struct Span {
   int64_t c0;
   int box, ncells, lsh;
@@ -597,7 +651,7 @@ __device__ __forceinline__ Span group_span(const int32_t* __restrict__ offset, c
   sp.c0 = d.c0;
   sp.box = d.box;
   sp.ncells = d.ncells;
-  sp.lsh = d.ncells <= 16 ? 1 : 0;
+  sp.lsh = d.ncells <= 8 ? 2 : (d.ncells <= 16 ? 1 : 0);
   const int j = lane >> sp.lsh;
   const int ja = j < d.ncells ? j : d.ncells;
   const int jb = j < d.ncells ? j + 1 : d.ncells;
@@ -822,17 +876,17 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
       const double shz = sh.s[2];                                        // grid of this step
       const int cbase = static_cast<int>(g.cbase);
       const int E = sp.E, E0 = sp.E0;
-      const int lsh = sp.lsh, j = lane >> lsh, p = lane & lsh, step = 1 + lsh;
+      const int lsh = sp.lsh, j = lane >> lsh, p = lane & ((1 << lsh) - 1), step = 1 << lsh;
       const bool cl_live = j < sp.ncells;
       const int lo = sp.lo, n = sp.n;
       const int64_t cl = sp.c0 + j - cbase;  // cell index inside the box
 
       // 1. stream to r_t and split the velocities into fixed-point parts (lane = record);
       //    tag records with their cell and draw the rotation (lane = cell)
-      bool near = !WALLS;
+      bool near = true;
 #pragma unroll
       for (int i = 0; i < kPer; ++i)
-        near = near & moves_near<FORCE>(g, r[i]);
+        near = near & moves_near<FORCE>(g, r[i]) & (!WALLS || stays_inside(g, r[i]));
       unsigned badm = __all_sync(0xffffffffu, near) ? stream_split<WALLS, FORCE, 1, MOMENTS>(g, gbox, r, st, E, lane)
                                                      : stream_split<WALLS, FORCE, 0, MOMENTS>(g, gbox, r, st, E, lane);
       for (int k = p; k < n; k += step) st.seg[lo + k] = static_cast<uint8_t>(j);
@@ -869,11 +923,11 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
             ls[c] += v.y;
           }
         }
-        if (lsh) {
+        for (int m = 1; m < step; m <<= 1) {  // warp-uniform: lsh is the group's
 #pragma unroll
           for (int c = 0; c < NQ; ++c) {
-            hs[c] += __shfl_xor_sync(0xffffffffu, hs[c], 1);
-            ls[c] += __shfl_xor_sync(0xffffffffu, ls[c], 1);
+            hs[c] += __shfl_xor_sync(0xffffffffu, hs[c], m);
+            ls[c] += __shfl_xor_sync(0xffffffffu, ls[c], m);
           }
         }
 #pragma unroll
@@ -947,18 +1001,18 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
             ha += a.x;
             la += a.y;
           }
-        if (lsh) {
-          hd += __shfl_xor_sync(0xffffffffu, hd, 1);
-          ld += __shfl_xor_sync(0xffffffffu, ld, 1);
-          ha += __shfl_xor_sync(0xffffffffu, ha, 1);
-          la += __shfl_xor_sync(0xffffffffu, la, 1);
+        for (int m = 1; m < step; m <<= 1) {
+          hd += __shfl_xor_sync(0xffffffffu, hd, m);
+          ld += __shfl_xor_sync(0xffffffffu, ld, m);
+          ha += __shfl_xor_sync(0xffffffffu, ha, m);
+          la += __shfl_xor_sync(0xffffffffu, la, m);
         }
         if (rot && p == 0)
-          st.cf[j][3] = cell_df<THERMO>(g, n, fix_join(hd, ld), fix_join(ha, la), st.bad[1][j] == 0);
+          st.cf[j][3] = cell_df<THERMO>(g, n, fix_join(hd, ld), fix_join(ha, la), st.bad[1][j] == 0, t1, cl);
       }
       __syncwarp();
       // 5. new velocities; keys and counts of the next step; write-out in cell order
-      near = !WALLS;
+      near = true;
 #pragma unroll
       for (int i = 0; i < kPer; ++i) {
         const int e = lane + 32 * i;
@@ -973,7 +1027,7 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
           r[i].vx = rot ? nx : r[i].vx;
           r[i].vy = rot ? ny : r[i].vy;
           r[i].vz = rot ? nz : r[i].vz;
-          near = near & moves_near<FORCE>(g, r[i]);
+          near = near & moves_near<FORCE>(g, r[i]) & (!WALLS || stays_inside(g, r[i]));
         }
       }
       if (__all_sync(0xffffffffu, near))
@@ -1290,8 +1344,12 @@ cudaError_t launch_collide_t(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* c
 template <int WARPS>
 cudaError_t launch_collide_w(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st,
                              bool prepare, int sel_override = -1) {
+  // 0-11: (walls | force | neither) x (fixed-target thermostat or none) x moments;
+  // 12-17: (walls | force | neither) x moments with the Maxwell-Boltzmann-scaling thermostat
+  const int kind = mb.walls ? 2 : (mb.force ? 1 : 0);
   const int sel = sel_override >= 0 ? sel_override
-                                    : (mb.walls ? 8 : (mb.force ? 4 : 0)) | (mb.thermostat ? 2 : 0) | (moments ? 1 : 0);
+                  : mb.thermostat == 2 ? 12 + 2 * kind + (moments ? 1 : 0)
+                                       : 4 * kind | (mb.thermostat ? 2 : 0) | (moments ? 1 : 0);
   switch (sel) {
     case 0: return launch_collide_t<WARPS, 0, 0, 0, 0>(mb, b, s, ctl, st, prepare);
     case 1: return launch_collide_t<WARPS, 0, 0, 0, 1>(mb, b, s, ctl, st, prepare);
@@ -1304,7 +1362,13 @@ cudaError_t launch_collide_w(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* c
     case 8: return launch_collide_t<WARPS, 1, 1, 0, 0>(mb, b, s, ctl, st, prepare);
     case 9: return launch_collide_t<WARPS, 1, 1, 0, 1>(mb, b, s, ctl, st, prepare);
     case 10: return launch_collide_t<WARPS, 1, 1, 1, 0>(mb, b, s, ctl, st, prepare);
-    default: return launch_collide_t<WARPS, 1, 1, 1, 1>(mb, b, s, ctl, st, prepare);
+    case 11: return launch_collide_t<WARPS, 1, 1, 1, 1>(mb, b, s, ctl, st, prepare);
+    case 12: return launch_collide_t<WARPS, 0, 0, 2, 0>(mb, b, s, ctl, st, prepare);
+    case 13: return launch_collide_t<WARPS, 0, 0, 2, 1>(mb, b, s, ctl, st, prepare);
+    case 14: return launch_collide_t<WARPS, 0, 1, 2, 0>(mb, b, s, ctl, st, prepare);
+    case 15: return launch_collide_t<WARPS, 0, 1, 2, 1>(mb, b, s, ctl, st, prepare);
+    case 16: return launch_collide_t<WARPS, 1, 1, 2, 0>(mb, b, s, ctl, st, prepare);
+    default: return launch_collide_t<WARPS, 1, 1, 2, 1>(mb, b, s, ctl, st, prepare);
   }
 }
 
@@ -1322,7 +1386,7 @@ cudaError_t prepare_collide_mixed() {
   MixBatch mb{};
   MixBufs b{};
   MixScratch s{};
-  for (int sel = 0; sel < 12 && e == cudaSuccess; ++sel) {
+  for (int sel = 0; sel < 18 && e == cudaSuccess; ++sel) {
     e = launch_collide_w<2>(mb, b, s, nullptr, false, nullptr, true, sel);
     if (e == cudaSuccess) e = launch_collide_w<4>(mb, b, s, nullptr, false, nullptr, true, sel);
   }

@@ -12,7 +12,7 @@ namespace mpcd {
 struct alignas(16) Geom {
   int32_t L[3];
   int32_t walls;       // bounce-back walls in z
-  int32_t thermostat;  // cell-level rescale of the relative kinetic energy
+  int32_t thermostat;  // cell-level rescale of the relative kinetic energy: 1 fixed, 2 MBS
   int32_t resort_k;    // physical re-sort period (0: never)
   int32_t pow2a;       // a is a power of two: (r - s) * (1/a) == (r - s) / a exactly
   int32_t force;       // any g component non-zero

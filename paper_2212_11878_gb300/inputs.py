@@ -71,6 +71,10 @@ WORKLOADS = {
                                      steps=20000, precision="mixed", resort_k=1, walls_z=1,
                                      g=(1e-3, 0.0, 0.0), thermostat=1,
                                      notes="bounce-back walls in z, body force along x"),
+    "poiseuille_256x64x64_mbs": Workload("poiseuille_256x64x64_mbs", (256, 64, 64), ppc=20.0, seed=BASE_SEED + 3,
+                                         steps=20000, precision="mixed", resort_k=1, walls_z=1,
+                                         g=(1e-3, 0.0, 0.0), thermostat=2,
+                                         notes="the channel with the Maxwell-Boltzmann-scaling cell thermostat"),
 }
 
 

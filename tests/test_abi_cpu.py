@@ -87,6 +87,7 @@ def test_version_string(libpath):
     dict(L=(0, 4, 4)), dict(a=0.0), dict(a=float("nan")), dict(dt=-0.1), dict(kT=0.0), dict(mass=-1.0),
     dict(ppc=-1.0), dict(walls_z=2), dict(walls_z=1, g=(0.0, 0.0, 0.1)), dict(resort_k=-1), dict(precision=7),
     dict(alpha=float("inf")), dict(L=(4096, 4096, 4096)), dict(precision=1, L=(1025, 1025, 1025)),
+    dict(thermostat=3), dict(thermostat=-1),
 ])
 def test_invalid_params_rejected_on_host(libpath, bad):
     p = abi.make_params(**{**dict(L=(4, 4, 4)), **bad})

@@ -47,6 +47,9 @@ CASES = {
     "walls": dict(L=(6, 5, 8), walls_z=1, g=(0.01, 0.0, 0.0)),
     "walls_thermo": dict(L=(6, 5, 8), walls_z=1, g=(0.02, 0.0, 0.0), thermostat=1, ppc=15),
     "thermo_periodic": dict(L=(6, 6, 6), thermostat=1, kT=0.8),
+    "mbs_periodic": dict(L=(7, 6, 6), thermostat=2, kT=0.8),
+    "walls_mbs": dict(L=(6, 5, 8), walls_z=1, g=(0.02, 0.0, 0.0), thermostat=2, ppc=15),
+    "mbs_sparse": dict(L=(8, 8, 8), thermostat=2, ppc=2.5),
 }
 
 

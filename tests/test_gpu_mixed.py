@@ -69,10 +69,16 @@ def test_init_matches_oracle_to_fp32(orc):
 
 @pytest.mark.parametrize("case", [dict(L=(12, 10, 8)), dict(L=(9, 9, 9), a=0.5, dt=0.2),
                                   dict(L=(8, 8, 8), g=(0.01, 0.02, -0.01)), dict(L=(8, 7, 6), ppc=25),
-                                  dict(L=(10, 9, 8), fast=0.02), dict(L=(9, 8, 7), g=(0.02, 0.0, 0.01), fast=0.01)])
+                                  dict(L=(10, 9, 8), fast=0.02), dict(L=(9, 8, 7), g=(0.02, 0.0, 0.01), fast=0.01),
+                                  dict(L=(10, 9, 8), thermostat=1, kT=1.3), dict(L=(11, 9, 8), thermostat=2, kT=1.3),
+                                  dict(L=(9, 8, 10), walls_z=1, g=(0.02, 0.01, 0.0)),
+                                  dict(L=(8, 9, 12), walls_z=1, g=(0.01, 0.0, 0.0), thermostat=2, ppc=15),
+                                  dict(L=(8, 8, 6), walls_z=1, g=(0.02, 0.0, 0.0), dt=0.3, fast=0.02)])
 def test_one_step_against_fp64_oracle(orc, case):
     """`fast`: that fraction of the particles moves 0.6 to 3 cells in the step, so that the
-    warps holding them take the general carry path instead of the one-cell one."""
+    warps holding them take the general carry path instead of the one-cell one.  With walls,
+    warps whose particles all stay clear of the walls take the same one-cell path; the others
+    bounce in the general loop."""
     case = dict(case)
     fast = case.pop("fast", 0.0)
     p = mixed_params(seed=5, **case)
@@ -94,7 +100,7 @@ def test_one_step_against_fp64_oracle(orc, case):
     ref = orc.step(oracle_params(orc, p), st, debug=True)
     rr, vr = st.by_id()
     # the sort, bit-exact against the GPU's own keys
-    C = int(np.prod(L))
+    C = int(np.prod(L)) if not p.walls_z else L[0] * L[1] * (L[2] + 1)
     keys = dbg["keys"]
     assert np.array_equal(dbg["counts"], np.bincount(keys, minlength=C))
     assert dbg["offsets"][0] == 0 and np.array_equal(dbg["offsets"][1:], np.cumsum(dbg["counts"]))
@@ -139,6 +145,32 @@ def test_cell_conservation():
     assert np.all(np.abs(P - mom[:, 1:4]).max(axis=1) <= 2e-6 * scale)
     assert np.all(np.abs(E - mom[:, 4]) <= 2e-6 * np.maximum(mom[:, 4], 1e-30))
     assert np.array_equal(mom[:, 0], np.bincount(keys, minlength=C).astype(float))
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_mbs_thermostat_gives_canonical_cell_energies(precision):
+    """With the Maxwell-Boltzmann-scaling thermostat each cell's kinetic energy relative to
+    its centre of mass, after the collision, is kT times a Gamma(3/2 (n_c - 1)) variate: mapped
+    through that CDF it is uniform on [0, 1], pooled over all cells and steps."""
+    L = (16, 16, 16)
+    kT = 1.7
+    p = abi.make_params(L, precision=precision, thermostat=2, kT=kT, seed=41)
+    C = int(np.prod(L))
+    pits = []
+    with abi.Box(p) as box:
+        for _ in range(3):
+            box.step(1)
+            dbg = box.debug_sort()
+            r, v = box.state()
+            keys = np.empty(box.n, np.int64)
+            keys[dbg["ids"]] = dbg["keys"]
+            cnt = np.bincount(keys, minlength=C)
+            u = np.stack([np.bincount(keys, weights=v[:, d], minlength=C) for d in range(3)], axis=1)
+            u /= np.maximum(cnt, 1)[:, None]
+            rel = 0.5 * np.bincount(keys, weights=((v - u[keys]) ** 2).sum(axis=1), minlength=C)
+            ok = cnt >= 2
+            pits.append(stats.gamma.cdf(rel[ok] / kT, 1.5 * (cnt[ok] - 1)))
+    assert stats.kstest(np.concatenate(pits), "uniform").pvalue > 1e-3
 
 
 def test_energy_and_momentum_do_not_drift():
