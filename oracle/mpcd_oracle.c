@@ -340,7 +340,7 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
 
     if (p->thermostat && nc >= 2) {
       /* R14: rescale the relative velocities so the cell's relative kinetic energy is
-       * (3/2)(n_c - 1) kT; R16 (MBS): kT times a Gamma(3/2 (n_c - 1)) draw instead. */
+       * (3/2)(n_c - 1) kT; R22 (MBS): kT times a Gamma(3/2 (n_c - 1)) draw instead. */
       double target = p->thermostat == 2 ? p->kT * orc_mbs_gamma(p, t, c, 1.5 * (double)(nc - 1))
                                          : 1.5 * (double)(nc - 1) * p->kT;
       double K = 0.0;

@@ -28,7 +28,7 @@
  *   R12 cells with fewer than two particles (real + virtual) are left unchanged.
  *   R13 bounce-back walls at z = 0 and z = Lz*a, virtual particles in cut cells.
  *   R14 optional cell-level velocity-rescaling thermostat.
- *   R16 optional Maxwell-Boltzmann-scaling (MBS) thermostat: the target of the R14 rescale
+ *   R22 optional Maxwell-Boltzmann-scaling (MBS) thermostat: the target of the R14 rescale
  *       is drawn per cell from the Gamma distribution of the relative kinetic energy of
  *       3(n_c - 1) degrees of freedom (Huang et al. 2010, cited in Sec. 2 and Sec. 4),
  *       with Marsaglia and Tsang's method (ACM TOMS 26(3), 2000).
@@ -57,7 +57,7 @@ typedef struct {
   uint64_t seed;      /* Philox key word 0 */
   int32_t walls_z;    /* 0: periodic in z; 1: bounce-back walls at z = 0 and z = Lz*a */
   int32_t thermostat; /* 0: none; 1: cell-level rescale of the relative kinetic energy to
-                         * 3/2 (n_c - 1) kT; 2: to kT times a Gamma(3/2 (n_c - 1)) draw (R16) */
+                         * 3/2 (n_c - 1) kT; 2: to kT times a Gamma(3/2 (n_c - 1)) draw (R22) */
 } orc_params;
 
 /* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): out = bijection(ctr) under key. */
@@ -72,7 +72,7 @@ void orc_shift(const orc_params* p, int64_t t, double s[3]);
 int64_t orc_cell_key(const orc_params* p, const double r[3], const double s[3]);
 /* Random rotation axis of cell `cell` in step t, uniform on the unit sphere (R9). */
 void orc_axis(const orc_params* p, int64_t t, int64_t cell, double n[3]);
-/* Gamma(shape, 1) variate of cell `cell` in step t for the MBS thermostat (R16), shape >= 1:
+/* Gamma(shape, 1) variate of cell `cell` in step t for the MBS thermostat (R22), shape >= 1:
  * Marsaglia-Tsang, attempt k on Philox counter (t, cell, THERMO, k); at most 64 attempts,
  * after which it returns shape - 1/3. */
 double orc_mbs_gamma(const orc_params* p, int64_t t, int64_t cell, double shape);

@@ -164,7 +164,7 @@ def axis(p: Params, t: int, cell: int) -> np.ndarray:
 
 
 def mbs_gamma(p: Params, t: int, cell: int, shape: float) -> float:
-    """Gamma(shape, 1) draw of the MBS thermostat for cell `cell` in step t (R16)."""
+    """Gamma(shape, 1) draw of the MBS thermostat for cell `cell` in step t (R22)."""
     return lib().orc_mbs_gamma(ctypes.byref(p), int(t), int(cell), float(shape))
 
 

@@ -1,4 +1,4 @@
-"""Pins for the oracle's Maxwell-Boltzmann-scaling (MBS) thermostat (reading R16).
+"""Pins for the oracle's Maxwell-Boltzmann-scaling (MBS) thermostat (reading R22).
 
 The thermostat rescales each cell's velocities relative to the cell's centre of mass so that
 their kinetic energy becomes kT times a Gamma(3/2 (n_c - 1)) draw: the canonical distribution
