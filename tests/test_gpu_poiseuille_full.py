@@ -2,7 +2,7 @@
 (20,971,520 particles), g = 1e-3 along x, thermostat, mixed form; 20,000 steps from rest,
 with the velocity profile averaged over steps 10,001-20,000 in 64 z-bins.
 
-Opt-in (about a minute on one GB300): set MPCD_LONG=1.  The profile comes from the per-cell
+Opt-in (about half a minute per thermostat on one GB300): set MPCD_LONG=1.  The profile comes from the per-cell
 moments of one step in fifty (each cut-cell layer's mean velocity, binned by the centre of
 its part of the channel), not from reading the particles back.
 
@@ -25,8 +25,10 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not os.environ.get("MPCD_LONG"), reason="long run: set MPCD_LONG=1")]
 
 
-def test_poiseuille_full_channel():
-    w = inputs.WORKLOADS["poiseuille_256x64x64"]
+@pytest.mark.parametrize("name", ["poiseuille_256x64x64", "poiseuille_256x64x64_mbs"])
+def test_poiseuille_full_channel(name):
+    """Both cell thermostats: the fixed-target rescale and Maxwell-Boltzmann scaling."""
+    w = inputs.WORKLOADS[name]
     p = abi.params_from_workload(w)
     Lx, Ly, H = w.L
     g, n_bar, dt, alpha = w.g[0], w.ppc, w.dt, math.radians(w.alpha_deg)
@@ -65,7 +67,7 @@ def test_poiseuille_full_channel():
            "wall_velocity_over_vmax": float(coef[0] / vmax),
            "rms_vs_parabola_over_vmax": float(np.sqrt(((prof - g / (2 * nu) * z * (H - z) * (1 - deficit)) ** 2).mean())
                                               / vmax)}
-    report("poiseuille_256x64x64_full", out)
+    report(name + "_full", out)
     assert abs(out["center_over_vmax"] - (1 - deficit)) < 0.05
     assert abs(out["nu_fit_over_theory"] - 1 / (1 - deficit)) < 0.08
     assert abs(out["wall_velocity_over_vmax"]) < 0.05
