@@ -153,6 +153,30 @@ double orc_mbs_gamma(const orc_params* p, int64_t t, int64_t cell, double shape)
   return d;
 }
 
+void orc_cell_local(const orc_params* p, const double r[3], const double s[3], double l[3]) {
+  for (int d = 0; d < 3; ++d) {
+    double q = (r[d] - s[d]) / p->a;
+    l[d] = q - floor(q);
+  }
+}
+
+static void cross(const double a[3], const double b[3], double out[3]) {
+  out[0] = a[1] * b[2] - a[2] * b[1];
+  out[1] = a[2] * b[0] - a[0] * b[2];
+  out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Angular momentum about the cell's centre of mass, m sum rho_i x v_i (R23). */
+static void cell_angular_momentum(const orc_params* p, const double* rho, const double* v, const int32_t* perm,
+                                  int32_t j0, int32_t j1, double L[3]) {
+  L[0] = L[1] = L[2] = 0.0;
+  for (int32_t j = j0; j < j1; ++j) {
+    double c[3];
+    cross(&rho[3 * (int64_t)(j - j0)], &v[3 * (int64_t)perm[j]], c);
+    for (int d = 0; d < 3; ++d) L[d] += p->mass * c[d];
+  }
+}
+
 void orc_rotate(const double n[3], double alpha, const double u[3], double v[3]) {
   double d[3], cr[3], out[3];
   for (int k = 0; k < 3; ++k) d[k] = v[k] - u[k];               /* relative velocity */
@@ -262,6 +286,7 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
   for (int d = 0; d < 3; ++d)
     if (p->L[d] < 1) return -1;
   if (p->walls_z && p->g[2] != 0.0) return -1;
+  if (p->angular && p->walls_z) return -1; /* R23 */
   int64_t C = orc_num_cells(p);
   if (C > INT32_MAX || n > INT32_MAX) return -1;
 
@@ -270,8 +295,9 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
   int32_t* off = (int32_t*)malloc(sizeof(int32_t) * (size_t)(C + 1));
   int32_t* cur = (int32_t*)malloc(sizeof(int32_t) * (size_t)C);
   int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-  if (!key || !cnt || !off || !cur || !perm) {
-    free(key); free(cnt); free(off); free(cur); free(perm);
+  double* rho = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1)); /* R23, per cell */
+  if (!key || !cnt || !off || !cur || !perm || !rho) {
+    free(key); free(cnt); free(off); free(cur); free(perm); free(rho);
     return -2;
   }
 
@@ -336,6 +362,23 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
     for (int d = 0; d < 3; ++d) u[d] = P[d] / M; /* R7 */
     double ax[3];
     orc_axis(p, t, c, ax);
+
+    /* R23: positions relative to the cell's centre of mass and the angular momentum about it
+     * before the collision */
+    double Lb[3] = {0.0, 0.0, 0.0};
+    if (p->angular) {
+      double mean[3] = {0.0, 0.0, 0.0};
+      for (int32_t j = off[c]; j < off[c + 1]; ++j) {
+        double* l = &rho[3 * (int64_t)(j - off[c])];
+        orc_cell_local(p, &r[3 * (int64_t)perm[j]], s, l);
+        for (int d = 0; d < 3; ++d) mean[d] += l[d];
+      }
+      for (int d = 0; d < 3; ++d) mean[d] /= (double)nc;
+      for (int32_t j = off[c]; j < off[c + 1]; ++j)
+        for (int d = 0; d < 3; ++d) rho[3 * (int64_t)(j - off[c]) + d] = p->a * (rho[3 * (int64_t)(j - off[c]) + d] - mean[d]);
+      cell_angular_momentum(p, rho, v, perm, off[c], off[c + 1], Lb);
+    }
+
     for (int32_t j = off[c]; j < off[c + 1]; ++j) orc_rotate(ax, p->alpha, u, &v[3 * (int64_t)perm[j]]);
 
     if (p->thermostat && nc >= 2) {
@@ -356,6 +399,57 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
         }
       }
     }
+
+    if (p->angular) {
+      /* R23: omega = I^-1 (L_before - L_after) with I = m sum (|rho|^2 1 - rho rho^T); then
+       * v_i += omega x rho_i, which keeps the cell's momentum (sum rho_i = 0) and restores
+       * its angular momentum (sum m rho_i x (omega x rho_i) = I omega). */
+      double La[3], dL[3], I[3][3] = {{0.0}}, rr = 0.0;
+      cell_angular_momentum(p, rho, v, perm, off[c], off[c + 1], La);
+      for (int d = 0; d < 3; ++d) dL[d] = Lb[d] - La[d];
+      for (int32_t j = off[c]; j < off[c + 1]; ++j) {
+        const double* q = &rho[3 * (int64_t)(j - off[c])];
+        double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        rr += q2;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) I[a][b] += p->mass * ((a == b ? q2 : 0.0) - q[a] * q[b]);
+      }
+      double w[3] = {0.0, 0.0, 0.0};
+      int apply = 0;
+      if (nc == 2) {
+        /* two particles: rho_2 = -rho_1, I = m rr (1 - e e^T) with e = rho_1/|rho_1|; the
+         * change of L is normal to e, where I acts as m rr */
+        double e2 = rr > 0.0 ? 2.0 / rr : 0.0; /* 1/|rho_1|^2 */
+        const double* q = &rho[0];
+        double along = (q[0] * dL[0] + q[1] * dL[1] + q[2] * dL[2]) * e2;
+        if (rr > 0.0) {
+          for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q[d]) / (p->mass * rr);
+          apply = 1;
+        }
+      } else {
+        /* the inverse by cofactors */
+        double cof[3][3];
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) {
+            int a1 = (a + 1) % 3, a2 = (a + 2) % 3, b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+            cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a2][b1];
+          }
+        double det = I[0][0] * cof[0][0] + I[0][1] * cof[0][1] + I[0][2] * cof[0][2];
+        double tr = (I[0][0] + I[1][1] + I[2][2]) / 3.0;
+        if (det > 1e-12 * tr * tr * tr) {
+          for (int a = 0; a < 3; ++a) /* I symmetric: inverse = cof^T / det = cof / det */
+            w[a] = (cof[a][0] * dL[0] + cof[a][1] * dL[1] + cof[a][2] * dL[2]) / det;
+          apply = 1;
+        }
+      }
+      if (apply)
+        for (int32_t j = off[c]; j < off[c + 1]; ++j) {
+          double corr[3];
+          cross(w, &rho[3 * (int64_t)(j - off[c])], corr);
+          double* vi = &v[3 * (int64_t)perm[j]];
+          for (int d = 0; d < 3; ++d) vi[d] += corr[d];
+        }
+    }
   }
 
   if (keys_out) memcpy(keys_out, key, sizeof(int32_t) * (size_t)n);
@@ -364,6 +458,7 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
   if (perm_out) memcpy(perm_out, perm, sizeof(int32_t) * (size_t)n);
   if (shift_out)
     for (int d = 0; d < 3; ++d) shift_out[d] = s[d];
+  free(rho);
 
   /* 8. every k steps the storage itself is put into cell order (Listing 1, permute) */
   if (p->resort_k > 0 && t % p->resort_k == 0 && n > 0) {

@@ -32,6 +32,14 @@
  *       is drawn per cell from the Gamma distribution of the relative kinetic energy of
  *       3(n_c - 1) degrees of freedom (Huang et al. 2010, cited in Sec. 2 and Sec. 4),
  *       with Marsaglia and Tsang's method (ACM TOMS 26(3), 2000).
+ *   R23 optional angular-momentum-conserving collision (the variants Sec. 2 mentions, from
+ *       the Gompper et al. review it cites): after the rotation (and the thermostat), every
+ *       member of a cell gets omega x rho_i, rho_i its position relative to the cell's centre
+ *       of mass and omega = I^-1 (L_before - L_after), I the cell's inertia tensor; cells of
+ *       two particles use I's pseudo-inverse, cells whose inertia tensor is singular
+ *       otherwise are left uncorrected.  Positions within a cell are taken on the shifted
+ *       grid (the fractional part of (r - s)/a), so a cell cut by the periodic boundary is
+ *       whole.  Not with walls: virtual particles have no positions.
  */
 #ifndef MPCD_ORACLE_H
 #define MPCD_ORACLE_H
@@ -58,6 +66,7 @@ typedef struct {
   int32_t walls_z;    /* 0: periodic in z; 1: bounce-back walls at z = 0 and z = Lz*a */
   int32_t thermostat; /* 0: none; 1: cell-level rescale of the relative kinetic energy to
                          * 3/2 (n_c - 1) kT; 2: to kT times a Gamma(3/2 (n_c - 1)) draw (R22) */
+  int32_t angular;    /* 1: angular-momentum-conserving collision (R23); periodic boxes only */
 } orc_params;
 
 /* Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): out = bijection(ctr) under key. */
@@ -76,6 +85,9 @@ void orc_axis(const orc_params* p, int64_t t, int64_t cell, double n[3]);
  * Marsaglia-Tsang, attempt k on Philox counter (t, cell, THERMO, k); at most 64 attempts,
  * after which it returns shape - 1/3. */
 double orc_mbs_gamma(const orc_params* p, int64_t t, int64_t cell, double shape);
+/* Position of r inside its cell on the grid shifted by s, in cell units: the fractional
+ * part of (r - s)/a per axis (R23). */
+void orc_cell_local(const orc_params* p, const double r[3], const double s[3], double l[3]);
 /* v <- u + rotation of (v - u) by alpha about unit axis n (Sec. 2, parts (ii)-(iii)). */
 void orc_rotate(const double n[3], double alpha, const double u[3], double v[3]);
 

@@ -59,11 +59,12 @@ class Params(ctypes.Structure):
         ("seed", ctypes.c_uint64),
         ("walls_z", ctypes.c_int32),
         ("thermostat", ctypes.c_int32),
+        ("angular", ctypes.c_int32),
     ]
 
 
 def make_params(L, a=1.0, dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, ppc=10.0, seed=20221211,
-                resort_k=0, walls_z=0, g=(0.0, 0.0, 0.0), thermostat=0, alpha=None) -> Params:
+                resort_k=0, walls_z=0, g=(0.0, 0.0, 0.0), thermostat=0, alpha=None, angular=0) -> Params:
     p = Params()
     if isinstance(L, int):
         L = (L, L, L)
@@ -79,6 +80,7 @@ def make_params(L, a=1.0, dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, ppc=10.0, s
     p.seed = int(seed)
     p.walls_z = int(walls_z)
     p.thermostat = int(thermostat)
+    p.angular = int(angular)
     return p
 
 
@@ -107,6 +109,8 @@ def lib():
             L.orc_axis.restype = None
             L.orc_mbs_gamma.argtypes = [pp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double]
             L.orc_mbs_gamma.restype = ctypes.c_double
+            L.orc_cell_local.argtypes = [pp, dp, dp, dp]
+            L.orc_cell_local.restype = None
             L.orc_rotate.argtypes = [dp, ctypes.c_double, dp, dp]
             L.orc_rotate.restype = None
             L.orc_init.argtypes = [pp, ctypes.c_int64, dp, dp]
@@ -166,6 +170,15 @@ def axis(p: Params, t: int, cell: int) -> np.ndarray:
 def mbs_gamma(p: Params, t: int, cell: int, shape: float) -> float:
     """Gamma(shape, 1) draw of the MBS thermostat for cell `cell` in step t (R22)."""
     return lib().orc_mbs_gamma(ctypes.byref(p), int(t), int(cell), float(shape))
+
+
+def cell_local(p: Params, r, s) -> np.ndarray:
+    """Position of r inside its cell of the grid shifted by s, in cell units (R23)."""
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.float64).reshape(3))
+    s = np.ascontiguousarray(np.asarray(s, dtype=np.float64).reshape(3))
+    out = np.zeros(3)
+    lib().orc_cell_local(ctypes.byref(p), _dp(r), _dp(s), _dp(out))
+    return out
 
 
 def rotate(n, alpha: float, u, v) -> np.ndarray:

@@ -39,6 +39,16 @@ MUTANTS = [
     ("MBS shape from n_c instead of n_c - 1", "orc_mbs_gamma(p, t, c, 1.5 * (double)(nc - 1))",
      "orc_mbs_gamma(p, t, c, 1.5 * (double)nc)", "mbs"),
     ("MBS target without kT", "? p->kT * orc_mbs_gamma(", "? orc_mbs_gamma(", "mbs"),
+    ("angular correction sign flipped", "for (int d = 0; d < 3; ++d) vi[d] += corr[d];",
+     "for (int d = 0; d < 3; ++d) vi[d] -= corr[d];", "angular or omega or two_particle"),
+    ("inertia tensor without the |rho|^2 term", "I[a][b] += p->mass * ((a == b ? q2 : 0.0) - q[a] * q[b]);",
+     "I[a][b] += p->mass * (0.0 - q[a] * q[b]);", "angular or omega or two_particle"),
+    ("positions not taken about the centre of mass", "= p->a * (rho[3 * (int64_t)(j - off[c]) + d] - mean[d]);",
+     "= p->a * (rho[3 * (int64_t)(j - off[c]) + d] - 0.0 * mean[d]);", "angular or omega or two_particle"),
+    ("two-particle omega off by two", "w[d] = (dL[d] - along * q[d]) / (p->mass * rr);",
+     "w[d] = (dL[d] - along * q[d]) / (2.0 * p->mass * rr);", "angular or omega or two_particle"),
+    ("cofactor indices swapped", "cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a2][b1];",
+     "cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a1][b2];", "angular or omega or two_particle"),
 ]
 
 
@@ -55,7 +65,8 @@ def test_pins_catch_mutant(tmp_path, name, old, new, select):
     env = dict(os.environ, ORACLE_LIB=str(lib))
     tests = [os.path.join(ROOT, "tests", f) for f in
              ("test_oracle_philox.py", "test_oracle_geometry.py", "test_oracle_rotation.py",
-              "test_oracle_step.py", "test_oracle_walls.py", "test_oracle_thermostat.py")]
+              "test_oracle_step.py", "test_oracle_walls.py", "test_oracle_thermostat.py",
+              "test_oracle_angular.py")]
     res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                           "-k", select + " and not poiseuille and not relaxes"] + tests,
                          cwd=ROOT, env=env, capture_output=True, text=True)
