@@ -22,7 +22,8 @@ MUTANTS = [
     ("mass weight dropped", "P[d] += m * vi[d];", "P[d] += vi[d];", "closed_form or conserves"),
     ("key index order swapped", "return c[0] + (int64_t)p->L[0] * (c[1] + (int64_t)p->L[1] * c[2]);",
      "return c[1] + (int64_t)p->L[1] * (c[0] + (int64_t)p->L[0] * c[2]);", "brute_force or face_point"),
-    ("shift sign flipped", "double q = (r[d] - s[d]) / p->a;", "double q = (r[d] + s[d]) / p->a;",
+    ("shift sign flipped", "double q = (r[d] - s[d]) / p->a;\n    int64_t k = (int64_t)floor(q);",
+     "double q = (r[d] + s[d]) / p->a;\n    int64_t k = (int64_t)floor(q);",
      "brute_force or face_point"),
     ("perm not stable", "for (int64_t i = 0; i < n; ++i) perm[cur[key[i]]++] = (int32_t)i;",
      "for (int64_t i = n - 1; i >= 0; --i) perm[cur[key[i]]++] = (int32_t)i;", "stable_argsort"),
