@@ -71,9 +71,10 @@ ALGO_STEP_BYTES_MIXED = 64.0
 # scaled to a launch by the particle count; a kernel changed since its capture has none.
 NCU_TRAFFIC = {("mixed", "collide"): (71.96, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)"),
                ("fp64", "rotate"): (78.47, "profiles/fp64_L128_kernels_full.md (sorted regime, non-re-sort step)")}
-# timed beside an FP64 run: the mixed form at 256^3, the 256-box ensemble and the walled
-# channel with each cell thermostat
-FORMS = ("mixed_L256", "batched_256", "poiseuille_256x64x64", "poiseuille_256x64x64_mbs")
+# timed beside an FP64 run: the mixed form at 256^3, the 256-box ensemble, the walled
+# channel with each cell thermostat, and the angular-momentum-conserving collision
+FORMS = ("mixed_L256", "batched_256", "poiseuille_256x64x64", "poiseuille_256x64x64_mbs", "fp64_L128_angular",
+         "mixed_L128_angular")
 
 
 def parse():
@@ -390,13 +391,20 @@ def main():
             fbox.sync()
             fval, fms, fl, fkt, _ = timed_steps(abi, torch, dist, fbox, stream, args.form_steps, world)
             fn = fbox.n
-            fk = kernel_table(fp, True, fn, fbox.ncell, fkt, args.form_steps)
-            captured = not (getattr(fw, "walls_z", 0) or getattr(fw, "thermostat", 0) or any(getattr(fw, "g", (0.0,))))
+            fmixed = fens or fw.precision == "mixed"
+            fk = kernel_table(fp, fmixed, fn, fbox.ncell, fkt, args.form_steps)
+            captured = not (getattr(fw, "walls_z", 0) or getattr(fw, "thermostat", 0) or any(getattr(fw, "g", (0.0,)))
+                            or getattr(fw, "angular", 0))
+            if fmixed:
+                froof = roofline_of(fk, True, hbm_peak, peak_src, fn, captured=captured)
+            else:  # the per-cell collide of these FP64 variants has no instruction model
+                froof = None
             forms[name] = {"value": fval, "unit": UNIT, "steps": args.form_steps, "ms_per_step": fms / args.form_steps,
                            "particles": fn, "cells": fbox.ncell, "boxes": fw.rec.nbox if fens else 1,
                            "speedup_vs_fp64": fval / value, "gpu_launches": fl,
-                           "hbm_roofline_frac_step": fval / world * ALGO_STEP_BYTES_MIXED / 1e9 / hbm_peak,
-                           "roofline": roofline_of(fk, True, hbm_peak, peak_src, fn, captured=captured),
+                           "hbm_roofline_frac_step": fval / world * (ALGO_STEP_BYTES_MIXED if fmixed else
+                                                                     ALGO_STEP_BYTES_FP64) / 1e9 / hbm_peak,
+                           "roofline": froof,
                            "kernels": {k: {"ms_per_step": v["ms_per_step"], "share": v["share"], "gbs": v["gbs"]}
                                        for k, v in fk.items()}}
             fbox.close()

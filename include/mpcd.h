@@ -67,7 +67,14 @@ typedef struct {
                       /*   Boltzmann scaling, Huang et al. 2010; Philox counter             */
                       /*   (t, cell, 3, attempt), Marsaglia-Tsang).  Other values: ERR_ARG  */
   int32_t resort_k;   /* physically re-order storage by cell every k steps (0: never)       */
-  int32_t reserved;   /* must be 0                                                          */
+  int32_t angular;    /* 1: angular-momentum-conserving collision (the variant Sec. 2       */
+                      /*   mentions): after the rotation (and thermostat) each member gets  */
+                      /*   omega x rho_i, rho_i its position from the cell's centre of mass */
+                      /*   on the shifted grid, omega = I^-1 (L_before - L_after), I the    */
+                      /*   cell's inertia tensor (pseudo-inverse for two particles; none    */
+                      /*   for a singular one).  Conserves each cell's momentum and angular */
+                      /*   momentum, not its energy.  Periodic boxes only (walls: ERR_ARG). */
+                      /*   The mixed form takes it through its per-cell path.  0: off.      */
 } mpcd_params;
 
 /* Create a box and initialise it on the current CUDA device (Sec. 4 workload): positions

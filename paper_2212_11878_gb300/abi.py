@@ -58,7 +58,7 @@ class Params(ctypes.Structure):
         ("walls_z", ctypes.c_int32),
         ("thermostat", ctypes.c_int32),
         ("resort_k", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("angular", ctypes.c_int32),
     ]
 
 
@@ -73,7 +73,8 @@ class Tuning(ctypes.Structure):
 
 
 def make_params(L, a=1.0, ppc=10.0, dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=20221211,
-                precision="fp64", walls_z=0, g=(0.0, 0.0, 0.0), thermostat=0, resort_k=1, alpha=None) -> Params:
+                precision="fp64", walls_z=0, g=(0.0, 0.0, 0.0), thermostat=0, resort_k=1, alpha=None,
+                angular=0) -> Params:
     p = Params()
     if isinstance(L, int):
         L = (L, L, L)
@@ -90,13 +91,14 @@ def make_params(L, a=1.0, ppc=10.0, dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, s
     p.walls_z = int(walls_z)
     p.thermostat = int(thermostat)
     p.resort_k = int(resort_k)
-    p.reserved = 0
+    p.angular = int(angular)
     return p
 
 
 def params_from_workload(w, **override) -> Params:
     kw = dict(L=w.L, a=w.a, ppc=w.ppc, dt=w.dt, alpha_deg=w.alpha_deg, kT=w.kT, mass=w.mass, seed=w.seed,
-              precision=w.precision, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat, resort_k=w.resort_k)
+              precision=w.precision, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat, resort_k=w.resort_k,
+              angular=getattr(w, "angular", 0))
     kw.update(override)
     return make_params(**kw)
 

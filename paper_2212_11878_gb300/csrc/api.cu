@@ -138,7 +138,8 @@ int check_params(const mpcd_params* p, std::string* why) {
   if (p->walls_z && p->g[2] != 0.0) return *why = "g[2] must be 0 with walls in z", MPCD_ERR_ARG;
   if (p->thermostat < 0 || p->thermostat > 2) return *why = "thermostat must be 0, 1 or 2", MPCD_ERR_ARG;
   if (p->resort_k < 0) return *why = "resort_k must be >= 0", MPCD_ERR_ARG;
-  if (p->reserved != 0) return *why = "reserved must be 0", MPCD_ERR_ARG;
+  if (p->angular != 0 && p->angular != 1) return *why = "angular must be 0 or 1", MPCD_ERR_ARG;
+  if (p->angular && p->walls_z) return *why = "angular-momentum conservation needs a periodic box (no walls)", MPCD_ERR_ARG;
   if (p->precision == MPCD_MIXED) {
     int bits = 0;
     for (int d = 0; d < 3; ++d) {
@@ -160,6 +161,7 @@ Geom make_geom(const mpcd_params* p) {
   for (int d = 0; d < 3; ++d) g.L[d] = p->L[d];
   g.walls = p->walls_z;
   g.thermostat = p->thermostat;
+  g.angular = p->angular;
   g.resort_k = p->resort_k;
   g.a = p->a;
   g.inv_a = 1.0 / p->a;
@@ -418,8 +420,8 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   if (nbox > 1) {
     for (int32_t b = 0; b < nbox; ++b) {
       if (p[b].precision != MPCD_MIXED) return fail(nullptr, MPCD_ERR_ARG, "ensembles use the mixed form (MPCD_MIXED)");
-      if (p[b].walls_z != p[0].walls_z || p[b].thermostat != p[0].thermostat)
-        return fail(nullptr, MPCD_ERR_ARG, "all boxes of an ensemble must share walls_z and thermostat");
+      if (p[b].walls_z != p[0].walls_z || p[b].thermostat != p[0].thermostat || p[b].angular != p[0].angular)
+        return fail(nullptr, MPCD_ERR_ARG, "all boxes of an ensemble must share walls_z, thermostat and angular");
     }
   }
   mpcd_t* h = new mpcd_t();
@@ -456,7 +458,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->geom.n = ntot;
   h->geom.ncell = ctot;
   for (int k = 0; k < kNumSlots; ++k) h->per_step[k] = kSlotLaunchesBase[k];
-  if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotRotate] = 1;  // cell_frame + rotate
+  if (!h->geom.walls && !h->geom.thermostat && !h->geom.angular) h->per_step[kSlotRotate] = 1;  // cell_frame + rotate
   h->n = ntot;
   h->ncell = ctot;
   auto bail = [&](int code) {
@@ -504,6 +506,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     h->mb.walls = h->geom.walls;
     h->mb.force = force ? 1 : 0;
     h->mb.thermostat = h->geom.thermostat;
+    h->mb.angular = h->geom.angular;
     if ((rc = build_groups(h))) return bail(rc);
     if ((rc = upload_shifts(h, 0))) return bail(rc);
   } else {
@@ -520,7 +523,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     if ((rc = dalloc(h, &h->scr.count, C))) return bail(rc);
     if ((rc = dalloc(h, &h->scr.offset, C + 1))) return bail(rc);
     if ((rc = dalloc(h, &h->scr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
-    if (!h->geom.walls && !h->geom.thermostat) {
+    if (!h->geom.walls && !h->geom.thermostat && !h->geom.angular) {
       if ((rc = dalloc(h, &h->scr.frame, 16 * C))) return bail(rc);
       if ((rc = dalloc(h, &h->scr.inv, n))) return bail(rc);
     }
@@ -604,7 +607,7 @@ int mpcd_step(mpcd_t* h, int64_t nsteps) {
     h->t += 1;
     h->last_resorted = mixed || resort_at(h, h->t);
     if (h->last_resorted) h->cur ^= 1;
-    h->perm_sorted = !mixed && (h->last_resorted || h->geom.walls || h->geom.thermostat);
+    h->perm_sorted = !mixed && (h->last_resorted || h->geom.walls || h->geom.thermostat || h->geom.angular);
     h->any_step = true;
     h->moments_valid = h->record_moments;
   }

@@ -269,11 +269,73 @@ __device__ __forceinline__ void write_moments(const Geom& g, Scratch& s, int64_t
   mo[4] = 0.5 * g.mass * SE;
 }
 
-// The whole collision of one cell by one thread (the shape of Listing 4): used for walls
-// and the thermostat, and by the allocation-free step.
+// Position inside the cell on the shifted grid, in cell units: the fractional part of
+// (r - s)/a (with a a power of two, (r - s) * (1/a) is that quotient exactly).
+__device__ __forceinline__ double cell_local(const Geom& g, double r, double s) {
+  const double q = g.pow2a ? (r - s) * g.inv_a : (r - s) / g.a;
+  return q - floor(q);
+}
+
+// Angular-momentum-conserving collision (the variant the paper mentions in Sec. 2): omega =
+// I^-1 (L_before - L_after) for the cell's members pm[0..n), with rho_i = a (l_i - mean l)
+// their positions about the centre of mass on the shifted grid, L = m sum rho x v, and
+// I = m sum (|rho|^2 1 - rho rho^T).  Two particles: the pseudo-inverse (I acts as m sum
+// |rho|^2 normal to their separation); a singular I otherwise: no correction (omega = 0).
+// after(v) gives a member's velocity after the rotation and the thermostat.
+template <typename After>
+__device__ void cell_omega(const Geom& g, const Fp64Bufs& b, int cur, const int32_t* pm, int n, const double s[3],
+                           After after, double mean[3], double w[3]) {
+  mean[0] = mean[1] = mean[2] = 0.0;
+  w[0] = w[1] = w[2] = 0.0;
+  for (int j = 0; j < n; ++j)
+    for (int d = 0; d < 3; ++d) mean[d] += cell_local(g, b.r[cur][d][pm[j]], s[d]);
+  for (int d = 0; d < 3; ++d) mean[d] /= static_cast<double>(n);
+  double dL[3] = {0.0, 0.0, 0.0}, I[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, rr = 0.0, q0[3];
+  for (int j = 0; j < n; ++j) {
+    const int i = pm[j];
+    double q[3], v[3], va[3];
+    for (int d = 0; d < 3; ++d) {
+      q[d] = g.a * (cell_local(g, b.r[cur][d][i], s[d]) - mean[d]);
+      v[d] = b.v[cur][d][i];
+      va[d] = v[d];
+    }
+    if (j == 0)
+      for (int d = 0; d < 3; ++d) q0[d] = q[d];
+    after(va[0], va[1], va[2]);
+    const double dv0 = v[0] - va[0], dv1 = v[1] - va[1], dv2 = v[2] - va[2];
+    dL[0] += g.mass * (q[1] * dv2 - q[2] * dv1);
+    dL[1] += g.mass * (q[2] * dv0 - q[0] * dv2);
+    dL[2] += g.mass * (q[0] * dv1 - q[1] * dv0);
+    const double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    rr += q2;
+    for (int x = 0; x < 3; ++x)
+      for (int y = 0; y < 3; ++y) I[x][y] += g.mass * ((x == y ? q2 : 0.0) - q[x] * q[y]);
+  }
+  if (n == 2) {
+    if (rr > 0.0) {
+      const double along = (q0[0] * dL[0] + q0[1] * dL[1] + q0[2] * dL[2]) * (2.0 / rr);
+      for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q0[d]) / (g.mass * rr);
+    }
+    return;
+  }
+  double cof[3][3];
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) {
+      const int x1 = (x + 1) % 3, x2 = (x + 2) % 3, y1 = (y + 1) % 3, y2 = (y + 2) % 3;
+      cof[x][y] = I[x1][y1] * I[x2][y2] - I[x1][y2] * I[x2][y1];
+    }
+  const double det = I[0][0] * cof[0][0] + I[0][1] * cof[0][1] + I[0][2] * cof[0][2];
+  const double tr = (I[0][0] + I[1][1] + I[2][2]) / 3.0;
+  if (det > 1e-12 * tr * tr * tr)
+    for (int x = 0; x < 3; ++x) w[x] = (cof[x][0] * dL[0] + cof[x][1] * dL[1] + cof[x][2] * dL[2]) / det;
+}
+
+// The whole collision of one cell by one thread (the shape of Listing 4): used for walls,
+// the thermostats and angular-momentum conservation, and by the allocation-free step.
 template <int WALLS, int THERMO, int MOMENTS>
 __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& s, int64_t c, int64_t t1, int cur,
-                                     bool resort, double shift_z) {
+                                     bool resort, const double* shift) {
+  const double shift_z = shift[2];
   const int o = s.offset[c];
   const int n = s.offset[c + 1] - o;
   int32_t* __restrict__ pm = s.perm + o;
@@ -323,6 +385,19 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
       f = sqrt(target / K);
     }
   }
+  double mean[3] = {0.0, 0.0, 0.0}, w[3] = {0.0, 0.0, 0.0};
+  const bool spin = !WALLS && rotate && g.angular;
+  if (spin)
+    cell_omega(g, b, cur, pm, n, shift,
+               [&](double& v0, double& v1, double& v2) {
+                 apply_frame(R, bv, v0, v1, v2);
+                 if (THERMO && n >= 2) {
+                   v0 = fma(f, v0 - u0, u0);
+                   v1 = fma(f, v1 - u1, u1);
+                   v2 = fma(f, v2 - u2, u2);
+                 }
+               },
+               mean, w);
   for (int j = 0; j < n; ++j) {
     const int i = pm[j];
     double v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
@@ -332,6 +407,14 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
         v0 = fma(f, v0 - u0, u0);
         v1 = fma(f, v1 - u1, u1);
         v2 = fma(f, v2 - u2, u2);
+      }
+      if (spin) {  // v += omega x rho
+        const double q0 = g.a * (cell_local(g, b.r[cur][0][i], shift[0]) - mean[0]);
+        const double q1 = g.a * (cell_local(g, b.r[cur][1][i], shift[1]) - mean[1]);
+        const double q2 = g.a * (cell_local(g, b.r[cur][2][i], shift[2]) - mean[2]);
+        v0 += w[1] * q2 - w[2] * q1;
+        v1 += w[2] * q0 - w[0] * q2;
+        v2 += w[0] * q1 - w[1] * q0;
       }
     }
     if (resort) {
@@ -357,7 +440,7 @@ __global__ void __launch_bounds__(kThreads) k_collide_fp64_generic(Geom g, Fp64B
   if (c >= g.ncell) return;
   const int64_t t1 = ctl->t + 1;
   const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
-  collide_cell_generic<WALLS, THERMO, MOMENTS>(g, b, s, c, t1, ctl->cur, resort, ctl->shift[2]);
+  collide_cell_generic<WALLS, THERMO, MOMENTS>(g, b, s, c, t1, ctl->cur, resort, ctl->shift);
 }
 
 // Periodic box, no thermostat, in two passes so that each runs at full occupancy:
@@ -610,7 +693,9 @@ void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl,
   }
 }
 
-bool fp64_dense_collide(const Geom& g, const Scratch& s) { return !g.walls && !g.thermostat && s.frame && s.inv; }
+bool fp64_dense_collide(const Geom& g, const Scratch& s) {
+  return !g.walls && !g.thermostat && !g.angular && s.frame && s.inv;
+}
 
 void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st) {
   if (!fp64_dense_collide(g, s)) {

@@ -466,12 +466,118 @@ __device__ __forceinline__ bool cell_sums_mixed(const V3& v, int n, long long S[
   return ok;
 }
 
+// Position of a streamed record inside its cell of this step's grid (shift sf, cell units),
+// exact in FP64: the offset less the shift less the whole cells that the key counted.
+__device__ __forceinline__ void mixed_local(const MixRec& r, const float sf[3], double l[3]) {
+  const float f[3] = {r.ox, r.oy, r.oz};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float x = __fsub_rn(f[d], sf[d]);
+    const int k = static_cast<int>(x >= 1.0f) - static_cast<int>(x < 0.0f);
+    l[d] = static_cast<double>(f[d]) - static_cast<double>(sf[d]) - static_cast<double>(k);
+  }
+}
+
+// Angular momentum of the cell about its centre of mass, sum rho x v (times m by the caller).
+__device__ __forceinline__ void mixed_spin(const MixRec* rec, int n, const float sf[3], const double mean[3], double a,
+                                           double L[3]) {
+  L[0] = L[1] = L[2] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double l[3];
+    mixed_local(rec[j], sf, l);
+    const double q0 = a * (l[0] - mean[0]), q1 = a * (l[1] - mean[1]), q2 = a * (l[2] - mean[2]);
+    const double v0 = rec[j].vx, v1 = rec[j].vy, v2 = rec[j].vz;
+    L[0] += q1 * v2 - q2 * v1;
+    L[1] += q2 * v0 - q0 * v2;
+    L[2] += q0 * v1 - q1 * v0;
+  }
+}
+
+// Before the collision: the members sorted by particle id (so the FP64 sums take one fixed
+// order), their mean position in the cell and their angular momentum about it.
+struct CellSpin {
+  double mean[3], Lb[3];
+};
+
+__device__ __noinline__ CellSpin mixed_spin_before(MixRec* rec, int n, const float* sf, double a) {
+  for (int j = 1; j < n; ++j) {  // insertion sort by particle id
+    const MixRec x = rec[j];
+    int k = j - 1;
+    while (k >= 0 && rec[k].id > x.id) {
+      rec[k + 1] = rec[k];
+      --k;
+    }
+    rec[k + 1] = x;
+  }
+  CellSpin cs;
+  cs.mean[0] = cs.mean[1] = cs.mean[2] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double l[3];
+    mixed_local(rec[j], sf, l);
+    for (int d = 0; d < 3; ++d) cs.mean[d] += l[d];
+  }
+  for (int d = 0; d < 3; ++d) cs.mean[d] /= static_cast<double>(n);
+  mixed_spin(rec, n, sf, cs.mean, a, cs.Lb);
+  return cs;
+}
+
+// Angular-momentum-conserving collision (the variant the paper mentions in Sec. 2), mixed
+// form, after the rotation and rescale: omega = I^-1 (L_before - L_after), v += omega x rho
+// rounded to FP32.  The same rule as the FP64 form (pseudo-inverse for two particles, none
+// for a singular inertia tensor).
+__device__ __noinline__ void mixed_angular(const Geom* __restrict__ gp, MixRec* rec, int n, const float* sf,
+                                           CellSpin cs) {
+  const Geom& g = *gp;
+  const double* mean = cs.mean;
+  const double* Lb = cs.Lb;
+  double La[3], I[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, rr = 0.0, q0[3] = {0.0, 0.0, 0.0};
+  mixed_spin(rec, n, sf, mean, g.a, La);
+  const double dL[3] = {Lb[0] - La[0], Lb[1] - La[1], Lb[2] - La[2]};
+  for (int j = 0; j < n; ++j) {
+    double l[3], q[3];
+    mixed_local(rec[j], sf, l);
+    for (int d = 0; d < 3; ++d) q[d] = g.a * (l[d] - mean[d]);
+    if (j == 0)
+      for (int d = 0; d < 3; ++d) q0[d] = q[d];
+    const double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    rr += q2;
+    for (int x = 0; x < 3; ++x)
+      for (int y = 0; y < 3; ++y) I[x][y] += (x == y ? q2 : 0.0) - q[x] * q[y];
+  }
+  double w[3] = {0.0, 0.0, 0.0};
+  if (n == 2) {
+    if (!(rr > 0.0)) return;
+    const double along = (q0[0] * dL[0] + q0[1] * dL[1] + q0[2] * dL[2]) * (2.0 / rr);
+    for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q0[d]) / rr;
+  } else {
+    double cof[3][3];
+    for (int x = 0; x < 3; ++x)
+      for (int y = 0; y < 3; ++y) {
+        const int x1 = (x + 1) % 3, x2 = (x + 2) % 3, y1 = (y + 1) % 3, y2 = (y + 2) % 3;
+        cof[x][y] = I[x1][y1] * I[x2][y2] - I[x1][y2] * I[x2][y1];
+      }
+    const double det = I[0][0] * cof[0][0] + I[0][1] * cof[0][1] + I[0][2] * cof[0][2];
+    const double tr = (I[0][0] + I[1][1] + I[2][2]) / 3.0;
+    if (!(det > 1e-12 * tr * tr * tr)) return;
+    for (int x = 0; x < 3; ++x) w[x] = (cof[x][0] * dL[0] + cof[x][1] * dL[1] + cof[x][2] * dL[2]) / det;
+  }
+  for (int j = 0; j < n; ++j) {
+    double l[3];
+    mixed_local(rec[j], sf, l);
+    const double qx = g.a * (l[0] - mean[0]), qy = g.a * (l[1] - mean[1]), qz = g.a * (l[2] - mean[2]);
+    rec[j].vx = static_cast<float>(rec[j].vx + (w[1] * qz - w[2] * qy));
+    rec[j].vy = static_cast<float>(rec[j].vy + (w[2] * qx - w[0] * qz));
+    rec[j].vz = static_cast<float>(rec[j].vz + (w[0] * qy - w[1] * qx));
+  }
+}
+
 // The whole collision of one cell by one thread over AoS records rec[0..n-1] in global
-// memory (crowded cells).  Its sums accumulate the same fixed-point parts in int64, so they
-// equal the staged path's bit for bit.
-template <int WALLS, int THERMO, int MOMENTS>
+// memory (crowded cells, and every cell with angular-momentum conservation, which also gets
+// this step's shift sf in cell units).  Its sums accumulate the same fixed-point parts in
+// int64, so they equal the staged path's bit for bit.
+template <int WALLS, int THERMO, int MOMENTS, int ANG = 0>
 __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c, int64_t t1, double shift_z,
-                                   double* moments) {
+                                   double* moments, const float* sf) {
   const V3 v{&rec[0].vx, &rec[0].vy, &rec[0].vz, 8};
   long long S[3], E2;
   const bool ok = cell_sums_mixed<MOMENTS>(v, n, S, E2);
@@ -479,6 +585,9 @@ __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c,
   CellFrame f;
   cell_prologue<WALLS>(g, S, n, c, t1, shift_z, f);
   if (!f.rot || !ok) return;
+  const bool spin = ANG && !WALLS && n >= 2;
+  CellSpin cs;
+  if (spin) cs = mixed_spin_before(rec, n, sf, g.a);
   long long dE = 0, Ea = 0;
   bool oke = n < 512;
   for (int j = 0; j < n; ++j) {
@@ -495,6 +604,7 @@ __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c,
     v.vy(j) = __fadd_rn(f.u[1], fmaf(df, v.vy(j), v.vy(j)));
     v.vz(j) = __fadd_rn(f.u[2], fmaf(df, v.vz(j), v.vz(j)));
   }
+  if (spin) mixed_angular(&g, rec, n, sf, cs);
 }
 
 // True when streaming a particle with velocity v moves each in-cell offset f in [0, 1) by
@@ -727,7 +837,7 @@ __device__ __forceinline__ MixRec lds_rec(const MixRec* p, int lane) {
 // A group too large for the stage (more than kMixCap records or 32 cells): one lane per
 // cell, in passes of 32 cells, records in place in the destination.
 // (Arguments are plain values and pointers so that calling it stores nothing to the stack.)
-template <int WALLS, int FORCE, int THERMO, int MOMENTS>
+template <int WALLS, int FORCE, int THERMO, int MOMENTS, int ANG = 0>
 __device__ __noinline__ void collide_group_direct(const Geom* __restrict__ gp, const BoxShift* __restrict__ shp,
                                                   int64_t c0, int ncells, const int32_t* __restrict__ offset,
                                                   const int32_t* __restrict__ perm, double* moments,
@@ -746,8 +856,8 @@ __device__ __noinline__ void collide_group_direct(const Geom* __restrict__ gp, c
       stream_record<WALLS, FORCE>(g, r);
       dst[o + j] = r;
     }
-    mixed_collide_cell<WALLS, THERMO, MOMENTS>(g, dst + o, n, c - cbase, t1, shp->s[2],
-                                               MOMENTS ? moments + 5 * (int64_t)cbase : nullptr);
+    mixed_collide_cell<WALLS, THERMO, MOMENTS, ANG>(g, dst + o, n, c - cbase, t1, shp->s[2],
+                                                    MOMENTS ? moments + 5 * (int64_t)cbase : nullptr, shp->sf);
     for (int j = 0; j < n; ++j) {
       const int k = cbase + next_key<WALLS, FORCE>(g, dst[o + j], sf);
       knext[o + j] = k;
@@ -1341,6 +1451,49 @@ cudaError_t launch_collide_t(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* c
   return cudaSuccess;
 }
 
+// Angular-momentum-conserving collision: every group goes through the per-cell path (a warp
+// per group, a lane per cell), the only one compiled with the correction, so the staged
+// kernel's code is untouched.  Periodic boxes only.
+template <int FORCE, int THERMO, int MOMENTS>
+__global__ void __launch_bounds__(128) k_collide_direct_mixed(MixBatch mb, MixBufs b, MixScratch s,
+                                                              Ctl* __restrict__ ctl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  const int64_t t1 = ctl->t + 1;
+  const int cur = ctl->cur, nxt = cur ^ 1;
+  for (int64_t gi = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; gi < mb.ngroups; gi += warps) {
+    const MixGroup d = mb.groups[gi];
+    collide_group_direct<0, FORCE, THERMO, MOMENTS, 1>(mb.boxes + d.box, mb.shifts + d.box, d.c0, d.ncells, s.offset,
+                                                       s.perm, s.moments, b.rec[cur], b.rec[nxt], s.key[nxt],
+                                                       s.count[nxt], t1, lane);
+  }
+}
+
+template <int FORCE, int THERMO, int MOMENTS>
+void launch_direct_t(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st) {
+  int64_t grid = (static_cast<int64_t>(mb.ngroups) + 3) / 4;
+  if (grid == 0) return;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_collide_direct_mixed<FORCE, THERMO, MOMENTS><<<static_cast<unsigned>(grid), 128, 0, st>>>(mb, b, s, ctl);
+}
+
+void launch_collide_direct(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st) {
+  switch ((mb.force ? 6 : 0) + 2 * mb.thermostat + (moments ? 1 : 0)) {
+    case 0: return launch_direct_t<0, 0, 0>(mb, b, s, ctl, st);
+    case 1: return launch_direct_t<0, 0, 1>(mb, b, s, ctl, st);
+    case 2: return launch_direct_t<0, 1, 0>(mb, b, s, ctl, st);
+    case 3: return launch_direct_t<0, 1, 1>(mb, b, s, ctl, st);
+    case 4: return launch_direct_t<0, 2, 0>(mb, b, s, ctl, st);
+    case 5: return launch_direct_t<0, 2, 1>(mb, b, s, ctl, st);
+    case 6: return launch_direct_t<1, 0, 0>(mb, b, s, ctl, st);
+    case 7: return launch_direct_t<1, 0, 1>(mb, b, s, ctl, st);
+    case 8: return launch_direct_t<1, 1, 0>(mb, b, s, ctl, st);
+    case 9: return launch_direct_t<1, 1, 1>(mb, b, s, ctl, st);
+    case 10: return launch_direct_t<1, 2, 0>(mb, b, s, ctl, st);
+    default: return launch_direct_t<1, 2, 1>(mb, b, s, ctl, st);
+  }
+}
+
 template <int WARPS>
 cudaError_t launch_collide_w(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st,
                              bool prepare, int sel_override = -1) {
@@ -1395,7 +1548,9 @@ cudaError_t prepare_collide_mixed() {
 }
 
 void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st) {
-  if (mb.warps == 2)
+  if (mb.angular)
+    launch_collide_direct(mb, b, s, ctl, moments, st);
+  else if (mb.warps == 2)
     (void)launch_collide_w<2>(mb, b, s, ctl, moments, st, false);
   else
     (void)launch_collide_w<4>(mb, b, s, ctl, moments, st, false);

@@ -17,7 +17,7 @@ struct alignas(16) Geom {
   int32_t pow2a;       // a is a power of two: (r - s) * (1/a) == (r - s) / a exactly
   int32_t force;       // any g component non-zero
   int32_t log2a;       // a = 2^log2a when pow2a
-  int32_t pad0;
+  int32_t angular;     // angular-momentum-conserving collision (periodic boxes)
   double a, inv_a;
   double B[3];         // box edge lengths L[d] * a
   double dt;
@@ -160,6 +160,7 @@ struct MixBatch {
   int64_t n;      // particles of all boxes
   int64_t ncell;  // cells of all boxes
   int32_t walls, force, thermostat, warps;  // uniform over boxes; warps per collide block
+  int32_t angular, pad;                     // uniform over boxes: every group takes the per-cell path
 };
 
 constexpr int kMixCap = 192;  // records one warp stages (larger groups take the per-cell path)

@@ -34,6 +34,7 @@ class Workload:
     walls_z: int = 0
     g: tuple = (0.0, 0.0, 0.0)
     thermostat: int = 0
+    angular: int = 0
     steps: int = 100
     notes: str = ""
 
@@ -71,6 +72,11 @@ WORKLOADS = {
                                      steps=20000, precision="mixed", resort_k=1, walls_z=1,
                                      g=(1e-3, 0.0, 0.0), thermostat=1,
                                      notes="bounce-back walls in z, body force along x"),
+    "fp64_L128_angular": Workload("fp64_L128_angular", (128, 128, 128), seed=BASE_SEED + 1, steps=1000, resort_k=10,
+                                  angular=1, notes="angular-momentum-conserving collision, FP64"),
+    "mixed_L128_angular": Workload("mixed_L128_angular", (128, 128, 128), seed=BASE_SEED + 2, steps=500,
+                                   precision="mixed", resort_k=1, angular=1,
+                                   notes="angular-momentum-conserving collision, mixed form (per-cell path)"),
     "poiseuille_256x64x64_mbs": Workload("poiseuille_256x64x64_mbs", (256, 64, 64), ppc=20.0, seed=BASE_SEED + 3,
                                          steps=20000, precision="mixed", resort_k=1, walls_z=1,
                                          g=(1e-3, 0.0, 0.0), thermostat=2,

@@ -20,7 +20,7 @@ TOL = 1e-12
 def oracle_params(orc, p: abi.Params):
     return orc.make_params(tuple(p.L), a=p.a, dt=p.dt, alpha=p.alpha, kT=p.kT, mass=p.mass, ppc=p.ppc,
                            seed=p.seed, resort_k=p.resort_k, walls_z=p.walls_z, g=tuple(p.g),
-                           thermostat=p.thermostat)
+                           thermostat=p.thermostat, angular=p.angular)
 
 
 def periodic_diff(a, b, box, walls_z=False):

@@ -43,13 +43,13 @@ def test_params_layout_matches_c(tmp_path):
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpcd.h"\n'
                     'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mpcd_params),'
                     ' offsetof(mpcd_params, a), offsetof(mpcd_params, g), offsetof(mpcd_params, seed),'
-                    ' offsetof(mpcd_params, walls_z), offsetof(mpcd_params, reserved)); return 0;}\n')
+                    ' offsetof(mpcd_params, walls_z), offsetof(mpcd_params, angular)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     P = abi.Params
     assert got == [__import__("ctypes").sizeof(P), P.a.offset, P.g.offset, P.seed.offset, P.walls_z.offset,
-                   P.reserved.offset]
+                   P.angular.offset]
 
 
 def test_tuning_layout_matches_c(tmp_path):
@@ -87,7 +87,7 @@ def test_version_string(libpath):
     dict(L=(0, 4, 4)), dict(a=0.0), dict(a=float("nan")), dict(dt=-0.1), dict(kT=0.0), dict(mass=-1.0),
     dict(ppc=-1.0), dict(walls_z=2), dict(walls_z=1, g=(0.0, 0.0, 0.1)), dict(resort_k=-1), dict(precision=7),
     dict(alpha=float("inf")), dict(L=(4096, 4096, 4096)), dict(precision=1, L=(1025, 1025, 1025)),
-    dict(thermostat=3), dict(thermostat=-1),
+    dict(thermostat=3), dict(thermostat=-1), dict(angular=2), dict(angular=1, walls_z=1),
 ])
 def test_invalid_params_rejected_on_host(libpath, bad):
     p = abi.make_params(**{**dict(L=(4, 4, 4)), **bad})

@@ -59,8 +59,10 @@ SPARSE_BOXES = [  # groups span more than 32 cells here and take the per-cell pa
 
 @pytest.mark.parametrize("boxes,extra", [(WALL_BOXES, dict(walls_z=1, thermostat=1)),
                                          (WALL_BOXES, dict(walls_z=1, thermostat=2)),
-                                         (BOXES, dict(thermostat=2)), (SPARSE_BOXES, {})],
-                         ids=["walls_force_thermostat", "walls_force_mbs", "periodic_mbs", "sparse"])
+                                         (BOXES, dict(thermostat=2)), (SPARSE_BOXES, {}),
+                                         (BOXES, dict(angular=1)), (SPARSE_BOXES, dict(angular=1, thermostat=1))],
+                         ids=["walls_force_thermostat", "walls_force_mbs", "periodic_mbs", "sparse", "angular",
+                              "angular_sparse_thermostat"])
 def test_each_box_equals_the_box_alone_other_kinds(boxes, extra):
     params = [abi.make_params(precision="mixed", **k, **extra) for k in boxes]
     with abi.Box(batch=params) as ens:

@@ -73,7 +73,8 @@ def test_init_matches_oracle_to_fp32(orc):
                                   dict(L=(10, 9, 8), thermostat=1, kT=1.3), dict(L=(11, 9, 8), thermostat=2, kT=1.3),
                                   dict(L=(9, 8, 10), walls_z=1, g=(0.02, 0.01, 0.0)),
                                   dict(L=(8, 9, 12), walls_z=1, g=(0.01, 0.0, 0.0), thermostat=2, ppc=15),
-                                  dict(L=(8, 8, 6), walls_z=1, g=(0.02, 0.0, 0.0), dt=0.3, fast=0.02)])
+                                  dict(L=(8, 8, 6), walls_z=1, g=(0.02, 0.0, 0.0), dt=0.3, fast=0.02),
+                                  dict(L=(10, 9, 8), angular=1), dict(L=(9, 8, 7), angular=1, thermostat=1, fast=0.01)])
 def test_one_step_against_fp64_oracle(orc, case):
     """`fast`: that fraction of the particles moves 0.6 to 3 cells in the step, so that the
     warps holding them take the general carry path instead of the one-cell one.  With walls,
@@ -171,6 +172,45 @@ def test_mbs_thermostat_gives_canonical_cell_energies(precision):
             ok = cnt >= 2
             pits.append(stats.gamma.cdf(rel[ok] / kT, 1.5 * (cnt[ok] - 1)))
     assert stats.kstest(np.concatenate(pits), "uniform").pvalue > 1e-3
+
+
+def test_angular_momentum_conserved_per_cell_mixed():
+    """Angular-momentum-conserving collision, mixed form: per cell, momentum and the angular
+    momentum about the centre of mass (positions on the shifted grid) are unchanged by the
+    collision to FP32 rounding of the stored velocities."""
+    L = (12, 10, 8)
+    p = mixed_params(L, seed=17, angular=1, dt=0.0)  # dt = 0: the collision alone changes v
+    C = int(np.prod(L))
+    n = int(round(10 * C))
+    r0, v0 = quantize(*inputs.uniform_gaussian_state(L, n, 18), L)
+    with abi.Box(p) as box:
+        box.set_state(r0, v0, 2)
+        abi.mpcd_record_moments(box.h, True)
+        box.step(1)
+        dbg = box.debug_sort()
+        rg, vg = box.state()
+        shift = box.moments()[1]
+    keys = np.empty(n, np.int64)
+    keys[dbg["ids"]] = dbg["keys"]
+    # position inside the cell the GPU assigned (periodic images folded next to it)
+    cell = np.stack([keys % L[0], (keys // L[0]) % L[1], keys // (L[0] * L[1])], axis=1)
+    loc = (rg - shift) / p.a - cell
+    loc -= np.array(L) * np.round((loc - 0.5) / np.array(L))
+    cnt = np.bincount(keys, minlength=C)
+    mean = np.stack([np.bincount(keys, weights=loc[:, d], minlength=C) for d in range(3)], axis=1)
+    rho = p.a * (loc - mean[keys] / np.maximum(cnt, 1)[keys, None])
+    per = lambda x: np.stack([np.bincount(keys, weights=x[:, d], minlength=C) for d in range(3)], axis=1)
+    dLc = per(np.cross(rho, vg)) - per(np.cross(rho, v0))
+    scale = np.bincount(keys, weights=np.linalg.norm(rho, axis=1) * np.abs(v0).sum(axis=1), minlength=C) + 1e-30
+    assert np.all(np.abs(dLc).max(axis=1) <= 2e-6 * scale)
+    dP = per(vg) - per(v0)
+    assert np.all(np.abs(dP).max(axis=1) <= 2e-6 * np.bincount(keys, weights=np.abs(v0).sum(axis=1), minlength=C) + 1e-30)
+    # the plain collision would change it: the check is not vacuous
+    with abi.Box(mixed_params(L, seed=17, dt=0.0)) as box:
+        box.set_state(r0, v0, 2)
+        box.step(1)
+        _, v_plain = box.state()
+    assert np.abs(per(np.cross(rho, v_plain)) - per(np.cross(rho, v0))).max() > 1e-3
 
 
 def test_energy_and_momentum_do_not_drift():
