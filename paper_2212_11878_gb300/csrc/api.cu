@@ -195,6 +195,11 @@ Geom make_geom(const mpcd_params* p) {
   }
   g.cos_af = static_cast<float>(g.cos_a);
   g.sin_af = static_cast<float>(g.sin_a);
+  g.dtf = static_cast<float>(g.dt);
+  g.inv_af = static_cast<float>(g.inv_a);
+  for (int d = 0; d < 3; ++d) g.gf[d] = p->g[d] != 0.0 ? static_cast<float>(p->g[d]) : 0.0f;
+  g.kTf = static_cast<float>(p->kT);
+  g.massf = static_cast<float>(p->mass);
   g.n = (int64_t)std::llround(p->ppc * (double)p->L[0] * p->L[1] * p->L[2]);
   g.ncell = (int64_t)p->L[0] * p->L[1] * ((int64_t)p->L[2] + (p->walls_z ? 1 : 0));
   return g;

@@ -102,11 +102,11 @@ template <int WALLS, int FORCE, int NEAR = 0>
 __device__ __forceinline__ void stream_mixed(const Geom& g, float f[3], int cc[3], float v[3]) {
   if (WALLS && NEAR) {
     // the first pass of the bounce loop below when it finds no wall: tau = dt
-    const float inv_a = static_cast<float>(g.inv_a);
-    const float tau = static_cast<float>(g.dt);
+    const float inv_a = g.inv_af;
+    const float tau = g.dtf;
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      const float gt = g.g[d] != 0.0 ? static_cast<float>(g.g[d]) : 0.0f;
+      const float gt = g.gf[d];
       f[d] = fmaf(fmaf(0.5f * gt, tau, v[d]), tau * inv_a, f[d]);
       v[d] = fmaf(gt, tau, v[d]);
       carry_near(f[d], cc[d], g.L[d]);
@@ -149,9 +149,9 @@ __device__ __forceinline__ void stream_mixed(const Geom& g, float f[3], int cc[3
     }
     return;
   }
-  const float inv_a = static_cast<float>(g.inv_a);
+  const float inv_a = g.inv_af;
   const int Lz = g.L[2];
-  float left = static_cast<float>(g.dt);
+  float left = g.dtf;
   for (int bounce = 0; bounce < 8 && left > 0.0f; ++bounce) {
     const float vz_c = v[2] * inv_a;  // cells per unit time
     const float zrel = fmaf(vz_c, left, f[2]);
@@ -168,7 +168,7 @@ __device__ __forceinline__ void stream_mixed(const Geom& g, float f[3], int cc[3
     if (tau > left) tau = left;
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
-      const float gt = g.g[d] != 0.0 ? static_cast<float>(g.g[d]) : 0.0f;
+      const float gt = g.gf[d];
       f[d] = fmaf(fmaf(0.5f * gt, tau, v[d]), tau * inv_a, f[d]);
       v[d] = fmaf(gt, tau, v[d]);
       carry_periodic(f[d], cc[d], g.L[d]);
@@ -425,7 +425,7 @@ __device__ __forceinline__ float cell_df(const Geom& g, int n, long long dE, lon
   if (THERMO && n >= 2) {
     const float dof = THERMO == 2 ? 2.0f * mbs_gamma_f32(g.seed, t1, cell, 1.5f * static_cast<float>(n - 1))
                                   : 3.0f * static_cast<float>(n - 1);
-    return sqrtf(dof * static_cast<float>(g.kT) / (static_cast<float>(g.mass) * ea)) - 1.0f;
+    return sqrtf(dof * g.kTf / (g.massf * ea)) - 1.0f;
   }
   return 0.5f * (ll_to_float(dE) * 0x1.0p-44f) / ea;
 }
@@ -621,8 +621,8 @@ __device__ __forceinline__ bool moves_near(const Geom& g, const MixRec& r) {
 // test as the first pass of the bounce loop in stream_mixed (NaN: false).
 __device__ __forceinline__ bool stays_inside(const Geom& g, const MixRec& r) {
   const int cz = r.cell >> (g.bits[0] + g.bits[1]);
-  const float tau = static_cast<float>(g.dt);
-  const float zrel = fmaf(r.vz * static_cast<float>(g.inv_a), tau, r.oz);
+  const float tau = g.dtf;
+  const float zrel = fmaf(r.vz * g.inv_af, tau, r.oz);
   return tau > 0.0f && zrel >= -static_cast<float>(cz) && zrel < static_cast<float>(g.L[2] - cz);
 }
 

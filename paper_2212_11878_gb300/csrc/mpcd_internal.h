@@ -35,6 +35,9 @@ struct alignas(16) Geom {
   float ha[3];         // g dt^2 / (2 a)
   float gdt[3];        // g dt
   float cos_af, sin_af;
+  // FP32 copies of dt, 1/a, g (0 where g is 0), kT and m: a double -> float conversion or a
+  // double compare in a kernel would occupy the narrow FP64 pipe
+  float dtf, inv_af, gf[3], kTf, massf;
   int32_t bits[3];     // bits of each packed cell coordinate
 };
 
