@@ -166,14 +166,17 @@ static void cross(const double a[3], const double b[3], double out[3]) {
   out[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-/* Angular momentum about the cell's centre of mass, m sum rho_i x v_i (R23). */
-static void cell_angular_momentum(const orc_params* p, const double* rho, const double* v, const int32_t* perm,
-                                  int32_t j0, int32_t j1, double L[3]) {
+/* Mass of the particle in storage slot i: its own (R24) or the box's. */
+static double mass_of(const orc_params* p, const double* mass, int64_t i) { return mass ? mass[i] : p->mass; }
+
+/* Angular momentum about the cell's centre of mass, sum m_i rho_i x v_i (R23). */
+static void cell_angular_momentum(const orc_params* p, const double* mass, const double* rho, const double* v,
+                                  const int32_t* perm, int32_t j0, int32_t j1, double L[3]) {
   L[0] = L[1] = L[2] = 0.0;
   for (int32_t j = j0; j < j1; ++j) {
     double c[3];
     cross(&rho[3 * (int64_t)(j - j0)], &v[3 * (int64_t)perm[j]], c);
-    for (int d = 0; d < 3; ++d) L[d] += p->mass * c[d];
+    for (int d = 0; d < 3; ++d) L[d] += mass_of(p, mass, perm[j]) * c[d];
   }
 }
 
@@ -282,7 +285,16 @@ void orc_init(const orc_params* p, int64_t n, double* r, double* v) {
 int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, int32_t* id,
              int32_t* keys_out, int32_t* counts_out, int32_t* offsets_out, int32_t* perm_out,
              double* moments_out, double* shift_out) {
+  return orc_step_m(p, n, t, r, v, id, NULL, keys_out, counts_out, offsets_out, perm_out, moments_out, shift_out);
+}
+
+int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, int32_t* id, double* mass,
+               int32_t* keys_out, int32_t* counts_out, int32_t* offsets_out, int32_t* perm_out,
+               double* moments_out, double* shift_out) {
   if (!p || n < 0 || t < 1 || p->a <= 0.0 || p->mass <= 0.0) return -1;
+  if (mass)
+    for (int64_t i = 0; i < n; ++i)
+      if (!(mass[i] > 0.0)) return -1;
   for (int d = 0; d < 3; ++d)
     if (p->L[d] < 1) return -1;
   if (p->walls_z && p->g[2] != 0.0) return -1;
@@ -325,9 +337,10 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
     double M = 0.0, P[3] = {0.0, 0.0, 0.0}, E = 0.0;
     for (int32_t j = off[c]; j < off[c + 1]; ++j) {
       const double* vi = &v[3 * (int64_t)perm[j]];
-      for (int d = 0; d < 3; ++d) P[d] += m * vi[d];
-      M += m;
-      E += 0.5 * m * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
+      const double mi = mass_of(p, mass, perm[j]); /* Listing 4 weights by mass */
+      for (int d = 0; d < 3; ++d) P[d] += mi * vi[d];
+      M += mi;
+      E += 0.5 * mi * (vi[0] * vi[0] + vi[1] * vi[1] + vi[2] * vi[2]);
     }
     if (moments_out) {
       moments_out[5 * c + 0] = M;
@@ -371,12 +384,13 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
       for (int32_t j = off[c]; j < off[c + 1]; ++j) {
         double* l = &rho[3 * (int64_t)(j - off[c])];
         orc_cell_local(p, &r[3 * (int64_t)perm[j]], s, l);
-        for (int d = 0; d < 3; ++d) mean[d] += l[d];
+        /* the centre of mass: with particle masses (R24) weighted, else the plain mean */
+        for (int d = 0; d < 3; ++d) mean[d] += mass ? mass[perm[j]] * l[d] : l[d];
       }
-      for (int d = 0; d < 3; ++d) mean[d] /= (double)nc;
+      for (int d = 0; d < 3; ++d) mean[d] /= mass ? M : (double)nc;
       for (int32_t j = off[c]; j < off[c + 1]; ++j)
         for (int d = 0; d < 3; ++d) rho[3 * (int64_t)(j - off[c]) + d] = p->a * (rho[3 * (int64_t)(j - off[c]) + d] - mean[d]);
-      cell_angular_momentum(p, rho, v, perm, off[c], off[c + 1], Lb);
+      cell_angular_momentum(p, mass, rho, v, perm, off[c], off[c + 1], Lb);
     }
 
     for (int32_t j = off[c]; j < off[c + 1]; ++j) orc_rotate(ax, p->alpha, u, &v[3 * (int64_t)perm[j]]);
@@ -389,7 +403,8 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
       double K = 0.0;
       for (int32_t j = off[c]; j < off[c + 1]; ++j) {
         const double* vi = &v[3 * (int64_t)perm[j]];
-        for (int d = 0; d < 3; ++d) K += 0.5 * m * (vi[d] - u[d]) * (vi[d] - u[d]);
+        const double mi = mass_of(p, mass, perm[j]);
+        for (int d = 0; d < 3; ++d) K += 0.5 * mi * (vi[d] - u[d]) * (vi[d] - u[d]);
       }
       if (K > 0.0) {
         double f = sqrt(target / K);
@@ -404,15 +419,17 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
       /* R23: omega = I^-1 (L_before - L_after) with I = m sum (|rho|^2 1 - rho rho^T); then
        * v_i += omega x rho_i, which keeps the cell's momentum (sum rho_i = 0) and restores
        * its angular momentum (sum m rho_i x (omega x rho_i) = I omega). */
-      double La[3], dL[3], I[3][3] = {{0.0}}, rr = 0.0;
-      cell_angular_momentum(p, rho, v, perm, off[c], off[c + 1], La);
+      double La[3], dL[3], I[3][3] = {{0.0}}, rr = 0.0, rrm = 0.0;
+      cell_angular_momentum(p, mass, rho, v, perm, off[c], off[c + 1], La);
       for (int d = 0; d < 3; ++d) dL[d] = Lb[d] - La[d];
       for (int32_t j = off[c]; j < off[c + 1]; ++j) {
         const double* q = &rho[3 * (int64_t)(j - off[c])];
         double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+        const double mi = mass_of(p, mass, perm[j]);
         rr += q2;
+        rrm += mi * q2;
         for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) I[a][b] += p->mass * ((a == b ? q2 : 0.0) - q[a] * q[b]);
+          for (int b = 0; b < 3; ++b) I[a][b] += mi * ((a == b ? q2 : 0.0) - q[a] * q[b]);
       }
       double w[3] = {0.0, 0.0, 0.0};
       int apply = 0;
@@ -422,8 +439,15 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
         double e2 = rr > 0.0 ? 2.0 / rr : 0.0; /* 1/|rho_1|^2 */
         const double* q = &rho[0];
         double along = (q[0] * dL[0] + q[1] * dL[1] + q[2] * dL[2]) * e2;
-        if (rr > 0.0) {
+        if (rr > 0.0 && !mass) {
           for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q[d]) / (p->mass * rr);
+          apply = 1;
+        } else if (rr > 0.0) {
+          /* unequal masses (R24): m_1 rho_1 + m_2 rho_2 = 0 keeps the pair on one line, and I
+           * acts as sum m_i |rho_i|^2 normal to it */
+          double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+          double al = (q[0] * dL[0] + q[1] * dL[1] + q[2] * dL[2]) / qq;
+          for (int d = 0; d < 3; ++d) w[d] = (dL[d] - al * q[d]) / rrm;
           apply = 1;
         }
       } else {
@@ -465,8 +489,9 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
     double* r2 = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     double* v2 = (double*)malloc(sizeof(double) * 3 * (size_t)n);
     int32_t* id2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
-    if (!r2 || !v2 || !id2) {
-      free(r2); free(v2); free(id2);
+    double* m2 = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    if (!r2 || !v2 || !id2 || !m2) {
+      free(r2); free(v2); free(id2); free(m2);
       free(key); free(cnt); free(off); free(cur); free(perm);
       return -2;
     }
@@ -477,11 +502,13 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
         v2[3 * j + d] = v[3 * i + d];
       }
       id2[j] = id ? id[i] : (int32_t)i;
+      m2[j] = mass ? mass[i] : 0.0;
     }
     memcpy(r, r2, sizeof(double) * 3 * (size_t)n);
     memcpy(v, v2, sizeof(double) * 3 * (size_t)n);
     if (id) memcpy(id, id2, sizeof(int32_t) * (size_t)n);
-    free(r2); free(v2); free(id2);
+    if (mass) memcpy(mass, m2, sizeof(double) * (size_t)n);
+    free(r2); free(v2); free(id2); free(m2);
   }
 
   free(key); free(cnt); free(off); free(cur); free(perm);

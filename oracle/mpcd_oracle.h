@@ -40,6 +40,10 @@
  *       otherwise are left uncorrected.  Positions within a cell are taken on the shifted
  *       grid (the fractional part of (r - s)/a), so a cell cut by the periodic boundary is
  *       whole.  Not with walls: virtual particles have no positions.
+ *   R24 optional per-particle masses (the masses Listing 4 sums): M = sum m_i,
+ *       P = sum m_i v_i, E = sum m_i v_i^2 / 2, the thermostat's kinetic energy and the
+ *       angular-momentum correction weighted by m_i, the centre of mass of R23 mass-weighted.
+ *       The rotation of v - u is unchanged; it conserves sum m_i v_i and sum m_i |v_i|^2 / 2.
  */
 #ifndef MPCD_ORACLE_H
 #define MPCD_ORACLE_H
@@ -108,6 +112,13 @@ void orc_init(const orc_params* p, int64_t n, double* r, double* v);
 int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, int32_t* id,
              int32_t* keys, int32_t* counts, int32_t* offsets, int32_t* perm,
              double* moments, double* shift);
+/* orc_step with per-particle masses (R24): mass[N] in storage order (> 0; NULL: every
+ * particle has p->mass), permuted with the state on re-sort steps.  The cell sums, the
+ * thermostat's kinetic energy and the angular-momentum correction weight by it; virtual wall
+ * particles keep p->mass. */
+int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, int32_t* id, double* mass,
+               int32_t* keys_out, int32_t* counts_out, int32_t* offsets_out, int32_t* perm_out,
+               double* moments_out, double* shift_out);
 
 #ifdef __cplusplus
 }

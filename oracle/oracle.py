@@ -117,6 +117,8 @@ def lib():
             L.orc_init.restype = None
             L.orc_step.argtypes = [pp, ctypes.c_int64, ctypes.c_int64, dp, dp, ip, ip, ip, ip, ip, dp, dp]
             L.orc_step.restype = ctypes.c_int
+            L.orc_step_m.argtypes = [pp, ctypes.c_int64, ctypes.c_int64, dp, dp, ip, dp, ip, ip, ip, ip, dp, dp]
+            L.orc_step_m.restype = ctypes.c_int
             _lib = L
         return _lib
 
@@ -197,15 +199,16 @@ def init(p: Params, n: int):
 
 
 class State:
-    """Oracle state: positions, velocities and particle ids in storage order, plus the
-    number of completed steps."""
+    """Oracle state: positions, velocities, particle ids and (optionally, R24) per-particle
+    masses in storage order, plus the number of completed steps."""
 
-    def __init__(self, r, v, ids=None, t: int = 0):
+    def __init__(self, r, v, ids=None, t: int = 0, m=None):
         self.r = np.ascontiguousarray(np.array(r, dtype=np.float64).reshape(-1, 3))
         self.v = np.ascontiguousarray(np.array(v, dtype=np.float64).reshape(-1, 3))
         n = self.r.shape[0]
         self.id = (np.arange(n, dtype=np.int32) if ids is None
                    else np.ascontiguousarray(np.asarray(ids, dtype=np.int32)))
+        self.m = None if m is None else np.ascontiguousarray(np.array(m, dtype=np.float64).reshape(n))
         self.t = int(t)
 
     @property
@@ -217,8 +220,12 @@ class State:
         order = np.argsort(self.id, kind="stable")
         return self.r[order], self.v[order]
 
+    def masses_by_id(self):
+        order = np.argsort(self.id, kind="stable")
+        return None if self.m is None else self.m[order]
+
     def copy(self) -> "State":
-        return State(self.r.copy(), self.v.copy(), self.id.copy(), self.t)
+        return State(self.r.copy(), self.v.copy(), self.id.copy(), self.t, None if self.m is None else self.m.copy())
 
 
 def step(p: Params, st: State, debug: bool = False):
@@ -236,8 +243,8 @@ def step(p: Params, st: State, debug: bool = False):
         perm = np.zeros(n, np.int32)
         moments = np.zeros((C, 5))
         out["ids"] = st.id.copy()
-    rc = lib().orc_step(ctypes.byref(p), n, st.t + 1, _dp(st.r), _dp(st.v), _ip(st.id),
-                        _ip(keys), _ip(counts), _ip(offsets), _ip(perm), _dp(moments), _dp(s))
+    rc = lib().orc_step_m(ctypes.byref(p), n, st.t + 1, _dp(st.r), _dp(st.v), _ip(st.id), _dp(st.m),
+                          _ip(keys), _ip(counts), _ip(offsets), _ip(perm), _dp(moments), _dp(s))
     if rc != 0:
         raise RuntimeError("orc_step failed with %d" % rc)
     st.t += 1

@@ -19,7 +19,7 @@ MUTANTS = [
     ("parallel part dropped", "out[k] = par * n[k] + c * perp + s * cr[k];",
      "out[k] = c * perp + s * cr[k];", "rotation"),
     ("rotation about v instead of v - u", "d[k] = v[k] - u[k];", "d[k] = v[k];", "galilean or conserves"),
-    ("mass weight dropped", "P[d] += m * vi[d];", "P[d] += vi[d];", "closed_form or conserves"),
+    ("mass weight dropped", "P[d] += mi * vi[d];", "P[d] += vi[d];", "closed_form or conserves or mass"),
     ("key index order swapped", "return c[0] + (int64_t)p->L[0] * (c[1] + (int64_t)p->L[1] * c[2]);",
      "return c[1] + (int64_t)p->L[1] * (c[0] + (int64_t)p->L[0] * c[2]);", "brute_force or face_point"),
     ("shift sign flipped", "double q = (r[d] - s[d]) / p->a;\n    int64_t k = (int64_t)floor(q);",
@@ -42,12 +42,17 @@ MUTANTS = [
     ("MBS target without kT", "? p->kT * orc_mbs_gamma(", "? orc_mbs_gamma(", "mbs"),
     ("angular correction sign flipped", "for (int d = 0; d < 3; ++d) vi[d] += corr[d];",
      "for (int d = 0; d < 3; ++d) vi[d] -= corr[d];", "angular or omega or two_particle"),
-    ("inertia tensor without the |rho|^2 term", "I[a][b] += p->mass * ((a == b ? q2 : 0.0) - q[a] * q[b]);",
-     "I[a][b] += p->mass * (0.0 - q[a] * q[b]);", "angular or omega or two_particle"),
+    ("inertia tensor without the |rho|^2 term", "I[a][b] += mi * ((a == b ? q2 : 0.0) - q[a] * q[b]);",
+     "I[a][b] += mi * (0.0 - q[a] * q[b]);", "angular or omega or two_particle"),
     ("positions not taken about the centre of mass", "= p->a * (rho[3 * (int64_t)(j - off[c]) + d] - mean[d]);",
      "= p->a * (rho[3 * (int64_t)(j - off[c]) + d] - 0.0 * mean[d]);", "angular or omega or two_particle"),
     ("two-particle omega off by two", "w[d] = (dL[d] - along * q[d]) / (p->mass * rr);",
      "w[d] = (dL[d] - along * q[d]) / (2.0 * p->mass * rr);", "angular or omega or two_particle"),
+    ("cell mass counts particles", "      M += mi;\n", "      M += 1.0;\n", "mass"),
+    ("thermostat energy unweighted", "K += 0.5 * mi * (vi[d] - u[d]) * (vi[d] - u[d]);",
+     "K += 0.5 * (vi[d] - u[d]) * (vi[d] - u[d]);", "mass"),
+    ("masses left behind on re-sort", "m2[j] = mass ? mass[i] : 0.0;", "m2[j] = mass ? mass[j] : 0.0;", "mass"),
+    ("centre of mass unweighted", "mean[d] += mass ? mass[perm[j]] * l[d] : l[d];", "mean[d] += l[d];", "mass"),
     ("cofactor indices swapped", "cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a2][b1];",
      "cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a1][b2];", "angular or omega or two_particle"),
 ]
@@ -67,7 +72,7 @@ def test_pins_catch_mutant(tmp_path, name, old, new, select):
     tests = [os.path.join(ROOT, "tests", f) for f in
              ("test_oracle_philox.py", "test_oracle_geometry.py", "test_oracle_rotation.py",
               "test_oracle_step.py", "test_oracle_walls.py", "test_oracle_thermostat.py",
-              "test_oracle_angular.py")]
+              "test_oracle_angular.py", "test_oracle_masses.py")]
     res = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
                           "-k", select + " and not poiseuille and not relaxes"] + tests,
                          cwd=ROOT, env=env, capture_output=True, text=True)
