@@ -72,9 +72,10 @@ ALGO_STEP_BYTES_MIXED = 64.0
 NCU_TRAFFIC = {("mixed", "collide"): (72.07, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)"),
                ("fp64", "rotate"): (78.47, "profiles/fp64_L128_kernels_full.md (sorted regime, non-re-sort step)")}
 # timed beside an FP64 run: the mixed form at 256^3, the 256-box ensemble, the walled
-# channel with each cell thermostat, and the angular-momentum-conserving collision
+# channel with each cell thermostat, the angular-momentum-conserving collision and per-particle
+# masses
 FORMS = ("mixed_L256", "batched_256", "poiseuille_256x64x64", "poiseuille_256x64x64_mbs", "fp64_L128_angular",
-         "mixed_L128_angular")
+         "mixed_L128_angular", "fp64_L128_masses")
 
 
 def parse():
@@ -235,7 +236,10 @@ def open_box(abi, inputs, name, rank):
             q.seed = replicas.ensemble_seed(q.seed, rank)
         return w, plist[0], abi.Box(batch=plist), True
     p = abi.params_from_workload(w, seed=replicas.box_seed(w.seed, rank))
-    return w, p, abi.Box(p), False
+    box = abi.Box(p)
+    if getattr(w, "mass_range", ()):
+        box.set_masses(inputs.particle_masses(box.n, p.seed, *w.mass_range, mass=p.mass))
+    return w, p, box, False
 
 
 def timed_steps(abi, torch, dist, box, stream, steps, world, sampler=None):

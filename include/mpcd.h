@@ -125,6 +125,19 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v);
  * runs on the device.  Synchronises. */
 int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64_t t);
 
+/* Per-particle masses (the m of the cell sums sum m v and sum m, Sec. 3.3 Listing 4), FP64
+ * form: m[n] in particle-id order, every value finite and > 0, n = mpcd_num_particles.
+ * They weight the centre-of-mass velocity, the moments, the thermostat's kinetic energy and
+ * the angular-momentum correction (whose centre becomes mass-weighted); the rotation of
+ * v - u keeps sum m v and sum m v^2 / 2.  Virtual wall particles and the initial velocities
+ * keep params.mass.  Masses follow their particles through re-sorts and mpcd_set_state.
+ * m = NULL restores the box mass.  With masses the collision takes the per-cell kernel.
+ * Errors: MPCD_ERR_ARG (mixed form: its 32-byte record has no field for a mass; n != N; a
+ * mass not finite or <= 0, named in the message).  Synchronises. */
+int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m);
+/* The masses in particle-id order (params.mass everywhere when none were set). */
+int mpcd_get_masses(mpcd_t* h, double* m);
+
 /* Same as mpcd_get_state / mpcd_set_state with device arrays.  get_state_device is enqueued
  * on the handle's stream without a host synchronisation; set_state_device checks the state
  * as mpcd_set_state does, which synchronises once. */

@@ -29,7 +29,7 @@ EXPORTS = [
     "mpcd_set_state", "mpcd_get_state_device", "mpcd_set_state_device", "mpcd_record_moments",
     "mpcd_cell_moments", "mpcd_debug_sort", "mpcd_timing", "mpcd_timing_read", "mpcd_launch_count",
     "mpcd_last_error", "mpcd_version", "mpcd_step_fp64_noalloc", "mpcd_box_offsets", "mpcd_get_tuning",
-    "mpcd_set_tuning", "mpcd_autotune",
+    "mpcd_set_tuning", "mpcd_autotune", "mpcd_set_masses", "mpcd_get_masses",
 ]
 MPCD_NOALLOC_MAX_PARTICLES = 1 << 19
 MPCD_NOALLOC_MAX_CELLS = 1 << 17
@@ -136,6 +136,8 @@ def lib():
                 "mpcd_num_boxes": ([H], i32),
                 "mpcd_get_state": ([H, dp, dp], ctypes.c_int),
                 "mpcd_set_state": ([H, i64, dp, dp, i64], ctypes.c_int),
+                "mpcd_set_masses": ([H, i64, dp], ctypes.c_int),
+                "mpcd_get_masses": ([H, dp], ctypes.c_int),
                 "mpcd_get_state_device": ([H, dp, dp], ctypes.c_int),
                 "mpcd_set_state_device": ([H, i64, dp, dp, i64], ctypes.c_int),
                 "mpcd_record_moments": ([H, i32], ctypes.c_int),
@@ -236,6 +238,22 @@ def mpcd_get_state(h, r=None, v=None):
     v = np.empty((n, 3)) if v is None else v
     _check(lib().mpcd_get_state(h, _ptr(r), _ptr(v)), h)
     return r, v
+
+
+def mpcd_set_masses(h, m):
+    """Per-particle masses in particle-id order (FP64 form); None restores the box mass."""
+    n = mpcd_num_particles(h)
+    if m is None:
+        _check(lib().mpcd_set_masses(h, n, None), h)
+        return
+    m = np.ascontiguousarray(np.asarray(m, dtype=np.float64).reshape(n))
+    _check(lib().mpcd_set_masses(h, n, _ptr(m)), h)
+
+
+def mpcd_get_masses(h):
+    m = np.empty(mpcd_num_particles(h))
+    _check(lib().mpcd_get_masses(h, _ptr(m)), h)
+    return m
 
 
 def mpcd_set_state(h, r, v, t: int = 0):
@@ -382,6 +400,9 @@ class Box:
 
     def set_state(self, r, v, t: int = 0):
         mpcd_set_state(self.h, r, v, t)
+
+    def set_masses(self, m):
+        mpcd_set_masses(self.h, m)
 
     def moments(self):
         return mpcd_cell_moments(self.h)

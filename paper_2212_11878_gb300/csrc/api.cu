@@ -44,6 +44,8 @@ struct mpcd_s {
   Geom geom{};
   int64_t n = 0, ncell = 0;
   Fp64Bufs f64{};
+  double* mass_buf[3] = {};  // FP64 particle masses: storage order (two buffer sets), id order
+  bool masses = false;       // f64.m points at mass_buf
   Scratch scr{};
   MixBufs mix{};
   MixScratch mscr{};
@@ -282,7 +284,7 @@ int enqueue_step(mpcd_t* h, bool moments, int par = 0) {
   if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(s.count, s.offset, s.partial, g.ncell, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotScatter, [&] { launch_scatter(g, s, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotCollide, [&] { launch_collide_fp64(g, h->f64, s, h->ctl, moments, h->stream); }))) return rc;
-  if (fp64_dense_collide(g, s))
+  if (fp64_dense_collide(g, h->f64, s))
     if ((rc = run_slot(h, kSlotRotate, [&] { launch_rotate_fp64(g, h->f64, s, h->ctl, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step(g, h->ctl, h->stream); }))) return rc;
   return MPCD_OK;
@@ -612,7 +614,8 @@ int mpcd_step(mpcd_t* h, int64_t nsteps) {
     h->t += 1;
     h->last_resorted = mixed || resort_at(h, h->t);
     if (h->last_resorted) h->cur ^= 1;
-    h->perm_sorted = !mixed && (h->last_resorted || h->geom.walls || h->geom.thermostat || h->geom.angular);
+    h->perm_sorted =
+        !mixed && (h->last_resorted || h->geom.walls || h->geom.thermostat || h->geom.angular || h->masses);
     h->any_step = true;
     h->moments_valid = h->record_moments;
   }
@@ -641,6 +644,50 @@ int mpcd_get_state_device(mpcd_t* h, double* r_dev, double* v_dev) {
     launch_get_state_fp64(h->geom, h->f64, h->cur, r_dev, v_dev, h->stream);
   MPCD_TRY(h, cudaGetLastError());
   h->launches += 1;
+  return MPCD_OK;
+}
+
+int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (h->precision != MPCD_FP64)
+    return fail(h, MPCD_ERR_ARG, "particle masses need the FP64 form (the 32-byte mixed record has no field for them)");
+  if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
+  if (!m) {
+    h->masses = false;
+    h->f64.m[0] = h->f64.m[1] = nullptr;
+  } else {
+    for (int64_t i = 0; i < n; ++i)
+      if (!(m[i] > 0.0) || !std::isfinite(m[i]))
+        return fail(h, MPCD_ERR_ARG, "masses must be finite and > 0 (particle " + std::to_string(i) + ")");
+    for (int k = 0; k < 3; ++k)
+      if (!h->mass_buf[k] && (rc = dalloc(h, &h->mass_buf[k], n > 0 ? n : 1))) return rc;
+    MPCD_TRY(h, cudaMemcpyAsync(h->mass_buf[2], m, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+    // into the storage order of the current buffer set; a re-sort carries them along
+    launch_gather_masses(n, h->mass_buf[2], h->f64.id[h->cur], h->mass_buf[h->cur], h->stream);
+    MPCD_TRY(h, cudaGetLastError());
+    h->launches += 1;
+    h->masses = true;
+    h->f64.m[0] = h->mass_buf[0];
+    h->f64.m[1] = h->mass_buf[1];
+  }
+  // the per-cell kernel sums with masses; the dense pair (cell_frame + rotate) only without
+  h->per_step[kSlotRotate] = (!h->geom.walls && !h->geom.thermostat && !h->geom.angular && !h->masses) ? 1 : 0;
+  drop_graph(h);  // the step graph holds the buffer pointers and the kernel choice
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPCD_OK;
+}
+
+int mpcd_get_masses(mpcd_t* h, double* m) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (!m) return fail(h, MPCD_ERR_ARG, "NULL output");
+  if (!h->masses) {
+    for (int64_t i = 0; i < h->n; ++i) m[i] = h->geom.mass;
+    return MPCD_OK;
+  }
+  MPCD_TRY(h, cudaMemcpyAsync(m, h->mass_buf[2], sizeof(double) * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   return MPCD_OK;
 }
 
@@ -692,6 +739,9 @@ int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const doubl
   else
     launch_set_state_fp64(h->geom, h->f64, r_dev, v_dev, h->stream);
   MPCD_TRY(h, cudaGetLastError());
+  if (h->masses)  // the new storage is in particle-id order
+    MPCD_TRY(h, cudaMemcpyAsync(h->mass_buf[0], h->mass_buf[2], sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice,
+                                h->stream));
   h->mixed_keys_valid = false;
   h->ctl_host = Ctl{};
   h->ctl_host.t = t;

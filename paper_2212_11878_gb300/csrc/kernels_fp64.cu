@@ -260,6 +260,47 @@ __device__ __forceinline__ void cell_sums(const Fp64Bufs& b, int cur, const int3
   }
 }
 
+// With particle masses (Listing 4 sums m v and m): exact sums of the rounded products
+// m_i v_i, m_i v_i.v_i and of m_i, each rounded once; the order of the members does not matter.
+template <int MOMENTS>
+__device__ void cell_sums_mass(const Fp64Bufs& b, int cur, const double* __restrict__ mp, const int32_t* pm, int n,
+                               double P[3], double& SE, double& M) {
+  Fx128 a0, a1, a2, ae, am;
+  fx_zero(a0);
+  fx_zero(a1);
+  fx_zero(a2);
+  fx_zero(ae);
+  fx_zero(am);
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    const int i = pm[j];
+    const double m = mp[i], v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
+    ok &= fx_add(a0, m * v0);
+    ok &= fx_add(a1, m * v1);
+    ok &= fx_add(a2, m * v2);
+    ok &= fx_add(am, m);
+    if (MOMENTS) ok &= fx_add(ae, m * fma(v0, v0, fma(v1, v1, v2 * v2)));
+  }
+  if (ok) {
+    P[0] = fx_value(a0);
+    P[1] = fx_value(a1);
+    P[2] = fx_value(a2);
+    M = fx_value(am);
+    SE = MOMENTS ? fx_value(ae) : 0.0;
+    return;
+  }
+  P[0] = P[1] = P[2] = SE = M = 0.0;  // a term beyond the exact range: plain FP64 sums
+  for (int j = 0; j < n; ++j) {
+    const int i = pm[j];
+    const double m = mp[i], v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
+    P[0] += m * v0;
+    P[1] += m * v1;
+    P[2] += m * v2;
+    M += m;
+    if (MOMENTS) SE += m * fma(v0, v0, fma(v1, v1, v2 * v2));
+  }
+}
+
 __device__ __forceinline__ void write_moments(const Geom& g, Scratch& s, int64_t c, int n, const double S[3], double SE) {
   double* mo = s.moments + 5 * c;
   mo[0] = static_cast<double>(n) * g.mass;
@@ -282,15 +323,25 @@ __device__ __forceinline__ double cell_local(const Geom& g, double r, double s) 
 // I = m sum (|rho|^2 1 - rho rho^T).  Two particles: the pseudo-inverse (I acts as m sum
 // |rho|^2 normal to their separation); a singular I otherwise: no correction (omega = 0).
 // after(v) gives a member's velocity after the rotation and the thermostat.
+// With particle masses mp the centre is mass-weighted and L and I weight by m_i.
 template <typename After>
 __device__ void cell_omega(const Geom& g, const Fp64Bufs& b, int cur, const int32_t* pm, int n, const double s[3],
                            After after, double mean[3], double w[3]) {
+  const double* __restrict__ mp = b.m[cur];
   mean[0] = mean[1] = mean[2] = 0.0;
   w[0] = w[1] = w[2] = 0.0;
-  for (int j = 0; j < n; ++j)
-    for (int d = 0; d < 3; ++d) mean[d] += cell_local(g, b.r[cur][d][pm[j]], s[d]);
-  for (int d = 0; d < 3; ++d) mean[d] /= static_cast<double>(n);
-  double dL[3] = {0.0, 0.0, 0.0}, I[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, rr = 0.0, q0[3];
+  double Mw = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double mi = mp ? mp[pm[j]] : 1.0;
+    Mw += mi;
+    for (int d = 0; d < 3; ++d) {
+      const double l = cell_local(g, b.r[cur][d][pm[j]], s[d]);
+      mean[d] += mp ? mi * l : l;
+    }
+  }
+  for (int d = 0; d < 3; ++d) mean[d] /= mp ? Mw : static_cast<double>(n);
+  double dL[3] = {0.0, 0.0, 0.0}, I[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, rr = 0.0, rrm = 0.0,
+         q0[3];
   for (int j = 0; j < n; ++j) {
     const int i = pm[j];
     double q[3], v[3], va[3];
@@ -303,18 +354,24 @@ __device__ void cell_omega(const Geom& g, const Fp64Bufs& b, int cur, const int3
       for (int d = 0; d < 3; ++d) q0[d] = q[d];
     after(va[0], va[1], va[2]);
     const double dv0 = v[0] - va[0], dv1 = v[1] - va[1], dv2 = v[2] - va[2];
-    dL[0] += g.mass * (q[1] * dv2 - q[2] * dv1);
-    dL[1] += g.mass * (q[2] * dv0 - q[0] * dv2);
-    dL[2] += g.mass * (q[0] * dv1 - q[1] * dv0);
+    const double mi = mp ? mp[i] : g.mass;
+    dL[0] += mi * (q[1] * dv2 - q[2] * dv1);
+    dL[1] += mi * (q[2] * dv0 - q[0] * dv2);
+    dL[2] += mi * (q[0] * dv1 - q[1] * dv0);
     const double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
     rr += q2;
+    rrm += mi * q2;
     for (int x = 0; x < 3; ++x)
-      for (int y = 0; y < 3; ++y) I[x][y] += g.mass * ((x == y ? q2 : 0.0) - q[x] * q[y]);
+      for (int y = 0; y < 3; ++y) I[x][y] += mi * ((x == y ? q2 : 0.0) - q[x] * q[y]);
   }
   if (n == 2) {
-    if (rr > 0.0) {
+    if (rr > 0.0 && !mp) {
       const double along = (q0[0] * dL[0] + q0[1] * dL[1] + q0[2] * dL[2]) * (2.0 / rr);
       for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q0[d]) / (g.mass * rr);
+    } else if (rr > 0.0) {  // unequal masses: I acts as sum m_i |rho_i|^2 normal to the pair
+      const double qq = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+      const double along = (q0[0] * dL[0] + q0[1] * dL[1] + q0[2] * dL[2]) / qq;
+      for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q0[d]) / rrm;
     }
     return;
   }
@@ -340,11 +397,29 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
   const int n = s.offset[c + 1] - o;
   int32_t* __restrict__ pm = s.perm + o;
   sort_entries(pm, n);
-  double S[3], SE;
-  cell_sums<MOMENTS>(b, cur, pm, n, S, SE);
-  if (MOMENTS) write_moments(g, s, c, n, S, SE);
+  const double* __restrict__ mp = b.m[cur];  // particle masses, or null for the box mass
+  double S[3], SE, Mc = 0.0;
+  if (mp) {
+    cell_sums_mass<MOMENTS>(b, cur, mp, pm, n, S, SE, Mc);  // S = sum m v, SE = sum m v.v
+    if (MOMENTS) {
+      double* mo = s.moments + 5 * c;
+      mo[0] = Mc;
+      mo[1] = S[0];
+      mo[2] = S[1];
+      mo[3] = S[2];
+      mo[4] = 0.5 * SE;
+    }
+  } else {
+    cell_sums<MOMENTS>(b, cur, pm, n, S, SE);
+    if (MOMENTS) write_moments(g, s, c, n, S, SE);
+  }
   if (n == 0) return;
   double u0 = S[0] * inv_count(n), u1 = S[1] * inv_count(n), u2 = S[2] * inv_count(n);
+  if (mp) {
+    u0 = S[0] / Mc;
+    u1 = S[1] / Mc;
+    u2 = S[2] / Mc;
+  }
   bool virt = false;
   if (WALLS) {
     const int64_t layer = c / ((int64_t)g.L[0] * g.L[1]);
@@ -357,10 +432,17 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
       gauss_pair(w.x, w.y, g0, g1);
       gauss_pair(w.z, w.w, g2, g3);
       const double sd = sqrt(Mv * g.kT);
-      const double M = (double)n * m + Mv;
-      u0 = (m * S[0] + sd * g0) / M;
-      u1 = (m * S[1] + sd * g1) / M;
-      u2 = (m * S[2] + sd * g2) / M;
+      if (mp) {  // virtual particles keep the box mass
+        const double M = Mc + Mv;
+        u0 = (S[0] + sd * g0) / M;
+        u1 = (S[1] + sd * g1) / M;
+        u2 = (S[2] + sd * g2) / M;
+      } else {
+        const double M = (double)n * m + Mv;
+        u0 = (m * S[0] + sd * g0) / M;
+        u1 = (m * S[1] + sd * g1) / M;
+        u2 = (m * S[2] + sd * g2) / M;
+      }
       virt = true;
     }
   }
@@ -376,7 +458,7 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
       double v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];
       apply_frame(R, bv, v0, v1, v2);
       const double d0 = v0 - u0, d1 = v1 - u1, d2 = v2 - u2;
-      K += 0.5 * g.mass * fma(d0, d0, fma(d1, d1, d2 * d2));
+      K += 0.5 * (mp ? mp[i] : g.mass) * fma(d0, d0, fma(d1, d1, d2 * d2));
     }
     if (K > 0.0) {
       // R14: relative kinetic energy 3/2 (n - 1) kT; MBS: kT times a Gamma(3/2 (n - 1)) draw
@@ -426,6 +508,7 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
       b.v[ob][1][dst] = v1;
       b.v[ob][2][dst] = v2;
       b.id[ob][dst] = b.id[cur][i];
+      if (mp) b.m[ob][dst] = mp[i];
     } else if (rotate) {
       b.v[cur][0][i] = v0;
       b.v[cur][1][i] = v1;
@@ -693,12 +776,22 @@ void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl,
   }
 }
 
-bool fp64_dense_collide(const Geom& g, const Scratch& s) {
-  return !g.walls && !g.thermostat && !g.angular && s.frame && s.inv;
+bool fp64_dense_collide(const Geom& g, const Fp64Bufs& b, const Scratch& s) {
+  return !g.walls && !g.thermostat && !g.angular && !b.m[0] && s.frame && s.inv;
+}
+
+__global__ void k_gather_masses(int64_t n, const double* __restrict__ m_by_id, const int32_t* __restrict__ id,
+                                double* __restrict__ dst) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    dst[j] = m_by_id[id[j]];
+}
+
+void launch_gather_masses(int64_t n, const double* m_by_id, const int32_t* id, double* dst, cudaStream_t st) {
+  if (n > 0) k_gather_masses<<<grid_for(n), kThreads, 0, st>>>(n, m_by_id, id, dst);
 }
 
 void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st) {
-  if (!fp64_dense_collide(g, s)) {
+  if (!fp64_dense_collide(g, b, s)) {
     launch_collide_fp64_generic(g, b, s, ctl, moments, st);
     return;
   }

@@ -60,6 +60,7 @@ struct Fp64Bufs {
   double* r[2][3];
   double* v[2][3];
   int32_t* id[2];
+  double* m[2];  // per-particle masses in storage order; null: every particle has the box mass
 };
 
 // Mixed-precision particle record, 32 bytes (one DRAM sector): in-cell offsets in cell
@@ -112,9 +113,12 @@ void launch_scan(const int32_t* count, int32_t* offset, int32_t* partial, int64_
 void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
 void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
 void launch_scatter(const Geom& g, Scratch s, cudaStream_t st);
-// periodic boxes without thermostat (fp64_dense_collide): cell_frame here, then
-// launch_rotate_fp64; otherwise one thread per cell here and no rotate launch
-bool fp64_dense_collide(const Geom& g, const Scratch& s);
+// periodic boxes without thermostat, angular-momentum correction or particle masses
+// (fp64_dense_collide): cell_frame here, then launch_rotate_fp64; otherwise one thread per
+// cell here and no rotate launch
+bool fp64_dense_collide(const Geom& g, const Fp64Bufs& b, const Scratch& s);
+// dst[j] = m_by_id[id[j]]: particle masses into storage order
+void launch_gather_masses(int64_t n, const double* m_by_id, const int32_t* id, double* dst, cudaStream_t st);
 void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st);
 void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
 // one thread per cell for every box kind (no frame buffer needed)

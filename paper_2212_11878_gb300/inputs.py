@@ -35,6 +35,7 @@ class Workload:
     g: tuple = (0.0, 0.0, 0.0)
     thermostat: int = 0
     angular: int = 0
+    mass_range: tuple = ()           # per-particle masses uniform in this range (times m), FP64 form
     steps: int = 100
     notes: str = ""
 
@@ -74,6 +75,8 @@ WORKLOADS = {
                                      notes="bounce-back walls in z, body force along x"),
     "fp64_L128_angular": Workload("fp64_L128_angular", (128, 128, 128), seed=BASE_SEED + 1, steps=1000, resort_k=10,
                                   angular=1, notes="angular-momentum-conserving collision, FP64"),
+    "fp64_L128_masses": Workload("fp64_L128_masses", (128, 128, 128), seed=BASE_SEED + 1, steps=1000, resort_k=10,
+                                 mass_range=(0.5, 4.0), notes="per-particle masses 0.5-4 m, FP64"),
     "mixed_L128_angular": Workload("mixed_L128_angular", (128, 128, 128), seed=BASE_SEED + 2, steps=500,
                                    precision="mixed", resort_k=1, angular=1,
                                    notes="angular-momentum-conserving collision, mixed form (per-cell path)"),
@@ -82,6 +85,12 @@ WORKLOADS = {
                                          g=(1e-3, 0.0, 0.0), thermostat=2,
                                          notes="the channel with the Maxwell-Boltzmann-scaling cell thermostat"),
 }
+
+
+def particle_masses(n: int, seed: int, lo: float, hi: float, mass: float = 1.0):
+    """Per-particle masses uniform in [lo, hi) times mass, in particle-id order."""
+    rng = np.random.Generator(np.random.Philox(seed + 7))
+    return np.ascontiguousarray(rng.uniform(lo, hi, n) * mass)
 
 
 def uniform_gaussian_state(L, n: int, seed: int, a: float = 1.0, kT: float = 1.0, mass: float = 1.0):

@@ -12,7 +12,7 @@ from parity import assert_sort_equal, assert_state_close, oracle_params
 pytestmark = pytest.mark.gpu
 
 
-def angular_multiplier(p, rr, ref, prev):
+def angular_multiplier(p, rr, ref, prev, m=None):
     """Per-particle (id order) factor on the 1e-12 bound for the angular-momentum-conserving
     collision.  Its correction omega = I^-1 dL turns rounding differences of the rotated
     velocities (a few ulps: the two sides round the rotation differently) into velocity
@@ -33,21 +33,25 @@ def angular_multiplier(p, rr, ref, prev):
         if len(idx) < 2:
             mult[idx] = prev[idx]
             continue
-        rho = loc[idx] - loc[idx].mean(axis=0)
-        I = (rho * rho).sum() * np.eye(3) - rho.T @ rho
+        w = np.ones(len(idx)) if m is None else m[idx]
+        rho = loc[idx] - (w[:, None] * loc[idx]).sum(axis=0) / w.sum()
+        I = (w * (rho * rho).sum(axis=1)).sum() * np.eye(3) - (w[:, None] * rho).T @ rho
         ev = np.linalg.eigvalsh(I)
         cond = ev[-1] / max(ev[0], ev[-1] * 1e-16) if len(idx) > 2 else ev[-1] / max(ev[1], ev[-1] * 1e-16)
         mult[idx] = max(1.0, cond / 100.0, prev[idx].max())
     return mult
 
 
-def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True):
-    """Advance the library and the oracle from the same state; compare after every step."""
+def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True, masses=None):
+    """Advance the library and the oracle from the same state (and per-particle masses, in
+    particle-id order); compare after every step."""
     box = abi.Box(p)
     try:
         box.set_state(r, v, t0)
+        if masses is not None:
+            box.set_masses(masses)
         op = oracle_params(orc, p)
-        st = orc.State(r, v, t=t0)
+        st = orc.State(r, v, t=t0, m=masses)
         mult = np.ones(len(r))
         for k in range(steps):
             box.step(1)
@@ -57,7 +61,7 @@ def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True):
             rg, vg = box.state()
             rr, vr = st.by_id()
             if p.angular:
-                mult = angular_multiplier(p, rr, ref, mult)
+                mult = angular_multiplier(p, rr, ref, mult, masses)
             assert_state_close(rg, vg, rr, vr, p, tol=1e-12 * mult, what="step %d" % (t0 + k + 1))
         return box.state(), st
     finally:
@@ -96,6 +100,54 @@ def test_steps_match_oracle(orc, name):
     n = int(round(p.ppc * p.L[0] * p.L[1] * p.L[2]))
     r, v = inputs.uniform_gaussian_state(tuple(p.L), n, 31 + len(name), a=p.a, kT=p.kT, mass=p.mass)
     run_pair(orc, p, r, v, steps=6, t0=3)
+
+
+MASS_CASES = {
+    "masses": dict(L=(7, 6, 5)),
+    "masses_walls_thermostat": dict(L=(6, 5, 8), walls_z=1, g=(0.01, 0.0, 0.0), thermostat=1, ppc=12),
+    "masses_mbs_resort": dict(L=(6, 6, 6), thermostat=2, resort_k=2),
+    "masses_angular": dict(L=(6, 6, 5), angular=1),
+    "masses_angular_sparse": dict(L=(7, 7, 7), angular=1, ppc=3, resort_k=3),
+}
+
+
+@pytest.mark.parametrize("name", list(MASS_CASES))
+def test_particle_masses_match_oracle(orc, name):
+    """Per-particle masses (Listing 4's m), 0.5 to 4 times the box mass, against the oracle
+    with the same masses; keys and sort bit-exact, state within the FP64 bound."""
+    p = abi.make_params(seed=2000 + len(name), **MASS_CASES[name])
+    n = int(round(p.ppc * p.L[0] * p.L[1] * p.L[2]))
+    r, v = inputs.uniform_gaussian_state(tuple(p.L), n, 41 + len(name), a=p.a)
+    m = np.random.default_rng(len(name)).uniform(0.5, 4.0, n) * p.mass
+    run_pair(orc, p, r, v, steps=6, t0=2, masses=m)
+
+
+def test_particle_masses_api():
+    p = abi.make_params((8, 8, 8), seed=5, resort_k=2)
+    n = int(round(p.ppc * 512))
+    m = np.random.default_rng(1).uniform(0.5, 3.0, n)
+    with abi.Box(p) as box, abi.Box(p) as plain:
+        assert np.array_equal(abi.mpcd_get_masses(box.h), np.full(n, p.mass))
+        box.set_masses(m)
+        box.step(5)  # two re-sorts
+        assert np.array_equal(abi.mpcd_get_masses(box.h), m)
+        r, v = box.state()
+        box.set_state(r, v, 5)  # storage back to id order: masses follow
+        assert np.array_equal(abi.mpcd_get_masses(box.h), m)
+        # the box mass restored: the same steps as a box that never had masses
+        r0, v0 = plain.state()
+        box.set_state(r0, v0, 0)
+        box.set_masses(None)
+        box.step(3)
+        plain.step(3)
+        assert np.array_equal(box.state()[1], plain.state()[1])
+        for bad in (np.full(n, -1.0), np.full(n, np.nan), np.ones(n - 1)):
+            with pytest.raises((abi.MpcdError, ValueError)):
+                box.set_masses(bad)
+    with abi.Box(abi.make_params((4, 4, 4), precision="mixed")) as mixed:
+        with pytest.raises(abi.MpcdError) as ei:
+            mixed.set_masses(np.ones(mixed.n))
+        assert ei.value.code == abi.MPCD_ERR_ARG
 
 
 def test_face_positions_bit_exact_keys(orc):
