@@ -131,7 +131,7 @@ int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64
  * the angular-momentum correction (whose centre becomes mass-weighted); the rotation of
  * v - u keeps sum m v and sum m v^2 / 2.  Virtual wall particles and the initial velocities
  * keep params.mass.  Masses follow their particles through re-sorts and mpcd_set_state.
- * m = NULL restores the box mass.  With masses the collision takes the per-cell kernel.
+ * m = NULL restores the box mass.
  * Errors: MPCD_ERR_ARG (mixed form: its 32-byte record has no field for a mass; n != N; a
  * mass not finite or <= 0, named in the message).  Synchronises. */
 int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m);

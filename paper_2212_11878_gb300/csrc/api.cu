@@ -45,7 +45,8 @@ struct mpcd_s {
   int64_t n = 0, ncell = 0;
   Fp64Bufs f64{};
   double* mass_buf[3] = {};  // FP64 particle masses: storage order (two buffer sets), id order
-  bool masses = false;       // f64.m points at mass_buf
+  Fp64Mass f64m{};           // points at mass_buf[0..1] while masses are set
+  bool masses = false;
   Scratch scr{};
   MixBufs mix{};
   MixScratch mscr{};
@@ -283,9 +284,9 @@ int enqueue_step(mpcd_t* h, bool moments, int par = 0) {
   if ((rc = run_slot(h, kSlotStreamBin, [&] { launch_stream_bin_fp64(g, h->f64, s, h->ctl, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(s.count, s.offset, s.partial, g.ncell, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotScatter, [&] { launch_scatter(g, s, h->stream); }))) return rc;
-  if ((rc = run_slot(h, kSlotCollide, [&] { launch_collide_fp64(g, h->f64, s, h->ctl, moments, h->stream); }))) return rc;
-  if (fp64_dense_collide(g, h->f64, s))
-    if ((rc = run_slot(h, kSlotRotate, [&] { launch_rotate_fp64(g, h->f64, s, h->ctl, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotCollide, [&] { launch_collide_fp64(g, h->f64, s, h->ctl, moments, h->stream, h->f64m); }))) return rc;
+  if (fp64_dense_collide(g, s))
+    if ((rc = run_slot(h, kSlotRotate, [&] { launch_rotate_fp64(g, h->f64, s, h->ctl, h->stream, h->f64m); }))) return rc;
   if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step(g, h->ctl, h->stream); }))) return rc;
   return MPCD_OK;
 }
@@ -614,8 +615,7 @@ int mpcd_step(mpcd_t* h, int64_t nsteps) {
     h->t += 1;
     h->last_resorted = mixed || resort_at(h, h->t);
     if (h->last_resorted) h->cur ^= 1;
-    h->perm_sorted =
-        !mixed && (h->last_resorted || h->geom.walls || h->geom.thermostat || h->geom.angular || h->masses);
+    h->perm_sorted = !mixed && (h->last_resorted || h->geom.walls || h->geom.thermostat || h->geom.angular);
     h->any_step = true;
     h->moments_valid = h->record_moments;
   }
@@ -655,7 +655,7 @@ int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m) {
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!m) {
     h->masses = false;
-    h->f64.m[0] = h->f64.m[1] = nullptr;
+    h->f64m.m[0] = h->f64m.m[1] = nullptr;
   } else {
     for (int64_t i = 0; i < n; ++i)
       if (!(m[i] > 0.0) || !std::isfinite(m[i]))
@@ -668,11 +668,10 @@ int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m) {
     MPCD_TRY(h, cudaGetLastError());
     h->launches += 1;
     h->masses = true;
-    h->f64.m[0] = h->mass_buf[0];
-    h->f64.m[1] = h->mass_buf[1];
+    h->f64m.m[0] = h->mass_buf[0];
+    h->f64m.m[1] = h->mass_buf[1];
   }
-  // the per-cell kernel sums with masses; the dense pair (cell_frame + rotate) only without
-  h->per_step[kSlotRotate] = (!h->geom.walls && !h->geom.thermostat && !h->geom.angular && !h->masses) ? 1 : 0;
+  h->per_step[kSlotRotate] = (!h->geom.walls && !h->geom.thermostat && !h->geom.angular) ? 1 : 0;
   drop_graph(h);  // the step graph holds the buffer pointers and the kernel choice
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   return MPCD_OK;

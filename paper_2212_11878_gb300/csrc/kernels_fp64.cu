@@ -325,9 +325,9 @@ __device__ __forceinline__ double cell_local(const Geom& g, double r, double s) 
 // after(v) gives a member's velocity after the rotation and the thermostat.
 // With particle masses mp the centre is mass-weighted and L and I weight by m_i.
 template <typename After>
-__device__ void cell_omega(const Geom& g, const Fp64Bufs& b, int cur, const int32_t* pm, int n, const double s[3],
-                           After after, double mean[3], double w[3]) {
-  const double* __restrict__ mp = b.m[cur];
+__device__ void cell_omega(const Geom& g, const Fp64Bufs& b, const Fp64Mass& ms, int cur, const int32_t* pm, int n,
+                           const double s[3], After after, double mean[3], double w[3]) {
+  const double* __restrict__ mp = ms.m[cur];
   mean[0] = mean[1] = mean[2] = 0.0;
   w[0] = w[1] = w[2] = 0.0;
   double Mw = 0.0;
@@ -390,14 +390,14 @@ __device__ void cell_omega(const Geom& g, const Fp64Bufs& b, int cur, const int3
 // The whole collision of one cell by one thread (the shape of Listing 4): used for walls,
 // the thermostats and angular-momentum conservation, and by the allocation-free step.
 template <int WALLS, int THERMO, int MOMENTS>
-__device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& s, int64_t c, int64_t t1, int cur,
-                                     bool resort, const double* shift) {
+__device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, const Fp64Mass& ms, Scratch& s, int64_t c,
+                                     int64_t t1, int cur, bool resort, const double* shift) {
   const double shift_z = shift[2];
   const int o = s.offset[c];
   const int n = s.offset[c + 1] - o;
   int32_t* __restrict__ pm = s.perm + o;
   sort_entries(pm, n);
-  const double* __restrict__ mp = b.m[cur];  // particle masses, or null for the box mass
+  const double* __restrict__ mp = ms.m[cur];  // particle masses, or null for the box mass
   double S[3], SE, Mc = 0.0;
   if (mp) {
     cell_sums_mass<MOMENTS>(b, cur, mp, pm, n, S, SE, Mc);  // S = sum m v, SE = sum m v.v
@@ -470,7 +470,7 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
   double mean[3] = {0.0, 0.0, 0.0}, w[3] = {0.0, 0.0, 0.0};
   const bool spin = !WALLS && rotate && g.angular;
   if (spin)
-    cell_omega(g, b, cur, pm, n, shift,
+    cell_omega(g, b, ms, cur, pm, n, shift,
                [&](double& v0, double& v1, double& v2) {
                  apply_frame(R, bv, v0, v1, v2);
                  if (THERMO && n >= 2) {
@@ -508,7 +508,7 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
       b.v[ob][1][dst] = v1;
       b.v[ob][2][dst] = v2;
       b.id[ob][dst] = b.id[cur][i];
-      if (mp) b.m[ob][dst] = mp[i];
+      if (mp) ms.m[ob][dst] = mp[i];
     } else if (rotate) {
       b.v[cur][0][i] = v0;
       b.v[cur][1][i] = v1;
@@ -518,12 +518,13 @@ __device__ void collide_cell_generic(const Geom& g, const Fp64Bufs& b, Scratch& 
 }
 
 template <int WALLS, int THERMO, int MOMENTS>
-__global__ void __launch_bounds__(kThreads) k_collide_fp64_generic(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
+__global__ void __launch_bounds__(kThreads) k_collide_fp64_generic(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
+                                                                   Fp64Mass ms) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   const int64_t t1 = ctl->t + 1;
   const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
-  collide_cell_generic<WALLS, THERMO, MOMENTS>(g, b, s, c, t1, ctl->cur, resort, ctl->shift);
+  collide_cell_generic<WALLS, THERMO, MOMENTS>(g, b, ms, s, c, t1, ctl->cur, resort, ctl->shift);
 }
 
 // Periodic box, no thermostat, in two passes so that each runs at full occupancy:
@@ -537,8 +538,9 @@ __global__ void __launch_bounds__(kThreads) k_collide_fp64_generic(Geom g, Fp64B
 //                particle is written to its destination slot in the other buffer set.
 constexpr int kFrameStride = 16;  // doubles per cell record: R[9], b[3], flag, 3 unused
 
-template <int MOMENTS>
-__global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
+template <int MOMENTS, int MASS = 0>
+__global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
+                                                         Fp64Mass ms) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= g.ncell) return;
   const int64_t t1 = ctl->t + 1;
@@ -551,18 +553,34 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
     sort_entries(pm, n);
     for (int j = 0; j < n; ++j) s.inv[pm[j]] = o + j;
   }
-  double S[3], SE;
-  cell_sums<MOMENTS>(b, cur, pm, n, S, SE);
-  if (MOMENTS) write_moments(g, s, c, n, S, SE);
+  double S[3], SE, Mc = 0.0;
+  if (MASS) {  // particle masses: S = sum m v (exact), Mc = sum m
+    cell_sums_mass<MOMENTS>(b, cur, ms.m[cur], pm, n, S, SE, Mc);
+    if (MOMENTS) {
+      double* mo = s.moments + 5 * c;
+      mo[0] = Mc;
+      mo[1] = S[0];
+      mo[2] = S[1];
+      mo[3] = S[2];
+      mo[4] = 0.5 * SE;
+    }
+  } else {
+    cell_sums<MOMENTS>(b, cur, pm, n, S, SE);
+    if (MOMENTS) write_moments(g, s, c, n, S, SE);
+  }
   double2* __restrict__ rec = reinterpret_cast<double2*>(s.frame + kFrameStride * c);
   const bool rotate = n >= 2;
   if (!rotate) {
     rec[6] = make_double2(0.0, 0.0);
     return;
   }
-  const double in = inv_count(n);
   double R[9], bv[3];
-  make_frame(g, t1, c, S[0] * in, S[1] * in, S[2] * in, R, bv);
+  if (MASS) {
+    make_frame(g, t1, c, S[0] / Mc, S[1] / Mc, S[2] / Mc, R, bv);
+  } else {
+    const double in = inv_count(n);
+    make_frame(g, t1, c, S[0] * in, S[1] * in, S[2] * in, R, bv);
+  }
   rec[0] = make_double2(R[0], R[1]);
   rec[1] = make_double2(R[2], R[3]);
   rec[2] = make_double2(R[4], R[5]);
@@ -592,7 +610,9 @@ __device__ __forceinline__ void rotate_load(const Fp64Bufs& b, const Scratch& s,
   for (int k = 0; k < 7; ++k) q.f[k] = rec[k];
 }
 
-__device__ __forceinline__ void rotate_finish(const Fp64Bufs& b, const Scratch& s, RotSlot& q, int cur, bool resort) {
+template <int MASS>
+__device__ __forceinline__ void rotate_finish(const Fp64Bufs& b, const Fp64Mass& ms, const Scratch& s, RotSlot& q, int cur,
+                                              bool resort) {
   const bool rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1.0 or 0.0, tested as bits
   double v0 = q.v[0], v1 = q.v[1], v2 = q.v[2];
   if (rot) {
@@ -611,6 +631,7 @@ __device__ __forceinline__ void rotate_finish(const Fp64Bufs& b, const Scratch& 
     b.v[ob][1][dst] = v1;
     b.v[ob][2][dst] = v2;
     b.id[ob][dst] = b.id[cur][i];
+    if (MASS) ms.m[ob][dst] = ms.m[cur][i];
   } else if (rot) {
     b.v[cur][0][i] = v0;
     b.v[cur][1][i] = v1;
@@ -618,14 +639,16 @@ __device__ __forceinline__ void rotate_finish(const Fp64Bufs& b, const Scratch& 
   }
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
+template <int MASS>
+__global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
+                                                       Fp64Mass ms) {
   const int64_t t1 = ctl->t + 1;
   const int cur = ctl->cur;
   const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     RotSlot q;
     rotate_load(b, s, i, cur, q);
-    rotate_finish(b, s, q, cur, resort);
+    rotate_finish<MASS>(b, ms, s, q, cur, resort);
   }
 }
 
@@ -761,23 +784,24 @@ void launch_scatter(const Geom& g, Scratch s, cudaStream_t st) {
   k_scatter<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.key, s.rank, s.offset, s.perm);
 }
 
-void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st) {
+void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st,
+                                 Fp64Mass ms) {
   const unsigned grid = static_cast<unsigned>((g.ncell + kThreads - 1) / kThreads);
   const int sel = (g.walls ? 4 : 0) | (g.thermostat ? 2 : 0) | (moments ? 1 : 0);
   switch (sel) {
-    case 0: k_collide_fp64_generic<0, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 1: k_collide_fp64_generic<0, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 2: k_collide_fp64_generic<0, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 3: k_collide_fp64_generic<0, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 4: k_collide_fp64_generic<1, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 5: k_collide_fp64_generic<1, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    case 6: k_collide_fp64_generic<1, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
-    default: k_collide_fp64_generic<1, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl); break;
+    case 0: k_collide_fp64_generic<0, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 1: k_collide_fp64_generic<0, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 2: k_collide_fp64_generic<0, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 3: k_collide_fp64_generic<0, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 4: k_collide_fp64_generic<1, 0, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 5: k_collide_fp64_generic<1, 0, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 6: k_collide_fp64_generic<1, 1, 0><<<grid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    default: k_collide_fp64_generic<1, 1, 1><<<grid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
   }
 }
 
-bool fp64_dense_collide(const Geom& g, const Fp64Bufs& b, const Scratch& s) {
-  return !g.walls && !g.thermostat && !g.angular && !b.m[0] && s.frame && s.inv;
+bool fp64_dense_collide(const Geom& g, const Scratch& s) {
+  return !g.walls && !g.thermostat && !g.angular && s.frame && s.inv;
 }
 
 __global__ void k_gather_masses(int64_t n, const double* __restrict__ m_by_id, const int32_t* __restrict__ id,
@@ -790,20 +814,29 @@ void launch_gather_masses(int64_t n, const double* m_by_id, const int32_t* id, d
   if (n > 0) k_gather_masses<<<grid_for(n), kThreads, 0, st>>>(n, m_by_id, id, dst);
 }
 
-void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st) {
-  if (!fp64_dense_collide(g, b, s)) {
-    launch_collide_fp64_generic(g, b, s, ctl, moments, st);
+void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st, Fp64Mass ms) {
+  if (!fp64_dense_collide(g, s)) {
+    launch_collide_fp64_generic(g, b, s, ctl, moments, st, ms);
     return;
   }
   const unsigned cgrid = static_cast<unsigned>((g.ncell + kThreads - 1) / kThreads);
-  if (moments)
-    k_cell_frame<1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl);
-  else
-    k_cell_frame<0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl);
+  if (ms.m[0]) {
+    if (moments)
+      k_cell_frame<1, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms);
+    else
+      k_cell_frame<0, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms);
+  } else if (moments) {
+    k_cell_frame<1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms);
+  } else {
+    k_cell_frame<0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms);
+  }
 }
 
-void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st) {
-  k_rotate<<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl);
+void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st, Fp64Mass ms) {
+  if (ms.m[0])
+    k_rotate<1><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms);
+  else
+    k_rotate<0><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms);
 }
 
 void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st) {

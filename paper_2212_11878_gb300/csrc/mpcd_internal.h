@@ -60,7 +60,13 @@ struct Fp64Bufs {
   double* r[2][3];
   double* v[2][3];
   int32_t* id[2];
-  double* m[2];  // per-particle masses in storage order; null: every particle has the box mass
+};
+
+// Per-particle masses of the FP64 form in storage order, per buffer set (null: every particle
+// has the box mass).  Passed as a separate, last kernel argument, and only to the kernels
+// that read it, so the argument layout of every other kernel stays as it is.
+struct Fp64Mass {
+  double* m[2];
 };
 
 // Mixed-precision particle record, 32 bytes (one DRAM sector): in-cell offsets in cell
@@ -113,16 +119,17 @@ void launch_scan(const int32_t* count, int32_t* offset, int32_t* partial, int64_
 void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
 void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
 void launch_scatter(const Geom& g, Scratch s, cudaStream_t st);
-// periodic boxes without thermostat, angular-momentum correction or particle masses
-// (fp64_dense_collide): cell_frame here, then launch_rotate_fp64; otherwise one thread per
-// cell here and no rotate launch
-bool fp64_dense_collide(const Geom& g, const Fp64Bufs& b, const Scratch& s);
+// periodic boxes without thermostat or angular-momentum correction (fp64_dense_collide):
+// cell_frame here, then launch_rotate_fp64; otherwise one thread per cell here and no
+// rotate launch
+bool fp64_dense_collide(const Geom& g, const Scratch& s);
 // dst[j] = m_by_id[id[j]]: particle masses into storage order
 void launch_gather_masses(int64_t n, const double* m_by_id, const int32_t* id, double* dst, cudaStream_t st);
-void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st);
-void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
+void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st, Fp64Mass ms);
+void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st, Fp64Mass ms);
 // one thread per cell for every box kind (no frame buffer needed)
-void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st);
+void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st,
+                                 Fp64Mass ms = Fp64Mass{});
 void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st);
 void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
