@@ -466,7 +466,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->geom.n = ntot;
   h->geom.ncell = ctot;
   for (int k = 0; k < kNumSlots; ++k) h->per_step[k] = kSlotLaunchesBase[k];
-  if (!h->geom.walls && !h->geom.thermostat && !h->geom.angular) h->per_step[kSlotRotate] = 1;  // cell_frame + rotate
+  if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotRotate] = 1;  // cell_frame + rotate
   h->n = ntot;
   h->ncell = ctot;
   auto bail = [&](int code) {
@@ -531,7 +531,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     if ((rc = dalloc(h, &h->scr.count, C))) return bail(rc);
     if ((rc = dalloc(h, &h->scr.offset, C + 1))) return bail(rc);
     if ((rc = dalloc(h, &h->scr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
-    if (!h->geom.walls && !h->geom.thermostat && !h->geom.angular) {
+    if (!h->geom.walls && !h->geom.thermostat) {
       if ((rc = dalloc(h, &h->scr.frame, 16 * C))) return bail(rc);
       if ((rc = dalloc(h, &h->scr.inv, n))) return bail(rc);
     }
@@ -671,7 +671,7 @@ int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m) {
     h->f64m.m[0] = h->mass_buf[0];
     h->f64m.m[1] = h->mass_buf[1];
   }
-  h->per_step[kSlotRotate] = (!h->geom.walls && !h->geom.thermostat && !h->geom.angular) ? 1 : 0;
+  h->per_step[kSlotRotate] = (!h->geom.walls && !h->geom.thermostat) ? 1 : 0;
   drop_graph(h);  // the step graph holds the buffer pointers and the kernel choice
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   return MPCD_OK;

@@ -538,7 +538,56 @@ __global__ void __launch_bounds__(kThreads) k_collide_fp64_generic(Geom g, Fp64B
 //                particle is written to its destination slot in the other buffer set.
 constexpr int kFrameStride = 16;  // doubles per cell record: R[9], b[3], flag, 3 unused
 
-template <int MOMENTS, int MASS = 0>
+// Angular-momentum correction of a dense cell from its moments (the variant Sec. 2 mentions):
+// with in-cell positions l_i and weights w_i (the particle masses, or 1 for the box mass,
+// which cancels from omega), A = sum w l, Q = sum w l l^T, B = sum w l v^T and P = sum w v,
+// the moments about the centre are a (B - lbar P^T) and a^2 (Q - W lbar lbar^T), so
+// L_before = eps : M, L_after = eps : (M R^T) (sum w rho = 0), I = tr(S) 1 - S.  omega as in
+// cell_omega; the frame then carries a omega and b - a omega x lbar, and rotate adds
+// (a omega) x l_i.
+__device__ void dense_omega(const Geom& g, const double R[9], double W, const double A[3], const double Q[6],
+                            const double B[9], const double P[3], const double l0[3], int n, double aw[3],
+                            double lbar[3]) {
+  aw[0] = aw[1] = aw[2] = 0.0;
+  for (int d = 0; d < 3; ++d) lbar[d] = A[d] / W;
+  double M[3][3], S[3][3];
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) M[x][y] = g.a * (B[3 * x + y] - lbar[x] * P[y]);
+  const int qi[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};  // Q: xx yy zz xy xz yz
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) S[x][y] = g.a * g.a * (Q[qi[x][y]] - W * lbar[x] * lbar[y]);
+  double N[3][3];  // M R^T
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) N[x][y] = M[x][0] * R[3 * y] + M[x][1] * R[3 * y + 1] + M[x][2] * R[3 * y + 2];
+  const double dL[3] = {(M[1][2] - M[2][1]) - (N[1][2] - N[2][1]), (M[2][0] - M[0][2]) - (N[2][0] - N[0][2]),
+                        (M[0][1] - M[1][0]) - (N[0][1] - N[1][0])};
+  const double tr = S[0][0] + S[1][1] + S[2][2];
+  double I[3][3];
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) I[x][y] = (x == y ? tr : 0.0) - S[x][y];
+  double w[3] = {0.0, 0.0, 0.0};
+  if (n == 2) {  // the pair lies on one line: I acts as tr(S) normal to it
+    const double q[3] = {g.a * (l0[0] - lbar[0]), g.a * (l0[1] - lbar[1]), g.a * (l0[2] - lbar[2])};
+    const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    if (!(qq > 0.0) || !(tr > 0.0)) return;
+    const double along = (q[0] * dL[0] + q[1] * dL[1] + q[2] * dL[2]) / qq;
+    for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q[d]) / tr;
+  } else {
+    double cof[3][3];
+    for (int x = 0; x < 3; ++x)
+      for (int y = 0; y < 3; ++y) {
+        const int x1 = (x + 1) % 3, x2 = (x + 2) % 3, y1 = (y + 1) % 3, y2 = (y + 2) % 3;
+        cof[x][y] = I[x1][y1] * I[x2][y2] - I[x1][y2] * I[x2][y1];
+      }
+    const double det = I[0][0] * cof[0][0] + I[0][1] * cof[0][1] + I[0][2] * cof[0][2];
+    const double t3 = (I[0][0] + I[1][1] + I[2][2]) / 3.0;
+    if (!(det > 1e-12 * t3 * t3 * t3)) return;
+    for (int x = 0; x < 3; ++x) w[x] = (cof[x][0] * dL[0] + cof[x][1] * dL[1] + cof[x][2] * dL[2]) / det;
+  }
+  for (int d = 0; d < 3; ++d) aw[d] = g.a * w[d];
+}
+
+template <int MOMENTS, int MASS = 0, int ANG = 0>
 __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
                                                          Fp64Mass ms) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -549,10 +598,9 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
   const int o = s.offset[c];
   const int n = s.offset[c + 1] - o;
   int32_t* __restrict__ pm = s.perm + o;
-  if (resort) {
-    sort_entries(pm, n);
+  if (resort || ANG) sort_entries(pm, n);  // ANG: one fixed order for the FP64 moment sums
+  if (resort)
     for (int j = 0; j < n; ++j) s.inv[pm[j]] = o + j;
-  }
   double S[3], SE, Mc = 0.0;
   if (MASS) {  // particle masses: S = sum m v (exact), Mc = sum m
     cell_sums_mass<MOMENTS>(b, cur, ms.m[cur], pm, n, S, SE, Mc);
@@ -581,13 +629,44 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
     const double in = inv_count(n);
     make_frame(g, t1, c, S[0] * in, S[1] * in, S[2] * in, R, bv);
   }
+  double aw[3] = {0.0, 0.0, 0.0};
+  if (ANG) {
+    double W = 0.0, A[3] = {0.0, 0.0, 0.0}, Q[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, B[9] = {0.0}, l0[3];
+    for (int j = 0; j < n; ++j) {
+      const int i = pm[j];
+      const double w = MASS ? ms.m[cur][i] : 1.0;
+      double l[3], v[3];
+      for (int d = 0; d < 3; ++d) {
+        l[d] = cell_local(g, b.r[cur][d][i], ctl->shift[d]);
+        v[d] = b.v[cur][d][i];
+      }
+      if (j == 0)
+        for (int d = 0; d < 3; ++d) l0[d] = l[d];
+      W += w;
+      for (int d = 0; d < 3; ++d) A[d] += w * l[d];
+      Q[0] += w * l[0] * l[0];
+      Q[1] += w * l[1] * l[1];
+      Q[2] += w * l[2] * l[2];
+      Q[3] += w * l[0] * l[1];
+      Q[4] += w * l[0] * l[2];
+      Q[5] += w * l[1] * l[2];
+      for (int x = 0; x < 3; ++x)
+        for (int y = 0; y < 3; ++y) B[3 * x + y] += w * l[x] * v[y];
+    }
+    double lbar[3];
+    dense_omega(g, R, W, A, Q, B, S, l0, n, aw, lbar);  // S: sum w v (the exact momentum sums)
+    bv[0] -= aw[1] * lbar[2] - aw[2] * lbar[1];
+    bv[1] -= aw[2] * lbar[0] - aw[0] * lbar[2];
+    bv[2] -= aw[0] * lbar[1] - aw[1] * lbar[0];
+  }
   rec[0] = make_double2(R[0], R[1]);
   rec[1] = make_double2(R[2], R[3]);
   rec[2] = make_double2(R[4], R[5]);
   rec[3] = make_double2(R[6], R[7]);
   rec[4] = make_double2(R[8], bv[0]);
   rec[5] = make_double2(bv[1], bv[2]);
-  rec[6] = make_double2(1.0, 0.0);
+  rec[6] = make_double2(1.0, aw[0]);
+  if (ANG) rec[7] = make_double2(aw[1], aw[2]);
 }
 
 // One storage slot of k_rotate: its velocity and its cell's frame record, all loaded
@@ -596,9 +675,10 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
 struct RotSlot {
   int64_t i;
   double v[3];
-  double2 f[7];
+  double2 f[8];  // f[7]: only with angular-momentum conservation
 };
 
+template <int ANG>
 __device__ __forceinline__ void rotate_load(const Fp64Bufs& b, const Scratch& s, int64_t i, int cur, RotSlot& q) {
   q.i = i;
   const int c = s.key[i];
@@ -607,18 +687,27 @@ __device__ __forceinline__ void rotate_load(const Fp64Bufs& b, const Scratch& s,
   q.v[2] = b.v[cur][2][i];
   const double2* __restrict__ rec = reinterpret_cast<const double2*>(s.frame + kFrameStride * (int64_t)c);
 #pragma unroll
-  for (int k = 0; k < 7; ++k) q.f[k] = rec[k];
+  for (int k = 0; k < 7 + ANG; ++k) q.f[k] = rec[k];
 }
 
-template <int MASS>
-__device__ __forceinline__ void rotate_finish(const Fp64Bufs& b, const Fp64Mass& ms, const Scratch& s, RotSlot& q, int cur,
-                                              bool resort) {
+template <int MASS, int ANG>
+__device__ __forceinline__ void rotate_finish(const Geom& g, const Fp64Bufs& b, const Fp64Mass& ms, const Scratch& s,
+                                              RotSlot& q, int cur, bool resort, const double* shift) {
   const bool rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1.0 or 0.0, tested as bits
   double v0 = q.v[0], v1 = q.v[1], v2 = q.v[2];
   if (rot) {
     const double R[9] = {q.f[0].x, q.f[0].y, q.f[1].x, q.f[1].y, q.f[2].x, q.f[2].y, q.f[3].x, q.f[3].y, q.f[4].x};
     const double bv[3] = {q.f[4].y, q.f[5].x, q.f[5].y};
     apply_frame(R, bv, v0, v1, v2);
+    if (ANG) {  // + (a omega) x l_i
+      const double w0 = q.f[6].y, w1 = q.f[7].x, w2 = q.f[7].y;
+      const double l0 = cell_local(g, b.r[cur][0][q.i], shift[0]);
+      const double l1 = cell_local(g, b.r[cur][1][q.i], shift[1]);
+      const double l2 = cell_local(g, b.r[cur][2][q.i], shift[2]);
+      v0 += w1 * l2 - w2 * l1;
+      v1 += w2 * l0 - w0 * l2;
+      v2 += w0 * l1 - w1 * l0;
+    }
   }
   const int64_t i = q.i;
   if (resort) {
@@ -639,7 +728,7 @@ __device__ __forceinline__ void rotate_finish(const Fp64Bufs& b, const Fp64Mass&
   }
 }
 
-template <int MASS>
+template <int MASS, int ANG = 0>
 __global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
                                                        Fp64Mass ms) {
   const int64_t t1 = ctl->t + 1;
@@ -647,8 +736,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scra
   const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     RotSlot q;
-    rotate_load(b, s, i, cur, q);
-    rotate_finish<MASS>(b, ms, s, q, cur, resort);
+    rotate_load<ANG>(b, s, i, cur, q);
+    rotate_finish<MASS, ANG>(g, b, ms, s, q, cur, resort, ctl->shift);
   }
 }
 
@@ -801,7 +890,7 @@ void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl,
 }
 
 bool fp64_dense_collide(const Geom& g, const Scratch& s) {
-  return !g.walls && !g.thermostat && !g.angular && s.frame && s.inv;
+  return !g.walls && !g.thermostat && s.frame && s.inv;
 }
 
 __global__ void k_gather_masses(int64_t n, const double* __restrict__ m_by_id, const int32_t* __restrict__ id,
@@ -820,23 +909,25 @@ void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool mo
     return;
   }
   const unsigned cgrid = static_cast<unsigned>((g.ncell + kThreads - 1) / kThreads);
-  if (ms.m[0]) {
-    if (moments)
-      k_cell_frame<1, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms);
-    else
-      k_cell_frame<0, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms);
-  } else if (moments) {
-    k_cell_frame<1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms);
-  } else {
-    k_cell_frame<0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms);
+  switch ((g.angular ? 4 : 0) | (ms.m[0] ? 2 : 0) | (moments ? 1 : 0)) {
+    case 0: k_cell_frame<0, 0, 0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 1: k_cell_frame<1, 0, 0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 2: k_cell_frame<0, 1, 0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 3: k_cell_frame<1, 1, 0><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 4: k_cell_frame<0, 0, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 5: k_cell_frame<1, 0, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 6: k_cell_frame<0, 1, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    default: k_cell_frame<1, 1, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
   }
 }
 
 void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st, Fp64Mass ms) {
-  if (ms.m[0])
-    k_rotate<1><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms);
-  else
-    k_rotate<0><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms);
+  switch ((g.angular ? 2 : 0) | (ms.m[0] ? 1 : 0)) {
+    case 0: k_rotate<0, 0><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 1: k_rotate<1, 0><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    case 2: k_rotate<0, 1><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+    default: k_rotate<1, 1><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms); break;
+  }
 }
 
 void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st) {
