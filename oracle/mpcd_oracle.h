@@ -14,7 +14,7 @@
  *   velocity, split it along a random axis and rotate the perpendicular part by a fixed
  *   angle (Sec. 2, parts (i)-(iii)).
  *
- * Where the paper is silent, the oracle takes these readings (each is listed in the design doc):
+ * Where the paper is silent, the oracle takes these readings:
  *   R1 stream then collide inside step t; steps are counted from 1.
  *   R2 shift s uniform in [-a/2, a/2)^3, cell = floor((r - s)/a) mod L.
  *   R3 a wrapped coordinate that rounds to L becomes 0.
