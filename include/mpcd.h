@@ -74,7 +74,7 @@ typedef struct {
                       /*   cell's inertia tensor (pseudo-inverse for two particles; none    */
                       /*   for a singular one).  Conserves each cell's momentum and angular */
                       /*   momentum, not its energy.  Periodic boxes only (walls: ERR_ARG). */
-                      /*   The mixed form takes it through its per-cell path.  0: off.      */
+                      /*   The mixed form takes it through its per-cell kernel.  0: off.    */
 } mpcd_params;
 
 /* Create a box and initialise it on the current CUDA device (Sec. 4 workload): positions

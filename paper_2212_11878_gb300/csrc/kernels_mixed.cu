@@ -478,77 +478,70 @@ __device__ __forceinline__ void mixed_local(const MixRec& r, const float sf[3], 
   }
 }
 
-// Angular momentum of the cell about its centre of mass, sum rho x v (times m by the caller).
-__device__ __forceinline__ void mixed_spin(const MixRec* rec, int n, const float sf[3], const double mean[3], double a,
-                                           double L[3]) {
-  L[0] = L[1] = L[2] = 0.0;
-  for (int j = 0; j < n; ++j) {
-    double l[3];
-    mixed_local(rec[j], sf, l);
-    const double q0 = a * (l[0] - mean[0]), q1 = a * (l[1] - mean[1]), q2 = a * (l[2] - mean[2]);
-    const double v0 = rec[j].vx, v1 = rec[j].vy, v2 = rec[j].vz;
-    L[0] += q1 * v2 - q2 * v1;
-    L[1] += q2 * v0 - q0 * v2;
-    L[2] += q0 * v1 - q1 * v0;
-  }
-}
-
-// Before the collision: the members sorted by particle id (so the FP64 sums take one fixed
-// order), their mean position in the cell and their angular momentum about it.
-struct CellSpin {
-  double mean[3], Lb[3];
+// Angular-momentum-conserving collision (the variant the paper mentions in Sec. 2), mixed
+// form, from the cell's moments: with in-cell positions l (exact in FP64) and velocities v
+// before the collision, A = sum l, Q = sum l l^T, B = sum l v^T and P = sum v, accumulated as
+// exact fixed-point sums of the FP64 products (two FP32 factors), so the member order does
+// not matter.  The moments about the centre are M = a (B - lbar P^T) and S = a^2 (Q - n lbar
+// lbar^T); L_before = eps : M and, after w = R (v - u) and the rescale by 1 + df,
+// L_after = (1 + df) eps : (M R^T); I = tr(S) 1 - S; omega = I^-1 (L_before - L_after) as
+// in the FP64 form.  Each member then gets (a omega) x (l - lbar).
+struct CellMoments {
+  Fx128 A[3], Q[6], B[9], P[3];
 };
 
-__device__ __noinline__ CellSpin mixed_spin_before(MixRec* rec, int n, const float* sf, double a) {
-  for (int j = 1; j < n; ++j) {  // insertion sort by particle id
-    const MixRec x = rec[j];
-    int k = j - 1;
-    while (k >= 0 && rec[k].id > x.id) {
-      rec[k + 1] = rec[k];
-      --k;
-    }
-    rec[k + 1] = x;
-  }
-  CellSpin cs;
-  cs.mean[0] = cs.mean[1] = cs.mean[2] = 0.0;
-  for (int j = 0; j < n; ++j) {
-    double l[3];
-    mixed_local(rec[j], sf, l);
-    for (int d = 0; d < 3; ++d) cs.mean[d] += l[d];
-  }
-  for (int d = 0; d < 3; ++d) cs.mean[d] /= static_cast<double>(n);
-  mixed_spin(rec, n, sf, cs.mean, a, cs.Lb);
-  return cs;
+__device__ __forceinline__ void moments_zero(CellMoments& cm) {
+  for (int k = 0; k < 3; ++k) fx_zero(cm.A[k]), fx_zero(cm.P[k]);
+  for (int k = 0; k < 6; ++k) fx_zero(cm.Q[k]);
+  for (int k = 0; k < 9; ++k) fx_zero(cm.B[k]);
 }
 
-// Angular-momentum-conserving collision (the variant the paper mentions in Sec. 2), mixed
-// form, after the rotation and rescale: omega = I^-1 (L_before - L_after), v += omega x rho
-// rounded to FP32.  The same rule as the FP64 form (pseudo-inverse for two particles, none
-// for a singular inertia tensor).
-__device__ __noinline__ void mixed_angular(const Geom* __restrict__ gp, MixRec* rec, int n, const float* sf,
-                                           CellSpin cs) {
-  const Geom& g = *gp;
-  const double* mean = cs.mean;
-  const double* Lb = cs.Lb;
-  double La[3], I[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}}, rr = 0.0, q0[3] = {0.0, 0.0, 0.0};
-  mixed_spin(rec, n, sf, mean, g.a, La);
-  const double dL[3] = {Lb[0] - La[0], Lb[1] - La[1], Lb[2] - La[2]};
-  for (int j = 0; j < n; ++j) {
-    double l[3], q[3];
-    mixed_local(rec[j], sf, l);
-    for (int d = 0; d < 3; ++d) q[d] = g.a * (l[d] - mean[d]);
-    if (j == 0)
-      for (int d = 0; d < 3; ++d) q0[d] = q[d];
-    const double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
-    rr += q2;
-    for (int x = 0; x < 3; ++x)
-      for (int y = 0; y < 3; ++y) I[x][y] += (x == y ? q2 : 0.0) - q[x] * q[y];
-  }
-  double w[3] = {0.0, 0.0, 0.0};
-  if (n == 2) {
-    if (!(rr > 0.0)) return;
-    const double along = (q0[0] * dL[0] + q0[1] * dL[1] + q0[2] * dL[2]) * (2.0 / rr);
-    for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q0[d]) / rr;
+// Adds a streamed record; false if a term left the exact range (the cell is then not corrected).
+__device__ __forceinline__ bool moments_add(CellMoments& cm, const MixRec& r, const float sf[3]) {
+  double l[3];
+  mixed_local(r, sf, l);
+  const double v[3] = {r.vx, r.vy, r.vz};
+  bool ok = true;
+  for (int d = 0; d < 3; ++d) ok &= fx_add(cm.A[d], l[d]) & fx_add(cm.P[d], v[d]);
+  ok &= fx_add(cm.Q[0], l[0] * l[0]) & fx_add(cm.Q[1], l[1] * l[1]) & fx_add(cm.Q[2], l[2] * l[2]);
+  ok &= fx_add(cm.Q[3], l[0] * l[1]) & fx_add(cm.Q[4], l[0] * l[2]) & fx_add(cm.Q[5], l[1] * l[2]);
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) ok &= fx_add(cm.B[3 * x + y], l[x] * v[y]);
+  return ok;
+}
+
+// a omega and lbar of a cell of n >= 2 members (aw = 0 when I is singular); l0: the in-cell
+// position of one member (the two-particle case needs their separation).
+__device__ __noinline__ void mixed_omega(const Geom* __restrict__ gp, const CellMoments* __restrict__ cm, const float* Rf,
+                                         float df, int n, const double* l0, double* aw, double* lbar) {
+  const double a = gp->a;
+  double R[9], A[3], Q[6], B[9], P[3];
+  for (int k = 0; k < 9; ++k) R[k] = Rf[k], B[k] = fx_value(cm->B[k]);
+  for (int k = 0; k < 3; ++k) A[k] = fx_value(cm->A[k]), P[k] = fx_value(cm->P[k]);
+  for (int k = 0; k < 6; ++k) Q[k] = fx_value(cm->Q[k]);
+  aw[0] = aw[1] = aw[2] = 0.0;
+  for (int d = 0; d < 3; ++d) lbar[d] = A[d] / n;
+  double Mm[3][3], S[3][3], N[3][3];
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) Mm[x][y] = a * (B[3 * x + y] - lbar[x] * P[y]);
+  const int qi[3][3] = {{0, 3, 4}, {3, 1, 5}, {4, 5, 2}};
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) S[x][y] = a * a * (Q[qi[x][y]] - n * lbar[x] * lbar[y]);
+  const double sc = 1.0 + static_cast<double>(df);
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) N[x][y] = sc * (Mm[x][0] * R[3 * y] + Mm[x][1] * R[3 * y + 1] + Mm[x][2] * R[3 * y + 2]);
+  const double dL[3] = {(Mm[1][2] - Mm[2][1]) - (N[1][2] - N[2][1]), (Mm[2][0] - Mm[0][2]) - (N[2][0] - N[0][2]),
+                        (Mm[0][1] - Mm[1][0]) - (N[0][1] - N[1][0])};
+  const double tr = S[0][0] + S[1][1] + S[2][2];
+  double I[3][3], w[3] = {0.0, 0.0, 0.0};
+  for (int x = 0; x < 3; ++x)
+    for (int y = 0; y < 3; ++y) I[x][y] = (x == y ? tr : 0.0) - S[x][y];
+  if (n == 2) {  // the pair lies on one line: I acts as tr(S) normal to it
+    const double q[3] = {a * (l0[0] - lbar[0]), a * (l0[1] - lbar[1]), a * (l0[2] - lbar[2])};
+    const double qq = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    if (!(qq > 0.0) || !(tr > 0.0)) return;
+    const double along = (q[0] * dL[0] + q[1] * dL[1] + q[2] * dL[2]) / qq;
+    for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q[d]) / tr;
   } else {
     double cof[3][3];
     for (int x = 0; x < 3; ++x)
@@ -557,27 +550,21 @@ __device__ __noinline__ void mixed_angular(const Geom* __restrict__ gp, MixRec* 
         cof[x][y] = I[x1][y1] * I[x2][y2] - I[x1][y2] * I[x2][y1];
       }
     const double det = I[0][0] * cof[0][0] + I[0][1] * cof[0][1] + I[0][2] * cof[0][2];
-    const double tr = (I[0][0] + I[1][1] + I[2][2]) / 3.0;
-    if (!(det > 1e-12 * tr * tr * tr)) return;
+    const double t3 = (I[0][0] + I[1][1] + I[2][2]) / 3.0;
+    if (!(det > 1e-12 * t3 * t3 * t3)) return;
     for (int x = 0; x < 3; ++x) w[x] = (cof[x][0] * dL[0] + cof[x][1] * dL[1] + cof[x][2] * dL[2]) / det;
   }
-  for (int j = 0; j < n; ++j) {
-    double l[3];
-    mixed_local(rec[j], sf, l);
-    const double qx = g.a * (l[0] - mean[0]), qy = g.a * (l[1] - mean[1]), qz = g.a * (l[2] - mean[2]);
-    rec[j].vx = static_cast<float>(rec[j].vx + (w[1] * qz - w[2] * qy));
-    rec[j].vy = static_cast<float>(rec[j].vy + (w[2] * qx - w[0] * qz));
-    rec[j].vz = static_cast<float>(rec[j].vz + (w[0] * qy - w[1] * qx));
-  }
+  for (int d = 0; d < 3; ++d) aw[d] = a * w[d];
 }
 
 // The whole collision of one cell by one thread over AoS records rec[0..n-1] in global
 // memory (crowded cells, and every cell with angular-momentum conservation, which also gets
-// this step's shift sf in cell units).  Its sums accumulate the same fixed-point parts in
-// int64, so they equal the staged path's bit for bit.
+// this step's shift sf in cell units and the cell's moments cm).  Its sums accumulate the
+// same fixed-point parts in int64, so they equal the staged path's bit for bit.
 template <int WALLS, int THERMO, int MOMENTS, int ANG = 0>
 __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c, int64_t t1, double shift_z,
-                                   double* moments, const float* sf) {
+                                   double* moments, const float* sf, const CellMoments* cm = nullptr,
+                                   bool cm_ok = false) {
   const V3 v{&rec[0].vx, &rec[0].vy, &rec[0].vz, 8};
   long long S[3], E2;
   const bool ok = cell_sums_mixed<MOMENTS>(v, n, S, E2);
@@ -585,9 +572,6 @@ __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c,
   CellFrame f;
   cell_prologue<WALLS>(g, S, n, c, t1, shift_z, f);
   if (!f.rot || !ok) return;
-  const bool spin = ANG && !WALLS && n >= 2;
-  CellSpin cs;
-  if (spin) cs = mixed_spin_before(rec, n, sf, g.a);
   long long dE = 0, Ea = 0;
   bool oke = n < 512;
   for (int j = 0; j < n; ++j) {
@@ -599,12 +583,32 @@ __device__ void mixed_collide_cell(const Geom& g, MixRec* rec, int n, int64_t c,
     oke &= fx_add<kFixDE>(dE, term) & fx_add<kFixV2>(Ea, sq3(w));
   }
   const float df = cell_df<THERMO>(g, n, dE, Ea, oke, t1, c);
-  for (int j = 0; j < n; ++j) {
-    v.vx(j) = __fadd_rn(f.u[0], fmaf(df, v.vx(j), v.vx(j)));
-    v.vy(j) = __fadd_rn(f.u[1], fmaf(df, v.vy(j), v.vy(j)));
-    v.vz(j) = __fadd_rn(f.u[2], fmaf(df, v.vz(j), v.vz(j)));
+  float aw[3] = {0.0f, 0.0f, 0.0f}, lb[3] = {0.0f, 0.0f, 0.0f};
+  const bool spin = ANG && !WALLS && n >= 2 && cm_ok;
+  if (spin) {
+    double l0[3], awd[3], lbd[3];
+    mixed_local(rec[0], sf, l0);
+    mixed_omega(&g, cm, f.R, df, n, l0, awd, lbd);
+    for (int d = 0; d < 3; ++d) aw[d] = static_cast<float>(awd[d]), lb[d] = static_cast<float>(lbd[d]);
   }
-  if (spin) mixed_angular(&g, rec, n, sf, cs);
+  for (int j = 0; j < n; ++j) {
+    float nx = __fadd_rn(f.u[0], fmaf(df, v.vx(j), v.vx(j)));
+    float ny = __fadd_rn(f.u[1], fmaf(df, v.vy(j), v.vy(j)));
+    float nz = __fadd_rn(f.u[2], fmaf(df, v.vz(j), v.vz(j)));
+    if (ANG && spin) {  // + (a omega) x (l - lbar), in FP32
+      float q[3];
+      for (int d = 0; d < 3; ++d) {
+        const float x = __fsub_rn((&rec[j].ox)[d], sf[d]);
+        q[d] = __fsub_rn(x, static_cast<float>(static_cast<int>(x >= 1.0f) - static_cast<int>(x < 0.0f))) - lb[d];
+      }
+      nx += aw[1] * q[2] - aw[2] * q[1];
+      ny += aw[2] * q[0] - aw[0] * q[2];
+      nz += aw[0] * q[1] - aw[1] * q[0];
+    }
+    v.vx(j) = nx;
+    v.vy(j) = ny;
+    v.vz(j) = nz;
+  }
 }
 
 // True when streaming a particle with velocity v moves each in-cell offset f in [0, 1) by
@@ -851,13 +855,18 @@ __device__ __noinline__ void collide_group_direct(const Geom* __restrict__ gp, c
     const int o = offset[c];
     const int n = offset[c + 1] - o;
     const int32_t* pm = perm + o;
+    CellMoments cm;
+    bool cm_ok = true;
+    if (ANG) moments_zero(cm);
     for (int j = 0; j < n; ++j) {
       MixRec r = load_rec(src + pm[j]);
       stream_record<WALLS, FORCE>(g, r);
       dst[o + j] = r;
+      if (ANG) cm_ok &= moments_add(cm, r, shp->sf);
     }
     mixed_collide_cell<WALLS, THERMO, MOMENTS, ANG>(g, dst + o, n, c - cbase, t1, shp->s[2],
-                                                    MOMENTS ? moments + 5 * (int64_t)cbase : nullptr, shp->sf);
+                                                    MOMENTS ? moments + 5 * (int64_t)cbase : nullptr, shp->sf,
+                                                    ANG ? &cm : nullptr, cm_ok);
     for (int j = 0; j < n; ++j) {
       const int k = cbase + next_key<WALLS, FORCE>(g, dst[o + j], sf);
       knext[o + j] = k;
