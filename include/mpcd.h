@@ -39,7 +39,9 @@ enum {
   MPCD_ERR_ARG = -1,     /* invalid argument; nothing was changed */
   MPCD_ERR_CUDA = -2,    /* a CUDA call failed; the handle is now poisoned */
   MPCD_ERR_OOM = -3,     /* device memory ran out while creating */
-  MPCD_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up; the handle is poisoned */
+  MPCD_ERR_TIMEOUT = -4, /* reserved for a bounded device-side wait that gave up; no kernel  */
+                         /* of this library waits on another (the scan is multi-pass), so   */
+                         /* no call returns it                                               */
   MPCD_ERR_STATE = -5    /* the handle was poisoned by an earlier error */
 };
 
@@ -106,7 +108,7 @@ int mpcd_set_stream(mpcd_t* h, void* stream);
  * Steps are numbered from 1 since creation or the last mpcd_set_state.  Asynchronous. */
 int mpcd_step(mpcd_t* h, int64_t nsteps);
 
-/* Wait for all enqueued work; reports a device-side timeout as MPCD_ERR_TIMEOUT. */
+/* Wait for all enqueued work (MPCD_ERR_CUDA if a kernel failed). */
 int mpcd_sync(mpcd_t* h);
 
 int64_t mpcd_num_particles(const mpcd_t* h); /* N, or -1 for NULL */

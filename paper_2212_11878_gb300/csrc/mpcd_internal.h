@@ -46,7 +46,7 @@ struct alignas(16) Geom {
 struct Ctl {
   int64_t t;            // completed steps; the step in flight is t + 1
   int32_t cur;          // particle buffer set holding the state (0 or 1)
-  int32_t err;          // error bits raised by kernels
+  int32_t err;          // reserved (no kernel raises error bits)
   double shift[3];      // grid shift of step t + 1 (the next step to run)
   double shift_next[3]; // grid shift of step t + 2
   double shift_last[3]; // grid shift of step t (the last completed step)

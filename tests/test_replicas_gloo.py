@@ -1,7 +1,10 @@
-"""The replica host logic on two CPU ranks (gloo): distinct seeds per rank, and the job's
-throughput as all ranks' updates over the slowest rank's time."""
+"""The replica host logic on two CPU ranks (gloo): distinct seeds per rank, the job's
+throughput as all ranks' updates over the slowest rank's time, and a rank that leaves: the
+other rank's next collective ends with an error instead of waiting forever."""
+import datetime
 import os
 import socket
+import time
 
 import pytest
 import torch
@@ -47,6 +50,34 @@ def test_two_rank_throughput_and_seeds():
         assert total == 3e6                    # all ranks' updates
         assert value == pytest.approx(3e6 / 0.020)
         assert len({s[0] for s in seeds}) == world and len({s[1] for s in seeds}) == world
+
+
+def _leaving_main(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    if rank == 1:
+        out[rank] = "left"  # leaves between steps, with no collective in flight
+        return
+    t0 = time.time()
+    try:
+        replicas.job_throughput(1e6, 10.0, dist)
+        out[rank] = ("no error", time.time() - t0)
+    except Exception as e:  # gloo reports the closed peer or the timeout
+        out[rank] = ("error", time.time() - t0, type(e).__name__)
+
+
+@pytest.mark.timeout(120)
+def test_rank_that_leaves_ends_the_next_collective_with_an_error():
+    world = 2
+    port = _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_leaving_main, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    assert res[1] == "left"
+    assert res[0][0] == "error", res[0]
+    assert res[0][1] < 30.0  # within the process group's timeout, with margin
 
 
 def test_single_process_is_plain_rate():
