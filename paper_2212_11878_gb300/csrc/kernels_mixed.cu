@@ -1460,21 +1460,71 @@ cudaError_t launch_collide_t(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* c
   return cudaSuccess;
 }
 
-// Angular-momentum-conserving collision: every group goes through the per-cell path (a warp
-// per group, a lane per cell), the only one compiled with the correction, so the staged
-// kernel's code is untouched.  Periodic boxes only.
+// A group of at most kMixCap records with angular-momentum conservation: the warp gathers and
+// streams the records into its stage st (lane = record), each lane collides its cells there
+// (lane = cell; the same per-cell arithmetic and member order as collide_group_direct, so the
+// same results), and the warp writes them out in cell order with the next step's keys.
+template <int FORCE, int THERMO, int MOMENTS>
+__device__ __noinline__ void collide_group_staged_ang(const Geom* __restrict__ gp, const BoxShift* __restrict__ shp,
+                                                      int64_t c0, int ncells, int E0, int E,
+                                                      const int32_t* __restrict__ offset,
+                                                      const int32_t* __restrict__ perm, double* moments,
+                                                      const MixRec* __restrict__ src, MixRec* __restrict__ dst,
+                                                      int32_t* __restrict__ knext, int32_t* __restrict__ cnext,
+                                                      int64_t t1, int lane, MixRec* st) {
+  const Geom& g = *gp;
+  const float sf[3] = {shp->sf_next[0], shp->sf_next[1], shp->sf_next[2]};
+  const int cbase = static_cast<int>(g.cbase);
+  for (int e = lane; e < E; e += 32) {
+    MixRec r = load_rec(src + perm[E0 + e]);
+    stream_record<0, FORCE>(g, r);
+    st[e] = r;
+  }
+  __syncwarp();
+  for (int64_t c = c0 + lane; c < c0 + ncells; c += 32) {
+    const int o = offset[c] - E0;
+    const int n = offset[c + 1] - offset[c];
+    CellMoments cm;
+    moments_zero(cm);
+    bool ok = true;
+    for (int j = 0; j < n; ++j) ok &= moments_add(cm, st[o + j], shp->sf);
+    mixed_collide_cell<0, THERMO, MOMENTS, 1>(g, st + o, n, c - cbase, t1, shp->s[2],
+                                              MOMENTS ? moments + 5 * (int64_t)cbase : nullptr, shp->sf, &cm, ok);
+  }
+  __syncwarp();
+  for (int e = lane; e < E; e += 32) {
+    const MixRec r = st[e];
+    store_rec(dst + E0 + e, r);
+    const int k = cbase + next_key<0, FORCE>(g, r, sf);
+    knext[E0 + e] = k;
+    atomicAdd(&cnext[k], 1);
+  }
+  __syncwarp();  // the stage is reused by the warp's next group
+}
+
+// Angular-momentum-conserving collision: a warp per group, only these paths compiled with the
+// correction, so the staged kernel's code is untouched.  Groups of at most kMixCap records
+// are staged in shared memory; larger ones go through collide_group_direct.  Periodic boxes
+// only.
 template <int FORCE, int THERMO, int MOMENTS>
 __global__ void __launch_bounds__(128) k_collide_direct_mixed(MixBatch mb, MixBufs b, MixScratch s,
                                                               Ctl* __restrict__ ctl) {
-  const int lane = threadIdx.x & 31;
+  __shared__ MixRec stage[4][kMixCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
   const int64_t t1 = ctl->t + 1;
   const int cur = ctl->cur, nxt = cur ^ 1;
   for (int64_t gi = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; gi < mb.ngroups; gi += warps) {
     const MixGroup d = mb.groups[gi];
-    collide_group_direct<0, FORCE, THERMO, MOMENTS, 1>(mb.boxes + d.box, mb.shifts + d.box, d.c0, d.ncells, s.offset,
-                                                       s.perm, s.moments, b.rec[cur], b.rec[nxt], s.key[nxt],
-                                                       s.count[nxt], t1, lane);
+    const int E0 = s.offset[d.c0], E = s.offset[d.c0 + d.ncells] - E0;
+    if (E <= kMixCap)
+      collide_group_staged_ang<FORCE, THERMO, MOMENTS>(mb.boxes + d.box, mb.shifts + d.box, d.c0, d.ncells, E0, E,
+                                                       s.offset, s.perm, s.moments, b.rec[cur], b.rec[nxt],
+                                                       s.key[nxt], s.count[nxt], t1, lane, stage[warp]);
+    else
+      collide_group_direct<0, FORCE, THERMO, MOMENTS, 1>(mb.boxes + d.box, mb.shifts + d.box, d.c0, d.ncells,
+                                                         s.offset, s.perm, s.moments, b.rec[cur], b.rec[nxt],
+                                                         s.key[nxt], s.count[nxt], t1, lane);
   }
 }
 
