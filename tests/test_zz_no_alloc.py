@@ -22,10 +22,14 @@ def _device_soa(torch, a):
     return [torch.from_numpy(np.ascontiguousarray(a[:, d])).to("cuda") for d in range(3)]
 
 
-def test_noalloc_step_matches_handle_path():
+@pytest.mark.parametrize("kw", [dict(), dict(thermostat=2), dict(angular=1, thermostat=1)],
+                         ids=["plain", "mbs_thermostat", "angular_thermostat"])
+def test_noalloc_step_matches_handle_path(kw):
+    """With a thermostat both paths take the per-cell kernel; plain boxes compare the
+    per-cell kernel with the dense pair."""
     torch = pytest.importorskip("torch")
     L = (12, 10, 8)
-    p = abi.make_params(L, resort_k=0, seed=4242)
+    p = abi.make_params(L, resort_k=0, seed=4242, **kw)
     n = int(round(p.ppc * 12 * 10 * 8))
     r, v = inputs.uniform_gaussian_state(L, n, 99)
     t0 = 5
