@@ -44,6 +44,7 @@ struct mpcd_s {
   Geom geom{};
   int64_t n = 0, ncell = 0;
   Fp64Bufs f64{};
+  double* host_stage = nullptr;  // 6 N doubles for the host get/set_state copies, made on first use
   double* mass_buf[3] = {};  // FP64 particle masses: storage order (two buffer sets), id order
   Fp64Mass f64m{};           // points at mass_buf[0..1] while masses are set
   bool masses = false;
@@ -690,14 +691,25 @@ int mpcd_get_masses(mpcd_t* h, double* m) {
   return MPCD_OK;
 }
 
+// The handle's staging buffer for host copies of the state (6 N doubles), allocated on the
+// first host get/set_state and kept: a stream-ordered allocation per call would map and
+// release it again at every synchronisation.
+static int host_stage(mpcd_t* h, double** out) {
+  if (!h->host_stage) {
+    int rc = dalloc(h, &h->host_stage, 6 * (h->n > 0 ? h->n : 1));
+    if (rc) return rc;
+  }
+  *out = h->host_stage;
+  return MPCD_OK;
+}
+
 int mpcd_get_state(mpcd_t* h, double* r, double* v) {
   int rc = guard(h);
   if (rc) return rc;
   if (!r || !v) return fail(h, MPCD_ERR_ARG, "NULL output");
-  // gather into a stream-ordered scratch of 6 N doubles, then copy to the host
+  // gather into the staging buffer, then copy to the host
   double* scratch = nullptr;
-  MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 6 * (size_t)(h->n > 0 ? h->n : 1),
-                              h->stream));
+  if ((rc = host_stage(h, &scratch))) return rc;
   if (h->precision == MPCD_MIXED)
     launch_get_state_mixed(h->mb, h->mix, h->cur, scratch, scratch + 3 * h->n, h->stream);
   else
@@ -706,7 +718,6 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(r, scratch, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(v, scratch + 3 * h->n, sizeof(double) * 3 * (size_t)h->n, cudaMemcpyDeviceToHost, h->stream);
-  cudaFreeAsync(scratch, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
   h->launches += 1;
@@ -715,7 +726,7 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v) {
 
 // Reject a state with a position outside its box or a non-finite velocity before any of it
 // is applied (checked on the device; synchronises).
-int check_state(mpcd_t* h, const double* r_dev, const double* v_dev) {
+static int check_state(mpcd_t* h, const double* r_dev, const double* v_dev) {
   MPCD_TRY(h, cudaMemsetAsync(h->d_bad, 0xFF, sizeof(unsigned long long), h->stream));
   launch_check_state(h->precision == MPCD_MIXED ? &h->mb : nullptr, h->geom, h->n, r_dev, v_dev, h->d_bad, h->stream);
   MPCD_TRY(h, cudaGetLastError());
@@ -763,15 +774,11 @@ int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!r || !v || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
   double* scratch = nullptr;  // the state is uploaded, then checked and applied on the device
-  MPCD_TRY(h, cudaMallocAsync(reinterpret_cast<void**>(&scratch), sizeof(double) * 6 * (size_t)(n > 0 ? n : 1), h->stream));
+  if ((rc = host_stage(h, &scratch))) return rc;
   cudaError_t e = cudaMemcpyAsync(scratch, r, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + 3 * n, v, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(scratch, h->stream);
-    return cuda_fail(h, e, "set_state copy");
-  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state copy");
   rc = mpcd_set_state_device(h, n, scratch, scratch + 3 * n, t);
-  cudaFreeAsync(scratch, h->stream);
   if (rc) return rc;
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   return MPCD_OK;

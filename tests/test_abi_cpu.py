@@ -36,6 +36,9 @@ def test_library_exports_every_declared_symbol(libpath):
     lib = abi.lib()
     for f in declared_functions():
         assert hasattr(lib, f)
+    # and no other C-linkage function: internal helpers stay out of the ABI
+    c_symbols = set(re.findall(r"\bT ([A-Za-z][A-Za-z0-9_]*)\n", out))
+    assert c_symbols <= set(declared_functions()), sorted(c_symbols - set(declared_functions()))
 
 
 def test_params_layout_matches_c(tmp_path):
