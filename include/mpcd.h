@@ -117,7 +117,9 @@ int64_t mpcd_steps_done(const mpcd_t* h);    /* steps enqueued since the state w
 int32_t mpcd_num_boxes(const mpcd_t* h);     /* 1 for mpcd_create                          */
 
 /* Copy the state to host arrays r[N*3], v[N*3] (FP64, particle-id order).  Mixed-precision
- * positions are returned as (cell index + offset) * a.  Synchronises. */
+ * positions are returned as (cell index + offset) * a.  Synchronises.  The first host
+ * get/set_state call allocates a device staging buffer of 6 N doubles, kept until
+ * mpcd_destroy. */
 int mpcd_get_state(mpcd_t* h, double* r, double* v);
 
 /* Replace the state from host arrays r[n*3], v[n*3] (particle-id order) and set the step
