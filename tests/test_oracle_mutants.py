@@ -53,6 +53,19 @@ MUTANTS = [
      "K += 0.5 * (vi[d] - u[d]) * (vi[d] - u[d]);", "mass"),
     ("masses left behind on re-sort", "m2[j] = mass ? mass[i] : 0.0;", "m2[j] = mass ? mass[j] : 0.0;", "mass"),
     ("centre of mass unweighted", "mean[d] += mass ? mass[perm[j]] * l[d] : l[d];", "mean[d] += l[d];", "mass"),
+    ("virtual mass left out of the cell mass", "        M += Mv;\n", "        M += 0.0;\n", "virtual"),
+    ("virtual momentum variance without the mass", "double sd = sqrt(Mv * p->kT);",
+     "double sd = sqrt(Mv * p->kT / m);", "virtual"),
+    ("virtual momentum variance from the real particles", "double sd = sqrt(Mv * p->kT);",
+     "double sd = sqrt((double)nc * m * p->kT);", "virtual"),
+    ("virtual fill in every layer", "if ((layer == 0 || layer == p->L[2]) && (double)nc < p->ppc) {",
+     "if ((double)nc < p->ppc) {", "virtual"),
+    ("virtual fill in the wrong wall layer", "if ((layer == 0 || layer == p->L[2]) && (double)nc < p->ppc) {",
+     "if ((layer == 0 || layer == p->L[2] - 1) && (double)nc < p->ppc) {", "virtual"),
+    ("virtual fill count rounded down", "double Mv = (p->ppc - (double)nc) * m;",
+     "double Mv = (floor(p->ppc) - (double)nc) * m;", "virtual"),
+    ("virtual momentum on the axis stream", "draw(p, (uint64_t)t, (uint64_t)c, ORC_TAG_WALL, w);",
+     "draw(p, (uint64_t)t, (uint64_t)c, ORC_TAG_AXIS, w);", "virtual"),
     ("cofactor indices swapped", "cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a2][b1];",
      "cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a1][b2];", "angular or omega or two_particle"),
 ]

@@ -9,6 +9,8 @@ import os
 import numpy as np
 import pytest
 
+from restate import philox as _numpy_philox
+
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "philox4x64_10_kat.txt")
 
 
@@ -28,18 +30,6 @@ def _kat_rows():
 @pytest.mark.parametrize("ctr,key,expect", _kat_rows())
 def test_published_kat(orc, ctr, key, expect):
     assert [int(x) for x in orc.philox(ctr, key)] == expect
-
-
-def _numpy_philox(ctr, key):
-    # numpy's Philox advances its 256-bit counter by one before producing a block, so the
-    # block for counter c comes from a generator started at c - 1.
-    c = 0
-    for i, w in enumerate(ctr):
-        c |= int(w) << (64 * i)
-    c = (c - 1) % (1 << 256)
-    start = np.array([(c >> (64 * i)) & ((1 << 64) - 1) for i in range(4)], dtype=np.uint64)
-    bg = np.random.Philox(key=np.array(key, dtype=np.uint64), counter=start)
-    return [int(x) for x in bg.random_raw(4)]
 
 
 def test_matches_numpy_philox(orc):

@@ -100,3 +100,120 @@ def test_poiseuille_profile(orc):
     assert abs(vertex - H / 2) < 0.05 * H              # symmetric between the walls
     assert abs(coef[0]) < 0.15 * vmax                  # little slip at z = 0
     assert abs(coef[0] + coef[1] * H + coef[2] * H * H) < 0.15 * vmax  # and at z = H
+
+
+# ---- R13: virtual particles in the cells cut by a wall ------------------------------------
+# A cell of the bottom layer (z below the shift) or of the top layer (z above Lz - 1 + s_z)
+# is cut by a wall.  If it holds n_c < ppc real particles it is filled up to ppc with virtual
+# particles of the box mass m, at rest on average: their summed momentum is Gaussian with
+# variance (ppc - n_c) m kT per component (the equipartition value of that many particles),
+# drawn by Box-Muller from Philox counter (t, cell, WALL, 0).  The centre-of-mass velocity of
+# the collision is then (m sum v + P_virtual) / (n_c m + (ppc - n_c) m).
+
+def _virtual_fill_expected(p, seed, t, r, v, m, kT, ppc, alpha, L):
+    """Velocities after one step with dt = 0, recomputed from the definition above with
+    numpy's Philox, Box-Muller written out and scipy's rotation (nothing from the oracle)."""
+    from scipy.spatial.transform import Rotation
+
+    import restate
+
+    s = restate.shift(seed, t, walls_z=True)
+    keys = []
+    for rr in r:
+        cx = int(math.floor(rr[0] - s[0])) % L[0]
+        cy = int(math.floor(rr[1] - s[1])) % L[1]
+        cz = min(max(int(math.floor(rr[2] - s[2])) + 1, 0), L[2])
+        keys.append(cx + L[0] * (cy + L[1] * cz))
+    keys = np.array(keys)
+    out = v.copy()
+    filled = set()
+    for c in np.unique(keys):
+        idx = np.nonzero(keys == c)[0]
+        nc = idx.size
+        P = m * v[idx].sum(axis=0)
+        M = nc * m
+        layer = c // (L[0] * L[1])
+        fill = (layer == 0 or layer == L[2]) and nc < ppc
+        if fill:
+            Mv = (ppc - nc) * m
+            w = restate.draw(seed, t, int(c), restate.TAG_WALL)
+            g0, g1 = restate.box_muller(w[0], w[1])
+            g2, _ = restate.box_muller(w[2], w[3])
+            P = P + math.sqrt(Mv * kT) * np.array([g0, g1, g2])
+            M = M + Mv
+            filled.add(int(c))
+        if nc < 2 and not fill:
+            continue
+        u = P / M
+        R = Rotation.from_rotvec(alpha * restate.axis(seed, t, int(c))).as_matrix()
+        out[idx] = u + (v[idx] - u) @ R.T
+    return out, filled, s
+
+
+def test_virtual_fill_closed_form(orc):
+    """Cut cells at both walls with fewer than ppc particles (three, and one), a cut cell
+    holding more than ppc, and an interior cell: every velocity after the collision equals
+    its value recomputed from the virtual-particle definition (m = 2, kT = 1.7 and a
+    fractional ppc, so that a missing mass factor, a wrong variance or a rounded fill
+    count shows)."""
+    L = (3, 2, 4)
+    m, kT, ppc, seed, alpha = 2.0, 1.7, 6.5, 4244, math.radians(100.0)
+    p = orc.make_params(L, walls_z=1, dt=0.0, alpha=alpha, mass=m, kT=kT, ppc=ppc, seed=seed)
+    import restate
+    s = restate.shift(seed, 1, walls_z=True)
+    assert 0.1 < s[2] < 0.9, s              # both wall layers are genuinely cut
+    rng = np.random.default_rng(11)
+
+    def at(cx, cy, z, k):
+        x = (cx + s[0] + 0.5) % L[0] + np.linspace(-0.3, 0.3, k)
+        y = (cy + s[1] + 0.5) % L[1] + np.linspace(0.2, -0.2, k)
+        return np.stack([np.mod(x, L[0]), np.mod(y, L[1]), np.full(k, z)], axis=1)
+
+    bottom = 0.5 * s[2]                     # layer 0: z in [0, s_z)
+    top = 0.5 * ((L[2] - 1 + s[2]) + L[2])  # layer Lz: z in [Lz - 1 + s_z, Lz)
+    interior = 1.5 + s[2]                   # layer 2
+    r = np.concatenate([at(0, 0, bottom, 3), at(1, 1, top, 3), at(2, 0, bottom, 1), at(0, 1, top, 7),
+                        at(1, 0, interior, 3)])
+    v = rng.normal(0.0, 1.0, r.shape) + np.array([0.4, -0.2, 0.1])
+    st = orc.State(r, v)
+    orc.step(p, st)
+    _, vr = st.by_id()
+    expect, filled, _ = _virtual_fill_expected(p, seed, 1, r, v, m, kT, ppc, alpha, L)
+    assert len(filled) == 3                 # the two three-particle cells and the lone particle
+    assert np.abs(vr - expect).max() < 1e-13, np.abs(vr - expect).max()
+    # the interior cell and the over-full cut cell are the plain collision (no fill)
+    assert not np.allclose(vr[-3:], v[-3:])
+
+
+def test_virtual_fill_only_in_cut_layers_and_variance(orc):
+    """One particle at rest in every cell, dt = 0, alpha = 180 degrees.  Interior cells hold a
+    single particle and no virtual ones, so nothing changes there.  In a cut cell the
+    collision gives v' = u + R(0 - u) = 2 u_perp, with u = P_virtual / (ppc m), hence
+    <|v'|^2> = (8/3) <|u|^2> = 8 (ppc - 1) kT / (ppc^2 m) over steps and cells, and the mean
+    of v' is zero."""
+    import restate
+
+    L = (6, 6, 3)
+    m, kT, ppc, seed = 2.0, 1.3, 5.5, 99
+    p = orc.make_params(L, walls_z=1, dt=0.0, alpha=math.pi, mass=m, kT=kT, ppc=ppc, seed=seed)
+    samples = []
+    for t in range(1, 151):
+        s = restate.shift(seed, t, walls_z=True)
+        xs = (np.arange(L[0]) + s[0] + 0.5) % L[0]
+        ys = (np.arange(L[1]) + s[1] + 0.5) % L[1]
+        zs = [0.5 * s[2]] + [k + s[2] - 0.5 for k in range(1, L[2])] + [0.5 * ((L[2] - 1 + s[2]) + L[2])]
+        grid = np.array([[x, y, z] for z in zs for y in ys for x in xs])
+        st = orc.State(grid, np.zeros_like(grid), t=t - 1)
+        orc.step(p, st)
+        _, vr = st.by_id()
+        layer = np.repeat(np.arange(L[2] + 1), L[0] * L[1])
+        cut = (layer == 0) | (layer == L[2])
+        assert np.all(vr[~cut] == 0.0), t   # no virtual particles in the interior
+        assert np.all(np.abs(vr[cut]).sum(axis=1) > 0.0), t
+        samples.append(vr[cut])
+    vv = np.concatenate(samples)
+    expect = 8.0 * (ppc - 1.0) * kT / (ppc * ppc * m)
+    got = (vv * vv).sum(axis=1).mean()
+    assert abs(got / expect - 1.0) < 0.05, (got, expect)
+    sem = math.sqrt(expect / 3.0 / len(vv))
+    assert np.all(np.abs(vv.mean(axis=0)) < 5.0 * sem)
