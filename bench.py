@@ -78,6 +78,20 @@ FORMS = ("mixed_L256", "batched_256", "poiseuille_256x64x64", "poiseuille_256x64
          "mixed_L128_angular", "fp64_L128_masses")
 
 
+# What each form reaches against the FP64 oracle (the parity and error-report tests), stated
+# beside its speed-up over the plain FP64 form (which matches the oracle to 1e-12).
+FORM_ACCURACY = {
+    "mixed_L256": "mixed: one step from identical states v within 8.9e-7 relative, positions 6e-8 cells, "
+                  "per-cell momentum 1.3e-7 and energy 3e-7 per collision (64^3 error report)",
+    "batched_256": "mixed, per box as mixed_L256; every box bit-identical to the box alone",
+    "poiseuille_256x64x64": "mixed with walls; Poiseuille profile within 1.8% rms of the FP64 form",
+    "poiseuille_256x64x64_mbs": "mixed with walls and MBS thermostat; canonical cell energies (KS)",
+    "fp64_L128_angular": "FP64: 1e-12 against the oracle (omega scaled by the inertia tensor's condition)",
+    "mixed_L128_angular": "mixed: per-cell momentum and angular momentum conserved to FP32 rounding",
+    "fp64_L128_masses": "FP64: 1e-12 against the oracle",
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -150,45 +164,56 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None}
 
 
-def cpu_oracle_run(w, steps, sample_note):
-    """Time the FP64 oracle (as it stands, one thread) on the workload on the host."""
+def cpu_oracle_run(w, steps, sample_note, all_cores=False):
+    """Time the FP64 oracle as it stands on the workload on the host: its serial build on one
+    core, or (all_cores) the same source built with OpenMP on every core of the host."""
     from oracle import oracle as orc
-    p = orc.make_params(w.L, a=w.a, dt=w.dt, alpha_deg=w.alpha_deg, kT=w.kT, mass=w.mass, ppc=w.ppc, seed=w.seed,
-                        resort_k=w.resort_k, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat)
-    r, v = orc.init(p, w.n_particles)
-    st = orc.State(r, v)
-    orc.step(p, st)   # untimed first step (page-in)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        orc.step(p, st)
-    dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    orc.use_openmp(all_cores)
+    try:
+        p = orc.make_params(w.L, a=w.a, dt=w.dt, alpha_deg=w.alpha_deg, kT=w.kT, mass=w.mass, ppc=w.ppc, seed=w.seed,
+                            resort_k=w.resort_k, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat,
+                            angular=getattr(w, "angular", 0))
+        r, v = orc.init(p, w.n_particles)
+        st = orc.presort(p, orc.State(r, v))
+        orc.step(p, st)   # untimed first step (page-in)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            orc.step(p, st)
+        dt = time.perf_counter() - t0
+    finally:
+        orc.use_openmp(False)
     value = w.n_particles * steps / dt
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%s: %d oracle steps of the full %d-particle box (%.1f s), single thread" % (
-                sample_note, steps, w.n_particles, dt)}
+    how = ("OpenMP build of the same source, %d threads" % cores) if all_cores else "serial build, single thread"
+    return {"value": value, "unit": UNIT, "cores": cores if all_cores else 1, "kind": "oracle",
+            "sample": "%s: %d oracle steps of the full %d-particle box (%.1f s), %s" % (
+                sample_note, steps, w.n_particles, dt, how)}
 
 
-REF_SAMPLE_L = 32         # reference arm: one oracle step per timed step on a 32^3 sub-box
-REF_TIME_LIMIT_S = 150.0  # ... and at most this much timed CPU work in all
+REF_TIME_LIMIT_S = 150.0  # the reference arm stops its timed steps after this much CPU time
 
 
 def run_reference(args, w):
-    """The reference arm: the FP64 oracle as it stands, single thread, on the host cores.  Each
-    step is a bounded sample of the workload: one oracle step of a sub-box of side 32 (or
-    the box itself if smaller) with the workload's density and parameters; the timed steps
-    stop early once REF_TIME_LIMIT_S of CPU time is spent (stated in `sample`)."""
+    """The reference arm: the FP64 oracle as it stands (its OpenMP build, every host core) on
+    the full workload box, from the same initial state as the library; the timed steps stop
+    early once REF_TIME_LIMIT_S of wall time is spent (stated in `sample`)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from oracle import oracle as orc
-    L = tuple(min(int(x), REF_SAMPLE_L) for x in w.L)
-    n = int(round(w.ppc * L[0] * L[1] * L[2]))
-    p = orc.make_params(L, a=w.a, dt=w.dt, alpha_deg=w.alpha_deg, kT=w.kT, mass=w.mass, ppc=w.ppc, seed=w.seed,
-                        resort_k=w.resort_k, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat)
+    cores = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    orc.use_openmp(True)
+    n = w.n_particles
+    p = orc.make_params(w.L, a=w.a, dt=w.dt, alpha_deg=w.alpha_deg, kT=w.kT, mass=w.mass, ppc=w.ppc, seed=w.seed,
+                        resort_k=w.resort_k, walls_z=w.walls_z, g=w.g, thermostat=w.thermostat,
+                        angular=getattr(w, "angular", 0))
     r, v = orc.init(p, n)
-    st = orc.State(r, v)
+    st = orc.presort(p, orc.State(r, v))
     for _ in range(max(1, args.warmup)):
         orc.step(p, st)
+        if st.t >= 3:
+            break
     done, t_cpu = 0, 0.0
     for _ in range(max(1, args.steps)):
         t0 = time.perf_counter()
@@ -198,13 +223,15 @@ def run_reference(args, w):
         if t_cpu > REF_TIME_LIMIT_S:
             break
     value = n * done / t_cpu
-    sample = ("%d oracle steps (of %d asked; %d warm-up) of a %dx%dx%d sub-box, %d particles, same density and "
-              "parameters as %s; %.1f s single thread" % (done, args.steps, args.warmup, L[0], L[1], L[2], n, w.name, t_cpu))
+    sample = ("%d oracle steps (of %d asked; %d warm-up) of the full %s box (%d particles); OpenMP build of the "
+              "oracle source, %d threads; %.1f s" % (done, args.steps, min(max(1, args.warmup), 3), w.name, n,
+                                                      int(os.environ["OMP_NUM_THREADS"]), t_cpu))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "L": list(w.L), "particles": w.n_particles, "precision": w.precision},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": w.name, "L": list(w.L), "particles": n, "precision": w.precision},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(os.environ["OMP_NUM_THREADS"]),
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -296,7 +323,7 @@ def kernel_table(p, mixed, n, C, ktimes, steps):
     return kernels
 
 
-def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True):
+def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True, fp64_probe=None):
     """The dominant kernel against its bound: HBM bytes (mixed form) or the FP64 pipe (FP64
     form: measured traffic stays far below HBM; the FP64 instruction count sets the floor).
     `captured`: the kernel variant is the one the ncu traffic figure was taken on (periodic,
@@ -319,6 +346,8 @@ def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True):
             "traffic": tr[0] * n if tr else None, "traffic_source": tr[1] if tr else None,
             "peak_source": "derived: %d SMs x %d FP64 instructions/clock x %.0f MHz" % (SMS, FP64_PER_CLK, SM_MAX_MHZ),
             "algo_fp64_ops_per_launch": d["fp64_ops_per_step"] / max(d["launches_per_step"], 1.0),
+            "peak_measured": fp64_probe, "frac_of_measured": d["fp64_gops"] / fp64_probe if fp64_probe else None,
+            "peak_measured_source": "mpcd_measure_fp64_rate: chains of independent DFMAs on every SM, this run",
             "hbm_gbs": d["gbs"], "hbm_frac": d["gbs"] / hbm_peak}
 
 
@@ -350,6 +379,7 @@ def main():
     peak_src = "measured" if hbm_peak else "fallback"
     hbm_peak = hbm_peak or 6800.0
 
+    fp64_probe = abi.mpcd_measure_fp64_rate() / 1e9   # G FP64 FMAs/s of this GPU, measured now
     stream = torch.cuda.Stream()
     w, p, box, ensemble = open_box(abi, inputs, args.workload, rank)
     h = box.h
@@ -382,6 +412,15 @@ def main():
     e2e_value, _, _ = replicas.job_throughput(n * args.e2e_steps, e2e_s * 1e3, dist if world > 1 else None, device="cuda")
     C = box.ncell
     kernels = kernel_table(p, mixed, n, C, ktimes, args.steps)
+    # the basis of the forms' speed-ups: this box again, timed over the forms' step count
+    basis = None
+    if not mixed and not args.no_forms:
+        box.set_state(r_np, v_np, abi.mpcd_steps_done(h))
+        box.step(args.warmup)
+        box.sync()
+        bval, bms, _, _, _ = timed_steps(abi, torch, dist, box, stream, args.form_steps, world)
+        basis = {"workload": w.name, "value": bval, "steps": args.form_steps, "warmup": args.warmup,
+                 "ms_per_step": bms / args.form_steps}
     box.close()
     del r_h, v_h
 
@@ -405,7 +444,8 @@ def main():
                 froof = None
             forms[name] = {"value": fval, "unit": UNIT, "steps": args.form_steps, "ms_per_step": fms / args.form_steps,
                            "particles": fn, "cells": fbox.ncell, "boxes": fw.rec.nbox if fens else 1,
-                           "speedup_vs_fp64": fval / value, "gpu_launches": fl,
+                           "speedup_vs_fp64": fval / basis["value"], "accuracy": FORM_ACCURACY.get(name),
+                           "gpu_launches": fl,
                            "hbm_roofline_frac_step": fval / world * (ALGO_STEP_BYTES_MIXED if fmixed else
                                                                      ALGO_STEP_BYTES_FP64) / 1e9 / hbm_peak,
                            "roofline": froof,
@@ -415,7 +455,9 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not ensemble:
-        cpu = cpu_oracle_run(w, args.cpu_steps, "cpu_baseline")
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        cpu = cpu_oracle_run(w, args.cpu_steps, "cpu_baseline", all_cores=True)
+        cpu["single_core"] = cpu_oracle_run(w, args.cpu_steps, "cpu_baseline")
 
     if rank == 0:
         ms_step = ms / args.steps
@@ -430,9 +472,10 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "hbm_roofline_frac_step": value / world * (ALGO_STEP_BYTES_MIXED if mixed else ALGO_STEP_BYTES_FP64) / 1e9
             / hbm_peak,
-            "roofline": roofline_of(kernels, mixed, hbm_peak, peak_src, n),
+            "roofline": roofline_of(kernels, mixed, hbm_peak, peak_src, n, fp64_probe=fp64_probe),
             "kernels": kernels,
             "forms": forms or None,
+            "forms_basis": basis,
             "gpu_launches": launches,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": n * 48, "d2h_bytes_per_step": n * 48,

@@ -38,7 +38,9 @@ enum {
   MPCD_OK = 0,
   MPCD_ERR_ARG = -1,     /* invalid argument; nothing was changed */
   MPCD_ERR_CUDA = -2,    /* a CUDA call failed; the handle is now poisoned */
-  MPCD_ERR_OOM = -3,     /* device memory ran out while creating */
+  MPCD_ERR_OOM = -3,     /* device memory ran out (create, or the first call that needs a */
+                         /* buffer: host get/set_state, set_masses, record_moments); the    */
+                         /* handle is not poisoned and nothing was changed                  */
   MPCD_ERR_TIMEOUT = -4, /* reserved for a bounded device-side wait that gave up; no kernel  */
                          /* of this library waits on another (the scan is multi-pass), so   */
                          /* no call returns it                                               */
@@ -81,8 +83,9 @@ typedef struct {
 
 /* Create a box and initialise it on the current CUDA device (Sec. 4 workload): positions
  * uniform in the box, velocities N(0, kT/m) per component with the net momentum removed,
- * drawn from Philox counters (i, 0, 0, 0) and (i, 1, 0, 0).  *out receives the handle, or
- * NULL on failure.  Errors: MPCD_ERR_ARG for invalid params, MPCD_ERR_OOM, MPCD_ERR_CUDA. */
+ * drawn from Philox counters (i, 0, 0, 0) and (i, 1, 0, 0).  The FP64 form then stores the
+ * particles in cell order (see mpcd_set_state).  *out receives the handle, or NULL on
+ * failure.  Errors: MPCD_ERR_ARG for invalid params, MPCD_ERR_OOM, MPCD_ERR_CUDA. */
 int mpcd_create(const mpcd_params* p, mpcd_t** out);
 
 /* Create an ensemble of nbox independent boxes (each with its own L, ppc, dt, alpha, g,
@@ -119,14 +122,19 @@ int32_t mpcd_num_boxes(const mpcd_t* h);     /* 1 for mpcd_create               
 /* Copy the state to host arrays r[N*3], v[N*3] (FP64, particle-id order).  Mixed-precision
  * positions are returned as (cell index + offset) * a.  Synchronises.  The first host
  * get/set_state call allocates a device staging buffer of 6 N doubles, kept until
- * mpcd_destroy. */
+ * mpcd_destroy; if that allocation fails the call returns MPCD_ERR_OOM, changes nothing and
+ * leaves the handle usable. */
 int mpcd_get_state(mpcd_t* h, double* r, double* v);
 
 /* Replace the state from host arrays r[n*3], v[n*3] (particle-id order) and set the step
  * counter to t (the next step is t + 1).  n must equal mpcd_num_particles.  Positions must
  * lie in their box ([0, L a) per axis) and velocities be finite; otherwise MPCD_ERR_ARG
  * (the message names the first offending particle) and the state is unchanged.  The check
- * runs on the device.  Synchronises. */
+ * runs on the device.  Storage order afterwards (FP64 form): the particles are stored in
+ * cell order of the unshifted grid (cell key of floor(r / a), stable in particle id), the
+ * Listing 1 `permute` applied once, so that the first steps already find each cell's members
+ * in neighbouring slots; the mixed form keeps id order until its first step.  Storage order
+ * is visible only through mpcd_debug_sort.  Synchronises. */
 int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64_t t);
 
 /* Per-particle masses (the m of the cell sums sum m v and sum m, Sec. 3.3 Listing 4), FP64
@@ -204,6 +212,14 @@ int64_t mpcd_launch_count(const mpcd_t* h);
  * The string is owned by the library. */
 const char* mpcd_last_error(const mpcd_t* h);
 
+/* Measurement aid (no counterpart in the paper): this GPU's FP64 fused multiply-add rate,
+ * in FP64 operations per second counted per thread (one DFMA of one lane = 1), from chains of
+ * independent DFMAs on every SM of the current device, best of three timed launches.  The
+ * FP64 form's kernels are bound by this rate, not by HBM, and bench reports them against it.
+ * Allocates 8 bytes and a stream for the duration of the call.  Errors: MPCD_ERR_ARG for
+ * NULL, MPCD_ERR_CUDA. */
+int mpcd_measure_fp64_rate(double* instr_per_s);
+
 /* Library build description, e.g. "libmpcd sm_103a". */
 const char* mpcd_version(void);
 
@@ -217,7 +233,9 @@ const char* mpcd_version(void);
  * Advances the box described by p (FP64 only; resort_k is ignored: storage order never
  * changes) from step t to t + 1, in place, on structure-of-arrays device arrays x, y, z,
  * vx, vy, vz of n particles, enqueued on `stream` (NULL: the legacy default stream).
- * Positions must already lie in the box.
+ * Positions must already lie in the box: they are not checked (a check would need a host
+ * synchronisation), and a position outside it, or a non-finite value, is clamped into an
+ * edge cell, which gives wrong physics without an error.
  *
  * Memory: nothing is allocated.  The sort's scratch lives in one static device array of
  * MPCD_NOALLOC_MAX_PARTICLES particles and MPCD_NOALLOC_MAX_CELLS cells (about 7 MB),
@@ -227,8 +245,13 @@ const char* mpcd_version(void);
  * ordering between them) race and give wrong results: serialise them.
  *
  * The first call on each device looks up the array's device address (with that device
- * current) and caches it; make that first call before any stream capture.
- * Errors: MPCD_ERR_ARG, MPCD_ERR_CUDA; the message is read with mpcd_last_error(NULL). */
+ * current) and caches it with the id of the current context; make that first call before
+ * any stream capture.  After a device reset the next call looks the address up again (the
+ * module is loaded anew), so that call, too, must come before any stream capture.
+ * Errors: MPCD_ERR_ARG, MPCD_ERR_CUDA (also when a CUDA error from earlier work is already
+ * pending on this thread: it is left pending, and nothing is launched).  The message is read
+ * with mpcd_last_error(NULL), a process-wide slot: callers on several threads see the last
+ * failure of any of them. */
 #define MPCD_NOALLOC_MAX_PARTICLES (1 << 19)
 #define MPCD_NOALLOC_MAX_CELLS (1 << 17)
 int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n, double* x, double* y, double* z, double* vx,

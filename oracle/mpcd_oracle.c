@@ -314,6 +314,7 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
   }
 
   /* 1. streaming (R1) */
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) stream_one(p, &r[3 * i], &v[3 * i]);
 
   /* 2. grid shift of this step (R2) */
@@ -321,6 +322,7 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
   orc_shift(p, t, s);
 
   /* 3. cell of every particle on the shifted grid (Sec. 3.1) */
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) key[i] = (int32_t)orc_cell_key(p, &r[3 * i], s);
 
   /* 4. linked-cell list as a stable counting sort (R6) */
@@ -332,8 +334,12 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
 
   /* 5.-7. per cell: centre of mass (Listing 4), relative velocity, rotation (Sec. 2) */
   const double m = p->mass;
+  /* cells are independent: each reads and writes only its own members and its own slice
+   * rho[3 off[c] ..] of the R23 scratch (the OpenMP build runs them in parallel) */
+#pragma omp parallel for schedule(dynamic, 256)
   for (int64_t c = 0; c < C; ++c) {
     int32_t nc = cnt[c];
+    double* rc = rho + 3 * (int64_t)off[c];
     double M = 0.0, P[3] = {0.0, 0.0, 0.0}, E = 0.0;
     for (int32_t j = off[c]; j < off[c + 1]; ++j) {
       const double* vi = &v[3 * (int64_t)perm[j]];
@@ -382,15 +388,15 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
     if (p->angular) {
       double mean[3] = {0.0, 0.0, 0.0};
       for (int32_t j = off[c]; j < off[c + 1]; ++j) {
-        double* l = &rho[3 * (int64_t)(j - off[c])];
+        double* l = &rc[3 * (int64_t)(j - off[c])];
         orc_cell_local(p, &r[3 * (int64_t)perm[j]], s, l);
         /* the centre of mass: with particle masses (R24) weighted, else the plain mean */
         for (int d = 0; d < 3; ++d) mean[d] += mass ? mass[perm[j]] * l[d] : l[d];
       }
       for (int d = 0; d < 3; ++d) mean[d] /= mass ? M : (double)nc;
       for (int32_t j = off[c]; j < off[c + 1]; ++j)
-        for (int d = 0; d < 3; ++d) rho[3 * (int64_t)(j - off[c]) + d] = p->a * (rho[3 * (int64_t)(j - off[c]) + d] - mean[d]);
-      cell_angular_momentum(p, mass, rho, v, perm, off[c], off[c + 1], Lb);
+        for (int d = 0; d < 3; ++d) rc[3 * (int64_t)(j - off[c]) + d] = p->a * (rc[3 * (int64_t)(j - off[c]) + d] - mean[d]);
+      cell_angular_momentum(p, mass, rc, v, perm, off[c], off[c + 1], Lb);
     }
 
     for (int32_t j = off[c]; j < off[c + 1]; ++j) orc_rotate(ax, p->alpha, u, &v[3 * (int64_t)perm[j]]);
@@ -420,10 +426,10 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
        * v_i += omega x rho_i, which keeps the cell's momentum (sum rho_i = 0) and restores
        * its angular momentum (sum m rho_i x (omega x rho_i) = I omega). */
       double La[3], dL[3], I[3][3] = {{0.0}}, rr = 0.0, rrm = 0.0;
-      cell_angular_momentum(p, mass, rho, v, perm, off[c], off[c + 1], La);
+      cell_angular_momentum(p, mass, rc, v, perm, off[c], off[c + 1], La);
       for (int d = 0; d < 3; ++d) dL[d] = Lb[d] - La[d];
       for (int32_t j = off[c]; j < off[c + 1]; ++j) {
-        const double* q = &rho[3 * (int64_t)(j - off[c])];
+        const double* q = &rc[3 * (int64_t)(j - off[c])];
         double q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
         const double mi = mass_of(p, mass, perm[j]);
         rr += q2;
@@ -437,7 +443,7 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
         /* two particles: rho_2 = -rho_1, I = m rr (1 - e e^T) with e = rho_1/|rho_1|; the
          * change of L is normal to e, where I acts as m rr */
         double e2 = rr > 0.0 ? 2.0 / rr : 0.0; /* 1/|rho_1|^2 */
-        const double* q = &rho[0];
+        const double* q = &rc[0];
         double along = (q[0] * dL[0] + q[1] * dL[1] + q[2] * dL[2]) * e2;
         if (rr > 0.0 && !mass) {
           for (int d = 0; d < 3; ++d) w[d] = (dL[d] - along * q[d]) / (p->mass * rr);
@@ -469,7 +475,7 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
       if (apply)
         for (int32_t j = off[c]; j < off[c + 1]; ++j) {
           double corr[3];
-          cross(w, &rho[3 * (int64_t)(j - off[c])], corr);
+          cross(w, &rc[3 * (int64_t)(j - off[c])], corr);
           double* vi = &v[3 * (int64_t)perm[j]];
           for (int d = 0; d < 3; ++d) vi[d] += corr[d];
         }
@@ -495,6 +501,7 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
       free(key); free(cnt); free(off); free(cur); free(perm);
       return -2;
     }
+#pragma omp parallel for schedule(static)
     for (int64_t j = 0; j < n; ++j) {
       int64_t i = perm[j];
       for (int d = 0; d < 3; ++d) {
@@ -512,5 +519,46 @@ int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, 
   }
 
   free(key); free(cnt); free(off); free(cur); free(perm);
+  return 0;
+}
+
+/* ------------------------------------------------------------------- presort ---- */
+/* R25: a stable counting sort of the storage by the cell of each position on the unshifted
+ * grid, then the permutation applied to every per-particle array. */
+int orc_presort(const orc_params* p, int64_t n, double* r, double* v, int32_t* id, double* mass) {
+  if (!p || n < 0) return -1;
+  if (n == 0) return 0;
+  int64_t C = orc_num_cells(p);
+  const double s0[3] = {0.0, 0.0, 0.0};
+  int32_t* key = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  int64_t* start = (int64_t*)calloc((size_t)C + 1, sizeof(int64_t));
+  int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  double* tmp = (double*)malloc(sizeof(double) * 3 * (size_t)n);
+  int32_t* itmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  if (!key || !start || !order || !tmp || !itmp) {
+    free(key); free(start); free(order); free(tmp); free(itmp);
+    return -2;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    key[i] = (int32_t)orc_cell_key(p, &r[3 * i], s0);
+    start[key[i] + 1] += 1;
+  }
+  for (int64_t c = 0; c < C; ++c) start[c + 1] += start[c];
+  for (int64_t i = 0; i < n; ++i) order[start[key[i]]++] = i; /* slot j holds old slot order[j] */
+  for (int64_t j = 0; j < n; ++j)
+    for (int d = 0; d < 3; ++d) tmp[3 * j + d] = r[3 * order[j] + d];
+  memcpy(r, tmp, sizeof(double) * 3 * (size_t)n);
+  for (int64_t j = 0; j < n; ++j)
+    for (int d = 0; d < 3; ++d) tmp[3 * j + d] = v[3 * order[j] + d];
+  memcpy(v, tmp, sizeof(double) * 3 * (size_t)n);
+  if (id) {
+    for (int64_t j = 0; j < n; ++j) itmp[j] = id[order[j]];
+    memcpy(id, itmp, sizeof(int32_t) * (size_t)n);
+  }
+  if (mass) {
+    for (int64_t j = 0; j < n; ++j) tmp[j] = mass[order[j]];
+    memcpy(mass, tmp, sizeof(double) * (size_t)n);
+  }
+  free(key); free(start); free(order); free(tmp); free(itmp);
   return 0;
 }

@@ -44,6 +44,10 @@
  *       P = sum m_i v_i, E = sum m_i v_i^2 / 2, the thermostat's kinetic energy and the
  *       angular-momentum correction weighted by m_i, the centre of mass of R23 mass-weighted.
  *       The rotation of v - u is unchanged; it conserves sum m_i v_i and sum m_i |v_i|^2 / 2.
+ *   R25 before a run the storage may be put in cell order once (orc_presort): a stable sort
+ *       by the cell of each position on the unshifted grid, the Listing 1 `permute` applied
+ *       to a state that was given in particle-id order.  It moves particles between storage
+ *       slots only; the stable in-cell order of R6 then follows the new storage order.
  */
 #ifndef MPCD_ORACLE_H
 #define MPCD_ORACLE_H
@@ -119,6 +123,12 @@ int orc_step(const orc_params* p, int64_t n, int64_t t, double* r, double* v, in
 int orc_step_m(const orc_params* p, int64_t n, int64_t t, double* r, double* v, int32_t* id, double* mass,
                int32_t* keys_out, int32_t* counts_out, int32_t* offsets_out, int32_t* perm_out,
                double* moments_out, double* shift_out);
+
+/* Put the storage in cell order before a run (reading R25): a stable sort of the storage
+ * slots by the cell key of each position on the unshifted grid (s = 0), the Listing 1
+ * `permute` applied once, so that particles of one cell sit together from the first step on.
+ * r, v (N x 3), id (N) and mass (N, may be NULL) are permuted together.  0 on success. */
+int orc_presort(const orc_params* p, int64_t n, double* r, double* v, int32_t* id, double* mass);
 
 #ifdef __cplusplus
 }

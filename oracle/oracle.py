@@ -21,26 +21,42 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(BUILD_DIR, "liborc.so")
+# the same source built with OpenMP: its pragmas run particles and cells in parallel, each
+# cell's arithmetic unchanged, so the results are the serial build's bits
+OMP_LIB_PATH = os.path.join(BUILD_DIR, "liborc_omp.so")
 SOURCES = [os.path.join(HERE, "mpcd_oracle.c")]
 
 TAG_INIT, TAG_SHIFT, TAG_AXIS, TAG_THERMO, TAG_WALL = 0, 1, 2, 3, 4
 
 _lock = threading.Lock()
 _lib = None
+_omp = False
 
 
-def build_library(force: bool = False) -> str:
-    """Compile ``liborc.so`` with gcc (plain C11, no fast-math, no implicit FMA contraction)."""
+def build_library(force: bool = False, openmp: bool = False) -> str:
+    """Compile ``liborc.so`` with gcc (plain C11, no fast-math, no implicit FMA contraction);
+    with ``openmp`` the same source with ``-fopenmp`` as ``liborc_omp.so``."""
     os.makedirs(BUILD_DIR, exist_ok=True)
+    path = OMP_LIB_PATH if openmp else LIB_PATH
     newest_src = max(os.path.getmtime(s) for s in SOURCES + [os.path.join(HERE, "mpcd_oracle.h")])
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest_src:
-        return LIB_PATH
-    tmp = LIB_PATH + ".tmp.%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-           "-o", tmp] + SOURCES + ["-lm"]
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= newest_src:
+        return path
+    tmp = path + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"] + \
+        (["-fopenmp"] if openmp else []) + ["-o", tmp] + SOURCES + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def use_openmp(flag: bool) -> None:
+    """Route every later call through the OpenMP build (True) or the serial one (False).
+    The thread count is OpenMP's (OMP_NUM_THREADS, else all cores)."""
+    global _lib, _omp
+    with _lock:
+        if flag != _omp:
+            _lib = None
+            _omp = flag
 
 
 class Params(ctypes.Structure):
@@ -89,7 +105,7 @@ def lib():
     with _lock:
         if _lib is None:
             # ORACLE_LIB lets the mutation tests load a deliberately broken copy
-            path = os.environ.get("ORACLE_LIB") or build_library()
+            path = os.environ.get("ORACLE_LIB") or build_library(openmp=_omp)
             L = ctypes.CDLL(path)
             u64p = ctypes.POINTER(ctypes.c_uint64)
             dp = ctypes.POINTER(ctypes.c_double)
@@ -119,6 +135,8 @@ def lib():
             L.orc_step.restype = ctypes.c_int
             L.orc_step_m.argtypes = [pp, ctypes.c_int64, ctypes.c_int64, dp, dp, ip, dp, ip, ip, ip, ip, dp, dp]
             L.orc_step_m.restype = ctypes.c_int
+            L.orc_presort.argtypes = [pp, ctypes.c_int64, dp, dp, ip, dp]
+            L.orc_presort.restype = ctypes.c_int
             _lib = L
         return _lib
 
@@ -252,6 +270,15 @@ def step(p: Params, st: State, debug: bool = False):
         out.update(keys=keys, counts=counts, offsets=offsets, perm=perm, moments=moments)
     out["shift"] = s
     return out
+
+
+def presort(p: Params, st: State) -> State:
+    """Put the storage of ``st`` in cell order of the unshifted grid, stable (reading R25);
+    ids and masses move with their particles."""
+    rc = lib().orc_presort(ctypes.byref(p), st.n, _dp(st.r), _dp(st.v), _ip(st.id), _dp(st.m))
+    if rc != 0:
+        raise RuntimeError("orc_presort failed with %d" % rc)
+    return st
 
 
 def run(p: Params, st: State, nsteps: int) -> State:

@@ -29,7 +29,7 @@ EXPORTS = [
     "mpcd_set_state", "mpcd_get_state_device", "mpcd_set_state_device", "mpcd_record_moments",
     "mpcd_cell_moments", "mpcd_debug_sort", "mpcd_timing", "mpcd_timing_read", "mpcd_launch_count",
     "mpcd_last_error", "mpcd_version", "mpcd_step_fp64_noalloc", "mpcd_box_offsets", "mpcd_get_tuning",
-    "mpcd_set_tuning", "mpcd_autotune", "mpcd_set_masses", "mpcd_get_masses",
+    "mpcd_set_tuning", "mpcd_autotune", "mpcd_set_masses", "mpcd_get_masses", "mpcd_measure_fp64_rate",
 ]
 MPCD_NOALLOC_MAX_PARTICLES = 1 << 19
 MPCD_NOALLOC_MAX_CELLS = 1 << 17
@@ -149,6 +149,7 @@ def lib():
                 "mpcd_launch_count": ([H], i64),
                 "mpcd_last_error": ([H], ctypes.c_char_p),
                 "mpcd_version": ([], ctypes.c_char_p),
+                "mpcd_measure_fp64_rate": ([dp], ctypes.c_int),
                 "mpcd_step_fp64_noalloc": ([ctypes.POINTER(Params), i64, i64] + [dp] * 6 + [ctypes.c_void_p],
                                            ctypes.c_int),
                 "mpcd_box_offsets": ([H, dp, dp], ctypes.c_int),
@@ -317,6 +318,15 @@ def mpcd_last_error(h=None) -> str:
 
 def mpcd_version() -> str:
     return lib().mpcd_version().decode()
+
+
+def mpcd_measure_fp64_rate() -> float:
+    """FP64 FMAs per second (counted per lane) of the current GPU, measured."""
+    out = ctypes.c_double(0.0)
+    rc = lib().mpcd_measure_fp64_rate(ctypes.byref(out))
+    if rc != MPCD_OK:
+        raise MpcdError(rc, "FP64 rate probe failed")
+    return out.value
 
 
 def mpcd_step_fp64_noalloc(params: Params, t: int, n: int, x, y, z, vx, vy, vz, stream=None):

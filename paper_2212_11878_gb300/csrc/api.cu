@@ -1,6 +1,7 @@
 // api.cu -- host runtime behind include/mpcd.h: handle lifetime, parameter checks, device
 // buffers, the per-step launch sequence (replayed from a captured CUDA graph), per-kernel
 // event timing and error reporting.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -352,6 +353,19 @@ int build_graph(mpcd_t* h) {
   return MPCD_OK;
 }
 
+// FP64 form: the state just written to buffer set 0 in particle-id order is put into cell
+// order (unshifted grid, stable by slot) in buffer set 1, which becomes the current set, so
+// that the first steps already read each cell's members from neighbouring slots.  The
+// caller writes the control block afterwards with cur = h->cur.
+int presort_fp64(mpcd_t* h) {
+  h->cur = 0;
+  if (h->precision != MPCD_FP64 || h->n == 0) return MPCD_OK;
+  h->launches += launch_presort_fp64(h->geom, h->f64, h->scr, h->f64m, h->stream);
+  MPCD_TRY(h, cudaGetLastError());
+  h->cur = 1;
+  return MPCD_OK;
+}
+
 int guard(mpcd_t* h) {
   if (!h) return MPCD_ERR_ARG;
   if (h->poisoned) return MPCD_ERR_STATE;
@@ -551,6 +565,12 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     launch_init_fp64(h->geom, h->f64, h->scr.red, h->red_blocks, h->ctl, h->stream);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return bail(cuda_fail(h, e, "init kernels"));
+  if ((rc = presort_fp64(h))) return bail(rc);
+  if (h->cur) {  // the presorted state is in buffer set 1 (the initial mean is no longer needed)
+    h->ctl_host.cur = h->cur;
+    if ((e = cudaMemcpyAsync(h->ctl, &h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+      return bail(cuda_fail(h, e, "cudaMemcpyAsync"));
+  }
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(h, e, "init sync"));
   *out = h;
   return MPCD_OK;
@@ -753,15 +773,16 @@ int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const doubl
     MPCD_TRY(h, cudaMemcpyAsync(h->mass_buf[0], h->mass_buf[2], sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice,
                                 h->stream));
   h->mixed_keys_valid = false;
+  if ((rc = presort_fp64(h))) return rc;
   h->ctl_host = Ctl{};
   h->ctl_host.t = t;
+  h->ctl_host.cur = h->cur;
   set_shifts(h->geom, &h->ctl_host);
   MPCD_TRY(h, cudaMemcpyAsync(h->ctl, &h->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, h->stream));
   if (h->precision == MPCD_MIXED)
     if ((rc = upload_shifts(h, t))) return rc;
   h->launches += 1;
   h->t = t;
-  h->cur = 0;
   h->any_step = false;
   h->last_resorted = false;
   h->moments_valid = false;
@@ -1017,7 +1038,40 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mu;
+// Per device: the scratch array's device address and the id of the context it was looked
+// up in.  A device reset (or any teardown of the primary context) loads the module again at
+// another address, so the address is looked up again whenever the current context's id
+// differs from the cached one.
 unsigned char* g_na_ptr[kNaMaxDevices] = {};
+unsigned long long g_na_ctx[kNaMaxDevices] = {};
+
+// The current context's unique id through the driver API, reached by entry point so that
+// the library needs no link against the driver library.  0 when it cannot be read.
+unsigned long long current_context_id() {
+  typedef CUresult (*GetCurrent)(CUcontext*);
+  typedef CUresult (*GetId)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {  // callers hold g_na_mu
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 __global__ void k_noalloc_ctl(Geom g, Ctl* c, int64_t t) {
   c->t = t;
@@ -1044,18 +1098,23 @@ extern "C" int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n
     return na_fail(MPCD_ERR_ARG, "the box has " + std::to_string(g.ncell) + " cells, more than MPCD_NOALLOC_MAX_CELLS = " +
                                      std::to_string(kNaMaxCells));
   if (n > 0 && !(x && y && z && vx && vy && vz)) return na_fail(MPCD_ERR_ARG, "NULL particle array");
+  // an error left pending by earlier work on this thread is not ours to report or clear
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "a CUDA error was already pending before mpcd_step_fp64_noalloc");
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
   if (dev < 0 || dev >= kNaMaxDevices) return na_fail(MPCD_ERR_ARG, "device index out of range");
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_na_ptr[dev] || ctx == 0 || ctx != g_na_ctx[dev]) {
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress");
       g_na_ptr[dev] = static_cast<unsigned char*>(ptr);
+      g_na_ctx[dev] = current_context_id();  // the lookup made the primary context current
     }
     base = g_na_ptr[dev];
   }

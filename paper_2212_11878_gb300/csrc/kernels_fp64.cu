@@ -848,7 +848,51 @@ __global__ void __launch_bounds__(kThreads) k_set_state_fp64(int64_t n, const do
   }
 }
 
+// ---- initial cell order (create / set_state) ----
+// Cell key of each current position on the unshifted grid and its arrival rank; positions
+// are only read.
+template <int POW2A>
+__global__ void __launch_bounds__(kThreads) k_presort_keys(Geom g, Fp64Bufs b, Scratch s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int cx = cell_coord<POW2A>(b.r[0][0][i], 0.0, g, 0);
+    const int cy = cell_coord<POW2A>(b.r[0][1][i], 0.0, g, 1);
+    const int cz = cell_coord<POW2A>(b.r[0][2][i], 0.0, g, 2);
+    const int k = cx + g.L[0] * (cy + g.L[1] * cz);
+    s.key[i] = k;
+    s.rank[i] = atomicAdd(&s.count[k], 1);
+  }
+}
+
+// Buffer set 1 slot j <- set 0 slot perm[j] (positions, velocities, ids, masses if any):
+// coalesced writes, gathered reads.
+__global__ void __launch_bounds__(kThreads) k_permute_fp64(int64_t n, const int32_t* __restrict__ perm, Fp64Bufs b,
+                                                           Fp64Mass ms) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = perm[j];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      b.r[1][d][j] = b.r[0][d][i];
+      b.v[1][d][j] = b.v[0][d][i];
+    }
+    b.id[1][j] = b.id[0][i];
+    if (ms.m[0]) ms.m[1][j] = ms.m[0][i];
+  }
+}
+
 }  // namespace
+
+int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaStream_t st) {
+  launch_zero_i32(s.count, g.ncell, st);
+  if (g.pow2a)
+    k_presort_keys<1><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s);
+  else
+    k_presort_keys<0><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s);
+  launch_scan(s.count, s.offset, s.partial, g.ncell, st);
+  launch_scatter(g, s, st);
+  launch_sort_segments(g, s, st);
+  k_permute_fp64<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.perm, b, ms);
+  return 8;  // kernels launched: zero, keys, scan (3), scatter, in-cell sort, gather
+}
 
 void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st) {
   k_init_fp64<<<red_blocks, kThreads, 0, st>>>(g, b, red);

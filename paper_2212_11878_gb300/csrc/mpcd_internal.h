@@ -132,6 +132,9 @@ void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl,
                                  Fp64Mass ms = Fp64Mass{});
 void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st);
 void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st);
+// Storage of buffer set 0 into cell order of the unshifted grid (stable by slot), written to
+// buffer set 1 with the ids and masses; returns the number of kernels launched.
+int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
 void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st);
 

@@ -51,7 +51,7 @@ def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True, masses=None):
         if masses is not None:
             box.set_masses(masses)
         op = oracle_params(orc, p)
-        st = orc.State(r, v, t=t0, m=masses)
+        st = orc.presort(op, orc.State(r, v, t=t0, m=masses))  # set_state stores in cell order
         mult = np.ones(len(r))
         for k in range(steps):
             box.step(1)
@@ -132,7 +132,7 @@ def test_particle_masses_api():
         box.step(5)  # two re-sorts
         assert np.array_equal(abi.mpcd_get_masses(box.h), m)
         r, v = box.state()
-        box.set_state(r, v, 5)  # storage back to id order: masses follow
+        box.set_state(r, v, 5)  # storage rebuilt from id order: masses follow
         assert np.array_equal(abi.mpcd_get_masses(box.h), m)
         # the box mass restored: the same steps as a box that never had masses
         r0, v0 = plain.state()
@@ -184,7 +184,7 @@ def test_trajectory_100_steps_L16(orc):
     p = abi.params_from_workload(w)
     op = oracle_params(orc, p)
     r0, v0 = orc.init(op, w.n_particles)
-    st = orc.State(r0, v0)
+    st = orc.presort(op, orc.State(r0, v0))
     with abi.Box(p) as box:
         box.set_state(r0, v0, 0)
         for _ in range(10):
@@ -207,8 +207,9 @@ def test_moments_match_oracle(orc):
         abi.mpcd_record_moments(box.h, True)
         box.step(1)
         mom, shift = box.moments()
-    st = orc.State(r, v)
-    ref = orc.step(oracle_params(orc, p), st, debug=True)
+    op = oracle_params(orc, p)
+    st = orc.presort(op, orc.State(r, v))
+    ref = orc.step(op, st, debug=True)
     assert np.array_equal(shift, ref["shift"])
     assert np.array_equal(mom[:, 0], ref["moments"][:, 0]) or np.allclose(mom[:, 0], ref["moments"][:, 0], rtol=1e-15)
     scale = np.maximum(np.abs(ref["moments"]).max(axis=0), 1.0)

@@ -44,8 +44,8 @@ MUTANTS = [
      "for (int d = 0; d < 3; ++d) vi[d] -= corr[d];", "angular or omega or two_particle"),
     ("inertia tensor without the |rho|^2 term", "I[a][b] += mi * ((a == b ? q2 : 0.0) - q[a] * q[b]);",
      "I[a][b] += mi * (0.0 - q[a] * q[b]);", "angular or omega or two_particle"),
-    ("positions not taken about the centre of mass", "= p->a * (rho[3 * (int64_t)(j - off[c]) + d] - mean[d]);",
-     "= p->a * (rho[3 * (int64_t)(j - off[c]) + d] - 0.0 * mean[d]);", "angular or omega or two_particle"),
+    ("positions not taken about the centre of mass", "= p->a * (rc[3 * (int64_t)(j - off[c]) + d] - mean[d]);",
+     "= p->a * (rc[3 * (int64_t)(j - off[c]) + d] - 0.0 * mean[d]);", "angular or omega or two_particle"),
     ("two-particle omega off by two", "w[d] = (dL[d] - along * q[d]) / (p->mass * rr);",
      "w[d] = (dL[d] - along * q[d]) / (2.0 * p->mass * rr);", "angular or omega or two_particle"),
     ("cell mass counts particles", "      M += mi;\n", "      M += 1.0;\n", "mass"),
@@ -66,6 +66,10 @@ MUTANTS = [
      "double Mv = (floor(p->ppc) - (double)nc) * m;", "virtual"),
     ("virtual momentum on the axis stream", "draw(p, (uint64_t)t, (uint64_t)c, ORC_TAG_WALL, w);",
      "draw(p, (uint64_t)t, (uint64_t)c, ORC_TAG_AXIS, w);", "virtual"),
+    ("presort not stable", "for (int64_t i = 0; i < n; ++i) order[start[key[i]]++] = i;",
+     "for (int64_t i = n - 1; i >= 0; --i) order[start[key[i]]++] = i;", "presort"),
+    ("presort on the shifted grid", "const double s0[3] = {0.0, 0.0, 0.0};",
+     "const double s0[3] = {0.25, 0.0, 0.0};", "presort"),
     ("cofactor indices swapped", "cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a2][b1];",
      "cof[a][b] = I[a1][b1] * I[a2][b2] - I[a1][b2] * I[a1][b2];", "angular or omega or two_particle"),
 ]

@@ -223,3 +223,41 @@ def test_relaxes_to_maxwell_boltzmann(orc):
     for d in range(3):
         assert abs(stats.kurtosis(st.v[:, d], fisher=False) - 3.0) < 0.07
     assert stats.kstest(comps, "norm").pvalue > 0.01
+
+
+def test_presort_is_a_stable_sort_by_unshifted_cell(orc):
+    """R25: storage after orc_presort equals numpy's stable argsort of the brute-force cells
+    floor(r / a) mod L (no shift), for a periodic box with a = 0.5 and a walled box, whose
+    unshifted layer is floor(z / a) + 1; ids and masses move with their particles and the
+    state by id is unchanged."""
+    for L, a, walls in (((5, 4, 3), 0.5, 0), ((4, 3, 5), 1.0, 1)):
+        p = orc.make_params(L, a=a, walls_z=walls)
+        n = 7 * int(np.prod(L))
+        r, v = inputs.uniform_gaussian_state(L, n, 17, a=a)
+        m = np.random.default_rng(3).uniform(0.5, 2.0, n)
+        st = orc.State(r, v, m=m)
+        orc.presort(p, st)
+        c = np.floor(r / a).astype(np.int64)
+        if walls:
+            c[:, 2] += 1
+        else:
+            c[:, 2] %= L[2]
+        c[:, 0] %= L[0]
+        c[:, 1] %= L[1]
+        lz = L[2] + (1 if walls else 0)
+        key = c[:, 0] + L[0] * (c[:, 1] + L[1] * c[:, 2])
+        assert key.max() < L[0] * L[1] * lz
+        order = np.argsort(key, kind="stable")
+        assert np.array_equal(st.id, order)
+        assert np.array_equal(st.r, r[order]) and np.array_equal(st.v, v[order])
+        assert np.array_equal(st.m, m[order])
+        rb, vb = st.by_id()
+        assert np.array_equal(rb, r) and np.array_equal(vb, v)
+        # a step from the sorted storage: the same physics (sums in another order)
+        st0 = orc.State(r, v, m=m)
+        orc.step(p, st0)
+        orc.step(p, st)
+        r0, v0 = st0.by_id()
+        r1, v1 = st.by_id()
+        assert np.array_equal(r0, r1)
+        assert np.abs(v0 - v1).max() < 1e-13

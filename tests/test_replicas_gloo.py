@@ -39,7 +39,7 @@ def _rank_main(rank, world, port, out):
 def test_two_rank_throughput_and_seeds():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_rank_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
@@ -71,7 +71,7 @@ def _leaving_main(rank, world, port, out):
 def test_rank_that_leaves_ends_the_next_collective_with_an_error():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_leaving_main, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
