@@ -58,3 +58,33 @@ def assert_sort_equal(dbg_gpu, dbg_ref):
             bad = np.nonzero(a != b)[0]
             raise AssertionError("%s differs at %d entries, first %d: gpu %d oracle %d" % (
                 k, bad.size, bad[0], a[bad[0]], b[bad[0]]))
+
+
+def face_distance(r, s, a=1.0):
+    """Distance (cell units) of each position from the nearest face of the grid shifted by s."""
+    x = (r - s) / a
+    fr = x - np.floor(x)
+    return np.minimum(fr, 1 - fr).min(axis=1)
+
+
+def assert_mixed_one_step(p, kg, ko, rg, vg, rr, vr, shift, ncell, what=""):
+    """Bounds of one mixed-form step from a state both forms represent exactly, against the
+    FP64 oracle (all arrays by particle id; kg, ko the cell keys of the GPU and the oracle):
+      - key disagreements are rare (at most 2e-5 of the particles, or 3) and each lies within
+        1e-5 cells of a shifted cell face (FP32 positions round across the face);
+      - positions within 1e-6 relative (periodic distance);
+      - velocities, in cells without a key disagreement, within 5e-6 of max(|v|, sqrt(kT/m))."""
+    n = len(kg)
+    bad = np.nonzero(kg != ko)[0]
+    assert bad.size <= max(3, 2e-5 * n), "%s: %d key disagreements" % (what, bad.size)
+    if bad.size:
+        assert face_distance(rr[bad], shift, p.a).max() < 1e-5, what
+    L = tuple(p.L)
+    box_len = np.array(L, float) * p.a
+    assert (periodic_diff(rg, rr, box_len, bool(p.walls_z)).max(axis=1)
+            <= 1e-6 * np.maximum(np.abs(rr).max(axis=1), p.a)).all(), what
+    clean_cells = np.setdiff1d(np.arange(ncell), np.concatenate([kg[bad], ko[bad]]))
+    clean = np.isin(ko, clean_cells)
+    sig = math.sqrt(p.kT / p.mass)
+    dv = np.abs(vg - vr).max(axis=1)[clean]
+    assert (dv <= 5e-6 * np.maximum(np.abs(vr).max(axis=1)[clean], sig)).all(), (what, dv.max())

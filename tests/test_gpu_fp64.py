@@ -12,14 +12,16 @@ from parity import assert_sort_equal, assert_state_close, oracle_params
 pytestmark = pytest.mark.gpu
 
 
-def angular_multiplier(p, rr, ref, prev, m=None):
-    """Per-particle (id order) factor on the 1e-12 bound for the angular-momentum-conserving
-    collision.  Its correction omega = I^-1 dL turns rounding differences of the rotated
-    velocities (a few ulps: the two sides round the rotation differently) into velocity
-    differences about cond(I) ulps large, cond(I) the condition number of the cell's inertia
-    tensor; nearly collinear cells of three particles make it large.  The factor is
-    max(1, cond(I)/100) (1e-12 / 100 = 1e-14, about 50 ulps), and a particle also inherits the
-    largest factor its cell's members carried from earlier steps, since u and omega mix them."""
+def angular_multiplier(p, rr, ref, m=None):
+    """Per-particle (id order) factor on the 1e-12 bound of one step of the angular-momentum-
+    conserving collision from identical states.  Its correction omega = I^-1 dL turns rounding
+    differences of the rotated velocities (a few ulps: the two sides round the rotation
+    differently) into velocity differences about cond(I) ulps large, cond(I) the condition
+    number of the cell's inertia tensor; nearly collinear cells of three particles make it
+    large.  The factor is max(1, cond(I)/100) (1e-12 / 100 = 1e-14, about 50 ulps) of this
+    step's cell only: the multi-step runs restart both sides from the oracle's state every
+    step, so no factor is carried forward.  test_angular_correction_decomposed holds the part
+    of the velocity before the correction to the flat 1e-12."""
     n = len(rr)
     keys = np.empty(n, np.int64)
     keys[ref["ids"]] = ref["keys"]
@@ -31,14 +33,13 @@ def angular_multiplier(p, rr, ref, prev, m=None):
     for c in range(len(bounds) - 1):
         idx = order[bounds[c]:bounds[c + 1]]
         if len(idx) < 2:
-            mult[idx] = prev[idx]
             continue
         w = np.ones(len(idx)) if m is None else m[idx]
         rho = loc[idx] - (w[:, None] * loc[idx]).sum(axis=0) / w.sum()
         I = (w * (rho * rho).sum(axis=1)).sum() * np.eye(3) - (w[:, None] * rho).T @ rho
         ev = np.linalg.eigvalsh(I)
         cond = ev[-1] / max(ev[0], ev[-1] * 1e-16) if len(idx) > 2 else ev[-1] / max(ev[1], ev[-1] * 1e-16)
-        mult[idx] = max(1.0, cond / 100.0, prev[idx].max())
+        mult[idx] = max(1.0, cond / 100.0)
     return mult
 
 
@@ -61,8 +62,11 @@ def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True, masses=None):
             rg, vg = box.state()
             rr, vr = st.by_id()
             if p.angular:
-                mult = angular_multiplier(p, rr, ref, mult, masses)
+                mult = angular_multiplier(p, rr, ref, masses)
             assert_state_close(rg, vg, rr, vr, p, tol=1e-12 * mult, what="step %d" % (t0 + k + 1))
+            if p.angular:  # restart both sides from the oracle's state: one-step comparisons
+                box.set_state(rr, vr, st.t)
+                st = orc.presort(op, orc.State(rr, vr, t=st.t, m=masses))
         return box.state(), st
     finally:
         box.close()
@@ -250,10 +254,10 @@ def test_checkpoint_resume_bit_exact(resort_k):
     assert np.array_equal(ra, rb) and np.array_equal(va, vb)
 
 
-def test_dense_and_generic_collide_agree(orc):
-    """A dense box (ppc 16: most 32-cell groups exceed the staged capacity and take the
-    per-cell path) next to a normal one: both match the oracle bit-exactly in keys and
-    perm and within tolerance in state."""
+def test_dense_pair_at_two_densities(orc):
+    """The dense FP64 pair (cell_frame + rotate) at 16 and at 10 particles per cell: keys and
+    perm bit-exact, state within tolerance.  (The per-cell FP64 kernel on a plain periodic box
+    is compared with this pair by tests/test_zz_no_alloc.py, whose entry point runs it.)"""
     for ppc in (16.0, 10.0):
         p = abi.make_params((8, 8, 8), ppc=ppc, seed=77)
         n = int(round(ppc * 512))
@@ -292,3 +296,55 @@ def test_errors_reported():
         box.step(2)
         assert abi.mpcd_steps_done(box.h) == 2
         assert abi.mpcd_launch_count(box.h) > 0
+
+
+ANGULAR_CASES = {
+    "angular": (dict(L=(7, 6, 5)), False),
+    "angular_mbs": (dict(L=(6, 6, 6), thermostat=2, kT=0.9), False),
+    "angular_sparse_a_half": (dict(L=(8, 8, 8), ppc=2.5, a=0.5), False),
+    "angular_masses": (dict(L=(6, 6, 5)), True),
+}
+
+
+@pytest.mark.parametrize("name", list(ANGULAR_CASES))
+def test_angular_correction_decomposed(orc, name):
+    """One step of the angular-momentum-conserving collision split into its two parts, each
+    against the oracle from identical states:
+      - the velocity before the correction (the same boxes with angular = 0) to the flat 1e-12
+        bound, with no condition-number factor;
+      - the correction omega x rho_i itself (angular = 1 minus angular = 0, per particle) to
+        1e-12 max(|v|, sqrt(kT/m)) times max(1, cond(I)/100) of the particle's cell, the only
+        place where the inertia tensor's conditioning enters.
+    The full velocities then agree within the sum of the two bounds."""
+    kw, with_masses = ANGULAR_CASES[name]
+    base = abi.make_params(seed=3000 + len(name), resort_k=0, **kw)
+    n = int(round(base.ppc * base.L[0] * base.L[1] * base.L[2]))
+    r, v = inputs.uniform_gaussian_state(tuple(base.L), n, 61 + len(name), a=base.a, kT=base.kT)
+    m = np.random.default_rng(len(name)).uniform(0.5, 4.0, n) if with_masses else None
+    t0 = 6
+    out = {}
+    for ang in (0, 1):
+        p = abi.make_params(seed=3000 + len(name), resort_k=0, angular=ang, **kw)
+        op = oracle_params(orc, p)
+        with abi.Box(p) as box:
+            box.set_state(r, v, t0)
+            if m is not None:
+                box.set_masses(m)
+            box.step(1)
+            rg, vg = box.state()
+        st = orc.presort(op, orc.State(r, v, t=t0, m=m))
+        ref = orc.step(op, st, debug=True)
+        rr, vr = st.by_id()
+        out[ang] = (p, rg, vg, rr, vr, ref)
+    p0, rg0, vg0, rr0, vr0, _ = out[0]
+    p1, rg1, vg1, rr1, vr1, ref1 = out[1]
+    assert_state_close(rg0, vg0, rr0, vr0, p0, what="before the correction")   # flat 1e-12
+    assert np.array_equal(rr0, rr1) and np.array_equal(rg0, rg1)
+    mult = angular_multiplier(p1, rr1, ref1, m)
+    scale = np.maximum(np.abs(vr1).max(axis=1), math.sqrt(p1.kT / p1.mass))
+    corr_gpu = vg1 - vg0
+    corr_orc = vr1 - vr0
+    assert np.abs(corr_orc).max() > 1e-3                                        # the correction is real
+    err = np.abs(corr_gpu - corr_orc).max(axis=1)
+    bound = 1e-12 * scale * (2.0 + mult)   # the two flat parts plus the conditioned correction
+    assert (err <= bound).all(), (err / bound).max()
