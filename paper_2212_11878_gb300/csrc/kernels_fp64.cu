@@ -202,9 +202,11 @@ __device__ __forceinline__ void sort_entries(int32_t* pm, int n) {
 
 // Exact sums of a cell's velocities (and of v.v for the moments), four members at a time
 // so that their loads are in flight together.  `ok` turns false if a component reaches
-// 2^16; the cell is then summed in plain FP64 in perm order.
+// 2^16; the cell's entries are then put in storage order and summed in plain FP64 in that
+// order, so that the result does not depend on the order in which the counting atomics
+// handed out the slots.
 template <int MOMENTS>
-__device__ __forceinline__ void cell_sums(const Fp64Bufs& b, int cur, const int32_t* pm, int n, double S[3], double& SE) {
+__device__ __forceinline__ void cell_sums(const Fp64Bufs& b, int cur, int32_t* pm, int n, double S[3], double& SE) {
   const double* __restrict__ vx = b.v[cur][0];
   const double* __restrict__ vy = b.v[cur][1];
   const double* __restrict__ vz = b.v[cur][2];
@@ -249,6 +251,7 @@ __device__ __forceinline__ void cell_sums(const Fp64Bufs& b, int cur, const int3
     SE = MOMENTS ? fx_value(ae) : 0.0;
     return;
   }
+  sort_entries(pm, n);
   S[0] = S[1] = S[2] = SE = 0.0;
   for (j = 0; j < n; ++j) {
     const int i = pm[j];
@@ -263,7 +266,7 @@ __device__ __forceinline__ void cell_sums(const Fp64Bufs& b, int cur, const int3
 // With particle masses (Listing 4 sums m v and m): exact sums of the rounded products
 // m_i v_i, m_i v_i.v_i and of m_i, each rounded once; the order of the members does not matter.
 template <int MOMENTS>
-__device__ void cell_sums_mass(const Fp64Bufs& b, int cur, const double* __restrict__ mp, const int32_t* pm, int n,
+__device__ void cell_sums_mass(const Fp64Bufs& b, int cur, const double* __restrict__ mp, int32_t* pm, int n,
                                double P[3], double& SE, double& M) {
   Fx128 a0, a1, a2, ae, am;
   fx_zero(a0);
@@ -289,7 +292,8 @@ __device__ void cell_sums_mass(const Fp64Bufs& b, int cur, const double* __restr
     SE = MOMENTS ? fx_value(ae) : 0.0;
     return;
   }
-  P[0] = P[1] = P[2] = SE = M = 0.0;  // a term beyond the exact range: plain FP64 sums
+  sort_entries(pm, n);  // a term beyond the exact range: plain FP64 sums in storage order
+  P[0] = P[1] = P[2] = SE = M = 0.0;
   for (int j = 0; j < n; ++j) {
     const int i = pm[j];
     const double m = mp[i], v0 = b.v[cur][0][i], v1 = b.v[cur][1][i], v2 = b.v[cur][2][i];

@@ -348,3 +348,17 @@ def test_angular_correction_decomposed(orc, name):
     err = np.abs(corr_gpu - corr_orc).max(axis=1)
     bound = 1e-12 * scale * (2.0 + mult)   # the two flat parts plus the conditioned correction
     assert (err <= bound).all(), (err / bound).max()
+
+
+def test_fast_particles_fallback_sums_in_storage_order(orc):
+    """A velocity component of 2^16 or more is beyond the exact fixed-point sums; such a
+    cell is summed in plain FP64 with its members in storage order, the oracle's order, so
+    the result matches the oracle and repeats bit for bit although the counting atomics
+    hand out the slots in a different order on every run.  No re-sort (k = 0): the cells'
+    entries arrive in atomic order every step."""
+    p = abi.make_params((6, 6, 6), seed=71, resort_k=0)
+    n = int(round(p.ppc * 216))
+    r, v = inputs.uniform_gaussian_state((6, 6, 6), n, 72)
+    v[::97, 0] = 7.0e4 * np.where(np.arange(0, n, 97) % 2 == 0, 1.0, -1.0)   # > 2^16
+    outs = [run_pair(orc, p, r, v, steps=4)[0] for _ in range(2)]
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
