@@ -47,12 +47,16 @@ FP64_BYTES = {
     "scatter": (12.0, 4.0),
     "collide": (4.0 + 24.0, 8.0 + 128.0),   # cell_frame: v through perm, offsets, 16-double frame
     "rotate": (24.0 + 24.0 + 4.0 + 8.0, 0.0),  # v read + written, key, frame gather (amortised)
+    # the rotation of step t fused with the streaming of step t + 1: r, v read and written,
+    # key of step t read and of step t + 1 written, rank written, frame gather (amortised)
+    "rotate_stream": (48.0 + 48.0 + 4.0 + 4.0 + 4.0 + 8.0, 4.0),
     "end_step": (0.0, 0.0),
 }
 FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # rotate on re-sort steps also moves r and the ids
+FP64_RESORT_EXTRA_FUSED = 4.0 + 8.0     # the fused pass moves r anyway; + the ids and the destination
 # FP64 instructions (DFMA, DADD, DMUL) per launch, as (per particle, per cell): the FP64 form
 # is bound by GB300's FP64 pipe (2 instructions per clock per SM), not by HBM.
-FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 71.0), "rotate": (9.0, 0.0)}
+FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 71.0), "rotate": (9.0, 0.0), "rotate_stream": (15.0, 0.0)}
 SMS, FP64_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_GOPS = SMS * FP64_PER_CLK * SM_MAX_MHZ / 1e3   # 629.3 G FP64 instructions/s
 ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step
@@ -302,23 +306,28 @@ def timed_steps(abi, torch, dist, box, stream, steps, world, sampler=None):
 
 def kernel_table(p, mixed, n, C, ktimes, steps):
     """Per-kernel device time per step, share, algorithmic HBM bytes and GB/s, and for the
-    FP64 kernels their FP64 instruction rate."""
+    FP64 kernels their FP64 instruction rate.  Rates are per launch of the kernel (its bytes
+    or instructions over its average launch time); the FP64 dense pair launches stream_bin and
+    rotate once per mpcd_step call and the fused rotate_stream on every other step."""
     kernels = {}
     total_kernel_ms = sum(v[0] for v in ktimes.values()) or 1.0
     model = MIXED_BYTES if mixed else FP64_BYTES
+    once_per_call = ("stream_bin", "rotate", "rotate_stream") if not mixed else ()
     for name, (kms, cnt) in ktimes.items():
         per_p, per_c = model.get(name, (0.0, 0.0))
-        bytes_step = per_p * n + per_c * C
-        if name == "rotate" and p.resort_k > 0 and not mixed:
-            bytes_step += FP64_RESORT_EXTRA * n / p.resort_k
-        ms_step = kms / steps
-        k = {"ms_per_step": ms_step, "launches": cnt, "share": kms / total_kernel_ms,
-             "algo_bytes_per_step": bytes_step, "gbs": bytes_step / (ms_step / 1e3) / 1e9 if kms > 0 else None,
-             "launches_per_step": cnt / steps}
+        invocations = cnt if name in once_per_call else steps   # slot invocations in the timed region
+        bytes_inv = per_p * n + per_c * C
+        if name in ("rotate", "rotate_stream") and p.resort_k > 0 and not mixed:
+            extra = FP64_RESORT_EXTRA if name == "rotate" else FP64_RESORT_EXTRA_FUSED
+            bytes_inv += extra * n / p.resort_k
+        ms_inv = kms / max(invocations, 1)
+        k = {"ms_per_step": kms / steps, "ms_per_invocation": ms_inv, "invocations": invocations, "launches": cnt,
+             "share": kms / total_kernel_ms, "algo_bytes_per_invocation": bytes_inv,
+             "gbs": bytes_inv / (ms_inv / 1e3) / 1e9 if kms > 0 else None}
         if not mixed and name in FP64_OPS:
             ops = FP64_OPS[name][0] * n + FP64_OPS[name][1] * C
-            k["fp64_ops_per_step"] = ops
-            k["fp64_gops"] = ops / (ms_step / 1e3) / 1e9 if kms > 0 else None
+            k["fp64_ops_per_invocation"] = ops
+            k["fp64_gops"] = ops / (ms_inv / 1e3) / 1e9 if kms > 0 else None
         kernels[name] = k
     return kernels
 
@@ -331,7 +340,7 @@ def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True, fp64_probe
     if mixed:
         dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
         d = kernels[dom]
-        per_launch = d["algo_bytes_per_step"] / max(d["launches_per_step"], 1.0)
+        per_launch = d["algo_bytes_per_invocation"]
         tr = NCU_TRAFFIC.get(("mixed", dom)) if captured else None
         return {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": d["gbs"] / hbm_peak, "traffic": tr[0] * n if tr else None,
@@ -345,7 +354,7 @@ def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True, fp64_probe
             "unit": "G FP64 instructions/s", "frac": d["fp64_gops"] / FP64_PEAK_GOPS,
             "traffic": tr[0] * n if tr else None, "traffic_source": tr[1] if tr else None,
             "peak_source": "derived: %d SMs x %d FP64 instructions/clock x %.0f MHz" % (SMS, FP64_PER_CLK, SM_MAX_MHZ),
-            "algo_fp64_ops_per_launch": d["fp64_ops_per_step"] / max(d["launches_per_step"], 1.0),
+            "algo_fp64_ops_per_launch": d["fp64_ops_per_invocation"],
             "peak_measured": fp64_probe, "frac_of_measured": d["fp64_gops"] / fp64_probe if fp64_probe else None,
             "peak_measured_source": "mpcd_measure_fp64_rate: chains of independent DFMAs on every SM, this run",
             "hbm_gbs": d["gbs"], "hbm_frac": d["gbs"] / hbm_peak}

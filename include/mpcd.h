@@ -191,17 +191,22 @@ typedef struct {
                         /*   per box at most 24 ppc and 192 - ceil(ppc + 4 sqrt(ppc))     */
   int32_t warps;        /* mixed form: warps per collide block (2 or 4) */
   int32_t resort_k;     /* FP64 form: physical re-sort period in steps (0: never) */
-  int32_t reserved;     /* must be 0 */
+  int32_t fuse;         /* FP64 periodic boxes without thermostat: 1 applies each step's      */
+                        /*   rotation in the same pass as the next step's streaming and       */
+                        /*   binning (one pass over the state instead of two; the last step   */
+                        /*   of every mpcd_step call still ends with its rotation), 0 runs    */
+                        /*   them as separate passes.  Identical results either way.         */
 } mpcd_tuning;
 
 int mpcd_get_tuning(const mpcd_t* h, mpcd_tuning* out);
-/* Errors: MPCD_ERR_ARG for out-of-range values. */
+/* Errors: MPCD_ERR_ARG for out-of-range values (fuse must be 0 or 1). */
 int mpcd_set_tuning(mpcd_t* h, const mpcd_tuning* t);
 
 /* Autotuner: times each candidate tuning on the handle's own box(es) for trial_steps steps
  * (CUDA events on the handle's stream), keeps the fastest and restores the state, so the
  * simulation is unchanged.  Candidates: group_target in {128, 144, 160, 168, 176} x warps
- * in {2, 4} for the mixed form; resort_k in {1, 2, 5, 10, 20, 50} for the FP64 form.
+ * in {2, 4} for the mixed form; resort_k in {1, 2, 5, 10, 20, 50} x fuse in {0, 1} for the
+ * FP64 form.
  * *best receives the choice and *best_ms its time per step (either may be NULL). */
 int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* best_ms);
 

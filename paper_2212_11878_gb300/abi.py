@@ -66,10 +66,10 @@ class Tuning(ctypes.Structure):
     """Mirror of ``mpcd_tuning``."""
 
     _fields_ = [("group_target", ctypes.c_int32), ("warps", ctypes.c_int32), ("resort_k", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("fuse", ctypes.c_int32)]
 
     def as_dict(self):
-        return {"group_target": self.group_target, "warps": self.warps, "resort_k": self.resort_k}
+        return {"group_target": self.group_target, "warps": self.warps, "resort_k": self.resort_k, "fuse": self.fuse}
 
 
 def make_params(L, a=1.0, ppc=10.0, dt=0.1, alpha_deg=130.0, kT=1.0, mass=1.0, seed=20221211,
@@ -349,8 +349,10 @@ def mpcd_get_tuning(h) -> Tuning:
     return t
 
 
-def mpcd_set_tuning(h, group_target=None, warps=None, resort_k=None):
+def mpcd_set_tuning(h, group_target=None, warps=None, resort_k=None, fuse=None):
     t = mpcd_get_tuning(h)
+    if fuse is not None:
+        t.fuse = int(fuse)
     if group_target is not None:
         t.group_target = int(group_target)
     if warps is not None:

@@ -21,10 +21,30 @@ using namespace mpcd;
 
 namespace {
 
-enum KernelSlot { kSlotZero = 0, kSlotStreamBin, kSlotScan, kSlotScatter, kSlotCollide, kSlotRotate, kSlotEndStep, kNumSlots };
-const char* kSlotNames[kNumSlots] = {"zero_counts", "stream_bin", "scan", "scatter", "collide", "rotate", "end_step"};
-// kernels launched per slot per step (collide: two for periodic boxes without thermostat)
-const int kSlotLaunchesBase[kNumSlots] = {1, 1, 3, 1, 1, 0, 1};
+enum KernelSlot {
+  kSlotZero = 0,
+  kSlotStreamBin,
+  kSlotScan,
+  kSlotScatter,
+  kSlotCollide,
+  kSlotRotate,
+  kSlotEndStep,
+  kSlotRotateStream,
+  kNumSlots
+};
+const char* kSlotNames[kNumSlots] = {"zero_counts", "stream_bin", "scan",     "scatter",
+                                     "collide",     "rotate",     "end_step", "rotate_stream"};
+// kernels launched per invocation of each slot (the rotation slots only for the dense pair)
+const int kSlotLaunchesBase[kNumSlots] = {1, 1, 3, 1, 1, 0, 1, 0};
+
+// The launch sequence of one step.  Full: every kernel of a step (mixed form, and FP64 boxes
+// whose collision is one per-cell kernel).  The FP64 dense pair splits its steps so that the
+// rotation of step t runs fused with the streaming of step t + 1: an mpcd_step(n) call is a
+// Head (step 1 up to its frames), n - 1 Bodies (the rotation of the previous step fused with
+// the streaming of this one, then this step up to its frames) and a Tail (the last rotation),
+// so that no call leaves a step half done.  With the tuning's fuse = 0 every step of the
+// dense pair is a Step: Full, then its own rotation.
+enum Piece { kPieceFull = 0, kPieceBody = 1, kPieceTail = 2, kPieceStep = 3 };  // Step: Full + Tail
 
 std::mutex g_err_mu;
 std::string g_create_err;
@@ -80,8 +100,10 @@ struct mpcd_s {
   bool record_moments = false;
   bool moments_valid = false;
 
-  cudaGraphExec_t graph = nullptr;     // FP64: one step
-  cudaGraphExec_t graph_par[2] = {};   // mixed: one step starting from buffer set 0 / 1
+  cudaGraphExec_t graph = nullptr;       // FP64: one step (the dense pair: up to its frames)
+  cudaGraphExec_t graph_body = nullptr;  // FP64 dense pair: the fused body of a step
+  cudaGraphExec_t graph_step = nullptr;  // FP64 dense pair, unfused: a step with its rotation
+  cudaGraphExec_t graph_par[2] = {};     // mixed: one step starting from buffer set 0 / 1
   bool graph_moments = false;
 
   bool timing = false;
@@ -255,9 +277,11 @@ int run_slot(mpcd_t* h, int slot, F&& launch) {
   return MPCD_OK;
 }
 
-// Enqueue one full step on h->stream.  `par` is the mixed form's buffer set at the start of
-// the step (the FP64 kernels read theirs from the control block).
-int enqueue_step(mpcd_t* h, bool moments, int par = 0) {
+bool dense_fp64(const mpcd_t* h) { return h->precision == MPCD_FP64 && fp64_dense_collide(h->geom, h->scr); }
+
+// Enqueue one piece of a step on h->stream.  `par` is the mixed form's buffer set at the start
+// of the step (the FP64 kernels read theirs from the control block).
+int enqueue_piece(mpcd_t* h, int piece, bool moments, int par = 0) {
   const Geom& g = h->geom;
   int rc;
   if (h->precision == MPCD_MIXED) {
@@ -282,13 +306,27 @@ int enqueue_step(mpcd_t* h, bool moments, int par = 0) {
     return MPCD_OK;
   }
   Scratch s = h->scr;
-  if ((rc = run_slot(h, kSlotZero, [&] { launch_zero_i32(s.count, g.ncell, h->stream); }))) return rc;
-  if ((rc = run_slot(h, kSlotStreamBin, [&] { launch_stream_bin_fp64(g, h->f64, s, h->ctl, h->stream); }))) return rc;
+  if (piece == kPieceTail)
+    return run_slot(h, kSlotRotate, [&] { launch_rotate_fp64(g, h->f64, s, h->ctl, h->stream, h->f64m); });
+  if (piece == kPieceStep) {
+    if ((rc = enqueue_piece(h, kPieceFull, moments, par))) return rc;
+    return enqueue_piece(h, kPieceTail, moments, par);
+  }
+  if ((rc = run_slot(h, kSlotZero, [&] {
+         launch_zero_i32(s.count, g.ncell, h->stream);
+         launch_zero_i32(s.cursor, g.ncell, h->stream);
+       })))
+    return rc;
+  if (piece == kPieceBody) {
+    if ((rc = run_slot(h, kSlotRotateStream,
+                       [&] { launch_rotate_stream_fp64(g, h->f64, s, h->ctl, h->stream, h->f64m); })))
+      return rc;
+  } else {
+    if ((rc = run_slot(h, kSlotStreamBin, [&] { launch_stream_bin_fp64(g, h->f64, s, h->ctl, h->stream); }))) return rc;
+  }
   if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(s.count, s.offset, s.partial, g.ncell, h->stream); }))) return rc;
-  if ((rc = run_slot(h, kSlotScatter, [&] { launch_scatter(g, s, h->stream); }))) return rc;
+  if ((rc = run_slot(h, kSlotScatter, [&] { launch_scatter(g, s, h->ctl, h->stream); }))) return rc;
   if ((rc = run_slot(h, kSlotCollide, [&] { launch_collide_fp64(g, h->f64, s, h->ctl, moments, h->stream, h->f64m); }))) return rc;
-  if (fp64_dense_collide(g, s))
-    if ((rc = run_slot(h, kSlotRotate, [&] { launch_rotate_fp64(g, h->f64, s, h->ctl, h->stream, h->f64m); }))) return rc;
   if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step(g, h->ctl, h->stream); }))) return rc;
   return MPCD_OK;
 }
@@ -306,27 +344,37 @@ int enqueue_bin_mixed(mpcd_t* h) {
   return MPCD_OK;
 }
 
-int launches_per_step(const mpcd_t* h) {
+int piece_launches(const mpcd_t* h, int piece) {
+  if (piece == kPieceTail) return h->per_step[kSlotRotate];
+  if (piece == kPieceStep) return piece_launches(h, kPieceFull) + piece_launches(h, kPieceTail);
   int k = 0;
-  for (int s = 0; s < kNumSlots; ++s) k += h->per_step[s];
+  for (int s = 0; s < kNumSlots; ++s) {
+    if (s == kSlotRotate || (s == kSlotRotateStream && piece != kPieceBody) || (s == kSlotStreamBin && piece == kPieceBody))
+      continue;
+    k += h->per_step[s];
+  }
   return k;
 }
 
 void drop_graph(mpcd_t* h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
+  if (h->graph_body) cudaGraphExecDestroy(h->graph_body);
+  h->graph_body = nullptr;
+  if (h->graph_step) cudaGraphExecDestroy(h->graph_step);
+  h->graph_step = nullptr;
   for (int k = 0; k < 2; ++k) {
     if (h->graph_par[k]) cudaGraphExecDestroy(h->graph_par[k]);
     h->graph_par[k] = nullptr;
   }
 }
 
-int capture_step(mpcd_t* h, int par, cudaGraphExec_t* out) {
+int capture_step(mpcd_t* h, int piece, int par, cudaGraphExec_t* out) {
   cudaGraph_t graph = nullptr;
   MPCD_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   const bool saved = h->timing;
   h->timing = false;
-  int rc = enqueue_step(h, h->record_moments, par);
+  int rc = enqueue_piece(h, piece, h->record_moments, par);
   h->timing = saved;
   cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
   if (rc) {
@@ -345,9 +393,11 @@ int build_graph(mpcd_t* h) {
   int rc;
   if (h->precision == MPCD_MIXED) {
     for (int k = 0; k < 2; ++k)
-      if ((rc = capture_step(h, k, &h->graph_par[k]))) return rc;
+      if ((rc = capture_step(h, kPieceFull, k, &h->graph_par[k]))) return rc;
   } else {
-    if ((rc = capture_step(h, 0, &h->graph))) return rc;
+    if ((rc = capture_step(h, kPieceFull, 0, &h->graph))) return rc;
+    if (dense_fp64(h) && (rc = capture_step(h, kPieceBody, 0, &h->graph_body))) return rc;
+    if (dense_fp64(h) && (rc = capture_step(h, kPieceStep, 0, &h->graph_step))) return rc;
   }
   h->graph_moments = h->record_moments;
   return MPCD_OK;
@@ -458,6 +508,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->tune.group_target = 168;
   h->tune.warps = 4;
   h->tune.resort_k = p[0].resort_k;
+  h->tune.fuse = 1;
   // per-box geometry; the handle's geom describes the whole concatenation for the kernels
   // that run over all cells or particles (zeroing, scan, sort)
   int64_t ctot = 0, ntot = 0;
@@ -481,7 +532,8 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->geom.n = ntot;
   h->geom.ncell = ctot;
   for (int k = 0; k < kNumSlots; ++k) h->per_step[k] = kSlotLaunchesBase[k];
-  if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotRotate] = 1;  // cell_frame + rotate
+  h->per_step[kSlotZero] = 2;  // counts and the scatter's cursors
+  if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotRotate] = h->per_step[kSlotRotateStream] = 1;
   h->n = ntot;
   h->ncell = ctot;
   auto bail = [&](int code) {
@@ -501,7 +553,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     h->per_step[kSlotZero] = 2;
     h->per_step[kSlotScatter] = 2;  // scatter + group bounds
     h->per_step[kSlotCollide] = 1;
-    h->per_step[kSlotRotate] = 0;
+    h->per_step[kSlotRotate] = h->per_step[kSlotRotateStream] = 0;
     for (int k = 0; k < 2; ++k) {
       if ((rc = dalloc(h, &h->mix.rec[k], n))) return bail(rc);
       if ((rc = dalloc(h, &h->mscr.key[k], n))) return bail(rc);
@@ -541,14 +593,17 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
       if ((rc = dalloc(h, &h->f64.id[k], n))) return bail(rc);
     }
     if ((rc = dalloc(h, &h->scr.key, n))) return bail(rc);
+    h->scr.key2 = h->scr.key;
     if ((rc = dalloc(h, &h->scr.rank, n))) return bail(rc);
     if ((rc = dalloc(h, &h->scr.perm, n))) return bail(rc);
     if ((rc = dalloc(h, &h->scr.count, C))) return bail(rc);
+    if ((rc = dalloc(h, &h->scr.cursor, C))) return bail(rc);
     if ((rc = dalloc(h, &h->scr.offset, C + 1))) return bail(rc);
     if ((rc = dalloc(h, &h->scr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
     if (!h->geom.walls && !h->geom.thermostat) {
       if ((rc = dalloc(h, &h->scr.frame, 16 * C))) return bail(rc);
       if ((rc = dalloc(h, &h->scr.inv, n))) return bail(rc);
+      if ((rc = dalloc(h, &h->scr.key2, n))) return bail(rc);  // keys of odd steps (fused pass)
     }
   }
   if ((rc = dalloc(h, &h->ctl, 1))) return bail(rc);
@@ -622,23 +677,32 @@ int mpcd_step(mpcd_t* h, int64_t nsteps) {
   if (rc) return rc;
   if (nsteps < 0) return fail(h, MPCD_ERR_ARG, "nsteps must be >= 0");
   const bool mixed = h->precision == MPCD_MIXED;
+  const bool dense = dense_fp64(h);
+  const bool fused = dense && h->tune.fuse;
   for (int64_t k = 0; k < nsteps; ++k) {
     if (mixed && !h->mixed_keys_valid)
       if ((rc = enqueue_bin_mixed(h))) return rc;
+    const int piece = !dense ? kPieceFull : !fused ? kPieceStep : (k > 0 ? kPieceBody : kPieceFull);
     if (h->timing) {
-      if ((rc = enqueue_step(h, h->record_moments, h->cur))) return rc;
+      if ((rc = enqueue_piece(h, piece, h->record_moments, h->cur))) return rc;
     } else {
       if ((mixed ? !h->graph_par[0] : !h->graph) || h->graph_moments != h->record_moments)
         if ((rc = build_graph(h))) return rc;
-      MPCD_TRY(h, cudaGraphLaunch(mixed ? h->graph_par[h->cur] : h->graph, h->stream));
+      cudaGraphExec_t ge = mixed ? h->graph_par[h->cur]
+                                 : (piece == kPieceBody ? h->graph_body : piece == kPieceStep ? h->graph_step : h->graph);
+      MPCD_TRY(h, cudaGraphLaunch(ge, h->stream));
     }
-    h->launches += launches_per_step(h);
+    h->launches += piece_launches(h, piece);
     h->t += 1;
     h->last_resorted = mixed || resort_at(h, h->t);
     if (h->last_resorted) h->cur ^= 1;
     h->perm_sorted = !mixed && (h->last_resorted || h->geom.walls || h->geom.thermostat || h->geom.angular);
     h->any_step = true;
     h->moments_valid = h->record_moments;
+  }
+  if (fused && nsteps > 0) {  // the last step's rotation
+    if ((rc = enqueue_piece(h, kPieceTail, h->record_moments))) return rc;
+    h->launches += piece_launches(h, kPieceTail);
   }
   return MPCD_OK;
 }
@@ -692,7 +756,7 @@ int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m) {
     h->f64m.m[0] = h->mass_buf[0];
     h->f64m.m[1] = h->mass_buf[1];
   }
-  h->per_step[kSlotRotate] = (!h->geom.walls && !h->geom.thermostat) ? 1 : 0;
+  h->per_step[kSlotRotate] = h->per_step[kSlotRotateStream] = (!h->geom.walls && !h->geom.thermostat) ? 1 : 0;
   drop_graph(h);  // the step graph holds the buffer pointers and the kernel choice
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   return MPCD_OK;
@@ -860,7 +924,8 @@ int mpcd_debug_sort(mpcd_t* h, int32_t* keys, int32_t* counts, int32_t* offsets,
     h->perm_sorted = true;
   }
   const size_t nb = sizeof(int32_t) * (size_t)h->n, cb = sizeof(int32_t) * (size_t)h->ncell;
-  if (keys) MPCD_TRY(h, cudaMemcpyAsync(keys, s.key, nb, cudaMemcpyDeviceToHost, h->stream));
+  const int32_t* keys_last = (!mixed && (h->t & 1)) ? s.key2 : s.key;  // keys of step h->t
+  if (keys) MPCD_TRY(h, cudaMemcpyAsync(keys, keys_last, nb, cudaMemcpyDeviceToHost, h->stream));
   if (counts) MPCD_TRY(h, cudaMemcpyAsync(counts, s.count, cb, cudaMemcpyDeviceToHost, h->stream));
   if (offsets) MPCD_TRY(h, cudaMemcpyAsync(offsets, s.offset, cb + sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   if (perm) MPCD_TRY(h, cudaMemcpyAsync(perm, s.perm, nb, cudaMemcpyDeviceToHost, h->stream));
@@ -940,9 +1005,10 @@ int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* bes
   std::vector<mpcd_tuning> cand;
   if (h->precision == MPCD_MIXED) {
     for (int w : {2, 4})
-      for (int tg : {128, 144, 160, 168, 176}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, 0});
+      for (int tg : {128, 144, 160, 168, 176}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, h->tune.fuse});
   } else {
-    for (int k : {1, 2, 5, 10, 20, 50}) cand.push_back(mpcd_tuning{h->tune.group_target, h->tune.warps, k, 0});
+    for (int f : {0, 1})
+      for (int k : {1, 2, 5, 10, 20, 50}) cand.push_back(mpcd_tuning{h->tune.group_target, h->tune.warps, k, f});
   }
   // keep the state: by-id FP64 copies are exact for both forms
   const int64_t t0 = h->t;
@@ -991,15 +1057,15 @@ int mpcd_get_tuning(const mpcd_t* h, mpcd_tuning* out) {
 int mpcd_set_tuning(mpcd_t* h, const mpcd_tuning* t) {
   int rc = guard(h);
   if (rc) return rc;
-  if (!t || t->reserved != 0 || t->group_target < 32 || t->group_target > 224 || (t->warps != 2 && t->warps != 4) ||
-      t->resort_k < 0)
-    return fail(h, MPCD_ERR_ARG, "tuning out of range (group_target 32..224, warps 2 or 4, resort_k >= 0)");
+  if (!t || (t->fuse != 0 && t->fuse != 1) || t->group_target < 32 || t->group_target > 224 ||
+      (t->warps != 2 && t->warps != 4) || t->resort_k < 0)
+    return fail(h, MPCD_ERR_ARG, "tuning out of range (group_target 32..224, warps 2 or 4, resort_k >= 0, fuse 0 or 1)");
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   const mpcd_tuning old = h->tune;
   h->tune = *t;
   if (h->precision == MPCD_MIXED) {
     if (old.group_target != t->group_target || old.warps != t->warps) return build_groups(h);
-  } else if (old.resort_k != t->resort_k) {
+  } else if (old.resort_k != t->resort_k || old.fuse != t->fuse) {
     // the re-sort schedule is part of the captured step and of the step-end kernel
     h->geom.resort_k = t->resort_k;
     drop_graph(h);
@@ -1124,6 +1190,7 @@ extern "C" int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n
   unsigned char* q = base + kNaCtlBytes;
   Scratch s{};
   s.key = reinterpret_cast<int32_t*>(q);
+  s.key2 = s.key;
   q += kNaPartBytes;
   s.rank = reinterpret_cast<int32_t*>(q);
   q += kNaPartBytes;
@@ -1146,7 +1213,7 @@ extern "C" int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n
   launch_zero_i32(s.count, g.ncell, st);
   launch_stream_bin_fp64(g, b, s, ctl, st);
   launch_scan(s.count, s.offset, s.partial, g.ncell, st);
-  launch_scatter(g, s, st);
+  launch_scatter(g, s, ctl, st);
   launch_collide_fp64_generic(g, b, s, ctl, false, st);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "mpcd_step_fp64_noalloc launch");

@@ -145,6 +145,103 @@ __device__ __forceinline__ void apply_frame(const double R[9], const double bvec
   v2 = a2;
 }
 
+// --------------------------------------------------- float-float rotation frame ----
+// GB300 issues about 60 times fewer FP64 than FP32 instructions per clock, so the dense pair
+// applies the frame v' = R v + b in float-float arithmetic (each value a pair of FP32 numbers
+// hi + lo): an FP32 product's rounding error is exact through an FMA, and Knuth's two-sum
+// gives a sum's error exactly, so the pair carries about 46 bits.  The split of a double and
+// the assembly of the result use integer instructions, and one exact DADD per component
+// joins the pair; the relative error of v' is below about 2^-44 (|v| + |b|) / max(|v'|, ...),
+// far inside the 1e-12 bound the FP64 form is held to.
+
+// x = hi + lo with hi the top 24 significand bits of x (truncated) and lo the remaining 29
+// rounded to 24: |x - hi - lo| <= 2^-48 |x| for 2^-74 <= |x| < 2^127.  Smaller magnitudes
+// give 0 (they lie far below the velocity scale); larger ones do not occur for finite states.
+__device__ __forceinline__ void ff_split(double x, float& hi, float& lo) {
+  const int h = __double2hiint(x);
+  const unsigned l = static_cast<unsigned>(__double2loint(x));
+  const int e = (h >> 20) & 0x7FF;
+  if (e < 949 || e > 1150) {
+    hi = e > 1150 ? __double2float_rn(x) : 0.0f;  // inf/NaN stay non-finite
+    lo = 0.0f;
+    return;
+  }
+  const unsigned sign = static_cast<unsigned>(h) & 0x80000000u;
+  hi = __uint_as_float(sign | (static_cast<unsigned>(e - 896) << 23) | ((static_cast<unsigned>(h) & 0xFFFFFu) << 3) |
+                       (l >> 29));
+  // the remaining 29 bits, worth (l mod 2^29) 2^(e - 1075); 2^(e - 1075) is a normal float for e >= 949
+  const float scale = __uint_as_float(static_cast<unsigned>(e - 948) << 23);
+  const float rest = __fmul_rn(__uint2float_rn(l & 0x1FFFFFFFu), scale);
+  lo = sign ? -rest : rest;
+}
+
+// A float as a double, from its bit fields (zero and subnormals give 0).
+__device__ __forceinline__ double ff_widen(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e == 0u) return 0.0;
+  return __hiloint2double(static_cast<int>((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)),
+                          static_cast<int>(b << 29));
+}
+
+// acc += a * x in float-float (a and x pairs): the product of the high parts exactly as
+// p + pe, the cross terms in FP32, p added to acc.hi by two-sum.  No contraction: every
+// operation is an explicit intrinsic.
+__device__ __forceinline__ void ff_madd(float ah, float al, float xh, float xl, float& sh, float& sl) {
+  const float p = __fmul_rn(ah, xh);
+  const float pe = __fmaf_rn(ah, xh, -p);
+  const float cross = __fmaf_rn(ah, xl, __fmul_rn(al, xh));
+  const float s2 = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s2, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s2, bb)), __fsub_rn(p, bb));
+  sh = s2;
+  sl = __fadd_rn(sl, __fadd_rn(err, __fadd_rn(pe, cross)));
+}
+
+// (sh, sl) -> double: renormalise by two-sum, then join the two halves with one exact DADD.
+__device__ __forceinline__ double ff_join(float sh, float sl) {
+  const float s = __fadd_rn(sh, sl);
+  const float bb = __fsub_rn(s, sh);
+  const float e = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(sl, bb));
+  return __dadd_rn(ff_widen(s), ff_widen(e));
+}
+
+// Frame record of the float-float form (32 floats = 128 bytes per cell): R hi [0, 9), R lo
+// [9, 18), b hi [18, 21), b lo [21, 24), rotate flag [24] (1 or 0).
+constexpr int kFfRhi = 0, kFfRlo = 9, kFfBhi = 18, kFfBlo = 21, kFfFlag = 24;
+
+__device__ __forceinline__ void ff_store_frame(float* f, const double R[9], const double bvec[3]) {
+  float w[28];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ff_split(R[k], w[kFfRhi + k], w[kFfRlo + k]);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) ff_split(bvec[k], w[kFfBhi + k], w[kFfBlo + k]);
+  w[kFfFlag] = 1.0f;
+  w[25] = w[26] = w[27] = 0.0f;
+  float4* o = reinterpret_cast<float4*>(f);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) o[k] = make_float4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+}
+
+// v' = R v + b with the frame in float-float form (w: the record's first 28 floats).
+__device__ __forceinline__ void ff_apply_frame(const float w[28], double& v0, double& v1, double& v2) {
+  float vh[3], vl[3];
+  ff_split(v0, vh[0], vl[0]);
+  ff_split(v1, vh[1], vl[1]);
+  ff_split(v2, vh[2], vl[2]);
+  double out[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float sh = w[kFfBhi + i], sl = w[kFfBlo + i];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ff_madd(w[kFfRhi + 3 * i + j], w[kFfRlo + 3 * i + j], vh[j], vl[j], sh, sl);
+    out[i] = ff_join(sh, sl);
+  }
+  v0 = out[0];
+  v1 = out[1];
+  v2 = out[2];
+}
+
 // -------------------------------------------------------------- cell coordinates ----
 // floor(q * 2^k) for |q * 2^k| < 2^30 from the bit pattern of q (integer pipe only; the
 // power-of-two scale is an exponent shift, so no FP64 multiply is needed).  Larger

@@ -34,6 +34,11 @@ unsigned grid_for(int64_t n, int per_thread = 1) {
 }
 
 
+// Cell keys of step t.  The dense pair double-buffers them by the parity of t: its fused
+// rotate-and-stream kernel reads step t's keys (the frame of each slot's cell) while it writes
+// step t + 1's at the re-sort destinations.  Everywhere else key2 == key.
+__device__ __forceinline__ int32_t* keys_of(const Scratch& s, int64_t t) { return (t & 1) ? s.key2 : s.key; }
+
 __device__ __forceinline__ double wrap_periodic(double x, double B) {
   return wrap_box(x, B, __double_as_longlong(B));
 }
@@ -128,6 +133,7 @@ template <int WALLS, int FORCE, int POW2A>
 __global__ void __launch_bounds__(kThreads, 4) k_stream_bin_fp64(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl) {
   const int cur = ctl->cur;
   const double shl[3] = {ctl->shift[0], ctl->shift[1], ctl->shift[2]};
+  int32_t* __restrict__ kout = keys_of(s, ctl->t + 1);
   double* __restrict__ rx = b.r[cur][0];
   double* __restrict__ ry = b.r[cur][1];
   double* __restrict__ rz = b.r[cur][2];
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream_bin_fp64(Geom g, Fp64Buf
       vy[i] = v0[1];
       vz[i] = v0[2];
     }
-    s.key[i] = k0;
+    kout[i] = k0;
     if (two) {
       rx[j] = r1[0];
       ry[j] = r1[1];
@@ -170,20 +176,34 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream_bin_fp64(Geom g, Fp64Buf
         vy[j] = v1[1];
         vz[j] = v1[2];
       }
-      s.key[j] = k1;
+      kout[j] = k1;
     }
-    const int a0 = atomicAdd(&s.count[k0], 1);
-    const int a1 = two ? atomicAdd(&s.count[k1], 1) : 0;
-    s.rank[i] = a0;
-    if (two) s.rank[j] = a1;
+    if (s.cursor) {  // the scatter takes the places from the cursor: counts without a round trip
+      atomicAdd(&s.count[k0], 1);
+      if (two) atomicAdd(&s.count[k1], 1);
+    } else {
+      const int a0 = atomicAdd(&s.count[k0], 1);
+      const int a1 = two ? atomicAdd(&s.count[k1], 1) : 0;
+      s.rank[i] = a0;
+      if (two) s.rank[j] = a1;
+    }
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_scatter(int64_t n, const int32_t* __restrict__ key,
-                                                      const int32_t* __restrict__ rank, const int32_t* __restrict__ offset,
-                                                      int32_t* __restrict__ perm) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    perm[offset[key[i]] + rank[i]] = static_cast<int32_t>(i);
+// perm[offset[key] + place] = slot, with the keys of the step in flight (ctl->t + 1), or of
+// s.key when ctl is null (the initial cell-order sort).  The place inside the cell is the
+// arrival rank of the counting atomics, or, with a cursor array, taken here from the cell's
+// cursor.  Either way a cell's entries are in no fixed order; the exact cell sums do not
+// depend on it, and the kernels that need storage order sort the cell's entries.
+__global__ void __launch_bounds__(kThreads) k_scatter(int64_t n, Scratch s, const Ctl* __restrict__ ctl) {
+  const int32_t* __restrict__ key = ctl ? keys_of(s, ctl->t + 1) : s.key;
+  const int32_t* __restrict__ offset = s.offset;
+  int32_t* __restrict__ perm = s.perm;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int k = key[i];
+    const int place = s.cursor ? atomicAdd(&s.cursor[k], 1) : s.rank[i];
+    perm[offset[k] + place] = static_cast<int32_t>(i);
+  }
 }
 
 // Insertion sort of a cell's perm entries: the counting atomics hand out arrival ranks in
@@ -663,6 +683,10 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
     bv[1] -= aw[2] * lbar[0] - aw[0] * lbar[2];
     bv[2] -= aw[0] * lbar[1] - aw[1] * lbar[0];
   }
+  if (!ANG) {  // the rotation applies the frame in float-float arithmetic
+    ff_store_frame(reinterpret_cast<float*>(s.frame + kFrameStride * c), R, bv);
+    return;
+  }
   rec[0] = make_double2(R[0], R[1]);
   rec[1] = make_double2(R[2], R[3]);
   rec[2] = make_double2(R[4], R[5]);
@@ -670,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
   rec[4] = make_double2(R[8], bv[0]);
   rec[5] = make_double2(bv[1], bv[2]);
   rec[6] = make_double2(1.0, aw[0]);
-  if (ANG) rec[7] = make_double2(aw[1], aw[2]);
+  rec[7] = make_double2(aw[1], aw[2]);
 }
 
 // One storage slot of k_rotate: its velocity and its cell's frame record, all loaded
@@ -683,9 +707,10 @@ struct RotSlot {
 };
 
 template <int ANG>
-__device__ __forceinline__ void rotate_load(const Fp64Bufs& b, const Scratch& s, int64_t i, int cur, RotSlot& q) {
+__device__ __forceinline__ void rotate_load(const Fp64Bufs& b, const Scratch& s, const int32_t* __restrict__ key,
+                                            int64_t i, int cur, RotSlot& q) {
   q.i = i;
-  const int c = s.key[i];
+  const int c = key[i];
   q.v[0] = b.v[cur][0][i];
   q.v[1] = b.v[cur][1][i];
   q.v[2] = b.v[cur][2][i];
@@ -694,24 +719,50 @@ __device__ __forceinline__ void rotate_load(const Fp64Bufs& b, const Scratch& s,
   for (int k = 0; k < 7 + ANG; ++k) q.f[k] = rec[k];
 }
 
+// The frame of a loaded record applied to v: float-float (the record's 28 floats) without
+// angular-momentum conservation, FP64 with it (R, b and a omega x l_i, l_i the position in
+// the cell of the grid shifted by shift).
+template <int ANG>
+__device__ __forceinline__ void rotate_apply(const Geom& g, const double2 f[8], const double r[3], const double* shift,
+                                             double& v0, double& v1, double& v2) {
+  if (!ANG) {
+    float w[28];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      w[4 * k + 0] = __int_as_float(__double2loint(f[k].x));
+      w[4 * k + 1] = __int_as_float(__double2hiint(f[k].x));
+      w[4 * k + 2] = __int_as_float(__double2loint(f[k].y));
+      w[4 * k + 3] = __int_as_float(__double2hiint(f[k].y));
+    }
+    ff_apply_frame(w, v0, v1, v2);
+    return;
+  }
+  const double R[9] = {f[0].x, f[0].y, f[1].x, f[1].y, f[2].x, f[2].y, f[3].x, f[3].y, f[4].x};
+  const double bv[3] = {f[4].y, f[5].x, f[5].y};
+  apply_frame(R, bv, v0, v1, v2);
+  const double w0 = f[6].y, w1 = f[7].x, w2 = f[7].y;  // + (a omega) x l_i
+  const double l0 = cell_local(g, r[0], shift[0]);
+  const double l1 = cell_local(g, r[1], shift[1]);
+  const double l2 = cell_local(g, r[2], shift[2]);
+  v0 += w1 * l2 - w2 * l1;
+  v1 += w2 * l0 - w0 * l2;
+  v2 += w0 * l1 - w1 * l0;
+}
+
 template <int MASS, int ANG>
 __device__ __forceinline__ void rotate_finish(const Geom& g, const Fp64Bufs& b, const Fp64Mass& ms, const Scratch& s,
                                               RotSlot& q, int cur, bool resort, const double* shift) {
-  const bool rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1.0 or 0.0, tested as bits
+  // flag (1 or 0; FP64 or FP32, as bits) in the record's sixth 16-byte word
+  const bool rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;
   double v0 = q.v[0], v1 = q.v[1], v2 = q.v[2];
   if (rot) {
-    const double R[9] = {q.f[0].x, q.f[0].y, q.f[1].x, q.f[1].y, q.f[2].x, q.f[2].y, q.f[3].x, q.f[3].y, q.f[4].x};
-    const double bv[3] = {q.f[4].y, q.f[5].x, q.f[5].y};
-    apply_frame(R, bv, v0, v1, v2);
-    if (ANG) {  // + (a omega) x l_i
-      const double w0 = q.f[6].y, w1 = q.f[7].x, w2 = q.f[7].y;
-      const double l0 = cell_local(g, b.r[cur][0][q.i], shift[0]);
-      const double l1 = cell_local(g, b.r[cur][1][q.i], shift[1]);
-      const double l2 = cell_local(g, b.r[cur][2][q.i], shift[2]);
-      v0 += w1 * l2 - w2 * l1;
-      v1 += w2 * l0 - w0 * l2;
-      v2 += w0 * l1 - w1 * l0;
+    double r[3] = {0.0, 0.0, 0.0};
+    if (ANG) {
+      r[0] = b.r[cur][0][q.i];
+      r[1] = b.r[cur][1][q.i];
+      r[2] = b.r[cur][2][q.i];
     }
+    rotate_apply<ANG>(g, q.f, r, shift, v0, v1, v2);
   }
   const int64_t i = q.i;
   if (resort) {
@@ -732,16 +783,67 @@ __device__ __forceinline__ void rotate_finish(const Geom& g, const Fp64Bufs& b, 
   }
 }
 
+// The dense pair's rotation runs after the step's end_step: ctl->t is the step whose frames
+// are applied, ctl->cur the buffer set the particles end up in (flipped on re-sort steps),
+// ctl->shift_last that step's grid shift.
 template <int MASS, int ANG = 0>
 __global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
                                                        Fp64Mass ms) {
-  const int64_t t1 = ctl->t + 1;
-  const int cur = ctl->cur;
-  const bool resort = g.resort_k > 0 && (t1 % g.resort_k) == 0;
+  const int64_t t = ctl->t;
+  const bool resort = g.resort_k > 0 && (t % g.resort_k) == 0;
+  const int src = resort ? ctl->cur ^ 1 : ctl->cur;
+  const int32_t* __restrict__ key = keys_of(s, t);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     RotSlot q;
-    rotate_load<ANG>(b, s, i, cur, q);
-    rotate_finish<MASS, ANG>(g, b, ms, s, q, cur, resort, ctl->shift);
+    rotate_load<ANG>(b, s, key, i, src, q);
+    rotate_finish<MASS, ANG>(g, b, ms, s, q, src, resort, ctl->shift_last);
+  }
+}
+
+// The rotation of step t fused with the streaming and binning of step t + 1 (one pass over
+// the state instead of two): each slot's velocity gets its cell's frame (v' = R v + b, the
+// same arithmetic as k_rotate), the particle moves on (the same arithmetic as stream_bin),
+// and it is written, on re-sort steps to its cell-order slot in the other buffer set, with
+// its key on step t + 1's shifted grid and its arrival rank in that cell.
+template <int FORCE, int POW2A, int MASS, int ANG>
+__global__ void __launch_bounds__(kThreads, 4) k_rotate_stream(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
+                                                              Fp64Mass ms) {
+  const int64_t t = ctl->t;
+  const bool resort = g.resort_k > 0 && (t % g.resort_k) == 0;
+  const int cur = ctl->cur;
+  const int src = resort ? cur ^ 1 : cur;
+  const int32_t* __restrict__ kin = keys_of(s, t);
+  int32_t* __restrict__ kout = keys_of(s, t + 1);
+  const double shn[3] = {ctl->shift[0], ctl->shift[1], ctl->shift[2]};  // step t + 1
+  const double shl[3] = {ctl->shift_last[0], ctl->shift_last[1], ctl->shift_last[2]};  // step t
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+    RotSlot q;
+    rotate_load<ANG>(b, s, kin, i, src, q);
+    double r[3] = {b.r[src][0][i], b.r[src][1][i], b.r[src][2][i]};
+    const bool rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1 or 0, as bits
+    double v[3] = {q.v[0], q.v[1], q.v[2]};
+    if (rot) rotate_apply<ANG>(g, q.f, r, shl, v[0], v[1], v[2]);  // l_i on step t's grid
+    const int64_t dst = resort ? s.inv[i] : i;
+    const int32_t pid = resort ? b.id[src][i] : 0;
+    const double pm = (MASS && resort) ? ms.m[src][i] : 0.0;
+    const int k = move_and_key<0, FORCE, POW2A>(g, r, v, shn);
+    b.r[cur][0][dst] = r[0];
+    b.r[cur][1][dst] = r[1];
+    b.r[cur][2][dst] = r[2];
+    if (resort || rot || FORCE) {
+      b.v[cur][0][dst] = v[0];
+      b.v[cur][1][dst] = v[1];
+      b.v[cur][2][dst] = v[2];
+    }
+    if (resort) {
+      b.id[cur][dst] = pid;
+      if (MASS) ms.m[cur][dst] = pm;
+    }
+    kout[dst] = k;
+    if (s.cursor)
+      atomicAdd(&s.count[k], 1);
+    else
+      s.rank[dst] = atomicAdd(&s.count[k], 1);
   }
 }
 
@@ -886,13 +988,14 @@ __global__ void __launch_bounds__(kThreads) k_permute_fp64(int64_t n, const int3
 }  // namespace
 
 int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaStream_t st) {
+  s.cursor = nullptr;  // ranks from the counting atomics
   launch_zero_i32(s.count, g.ncell, st);
   if (g.pow2a)
     k_presort_keys<1><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s);
   else
     k_presort_keys<0><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s);
   launch_scan(s.count, s.offset, s.partial, g.ncell, st);
-  launch_scatter(g, s, st);
+  launch_scatter(g, s, nullptr, st);
   launch_sort_segments(g, s, st);
   k_permute_fp64<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.perm, b, ms);
   return 8;  // kernels launched: zero, keys, scan (3), scatter, in-cell sort, gather
@@ -917,8 +1020,8 @@ void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cuda
   }
 }
 
-void launch_scatter(const Geom& g, Scratch s, cudaStream_t st) {
-  k_scatter<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.key, s.rank, s.offset, s.perm);
+void launch_scatter(const Geom& g, Scratch s, const Ctl* ctl, cudaStream_t st) {
+  k_scatter<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s, ctl);
 }
 
 void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st,
@@ -967,6 +1070,25 @@ void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool mo
     case 6: k_cell_frame<0, 1, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
     default: k_cell_frame<1, 1, 1><<<cgrid, kThreads, 0, st>>>(g, b, s, ctl, ms); break;
   }
+}
+
+namespace {
+template <int F, int P, int M, int A>
+void rotate_stream_launch(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st, Fp64Mass ms) {
+  k_rotate_stream<F, P, M, A><<<grid_for(g.n), kThreads, 0, st>>>(g, b, s, ctl, ms);
+}
+}  // namespace
+
+void launch_rotate_stream_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st, Fp64Mass ms) {
+  using Launch = void (*)(const Geom&, Fp64Bufs, Scratch, Ctl*, cudaStream_t, Fp64Mass);
+  static const Launch table[16] = {
+      rotate_stream_launch<0, 0, 0, 0>, rotate_stream_launch<0, 0, 0, 1>, rotate_stream_launch<0, 0, 1, 0>,
+      rotate_stream_launch<0, 0, 1, 1>, rotate_stream_launch<0, 1, 0, 0>, rotate_stream_launch<0, 1, 0, 1>,
+      rotate_stream_launch<0, 1, 1, 0>, rotate_stream_launch<0, 1, 1, 1>, rotate_stream_launch<1, 0, 0, 0>,
+      rotate_stream_launch<1, 0, 0, 1>, rotate_stream_launch<1, 0, 1, 0>, rotate_stream_launch<1, 0, 1, 1>,
+      rotate_stream_launch<1, 1, 0, 0>, rotate_stream_launch<1, 1, 0, 1>, rotate_stream_launch<1, 1, 1, 0>,
+      rotate_stream_launch<1, 1, 1, 1>};
+  table[(g.force ? 8 : 0) | (g.pow2a ? 4 : 0) | (ms.m[0] ? 2 : 0) | (g.angular ? 1 : 0)](g, b, s, ctl, st, ms);
 }
 
 void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st, Fp64Mass ms) {

@@ -99,8 +99,10 @@ struct MixScratch {
 
 // Per-step scratch of the counting sort and the cell reduction.
 struct Scratch {
-  int32_t* key;      // [N] cell key per storage slot
+  int32_t* key;      // [N] cell key per storage slot (of even steps where key2 is separate)
+  int32_t* key2;     // [N] keys of odd steps for the dense pair's fused pass; else == key
   int32_t* rank;     // [N] arrival rank inside the cell (from the counting atomics)
+  int32_t* cursor;   // [C] per-cell place cursor of the scatter; null: the scatter uses rank
   int32_t* perm;     // [N] storage slot of the j-th particle in cell order
   int32_t* count;    // [C] particles per cell
   int32_t* offset;   // [C + 1] exclusive prefix sum of count
@@ -118,7 +120,8 @@ void launch_scan(const int32_t* count, int32_t* offset, int32_t* partial, int64_
 
 void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);
 void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st);
-void launch_scatter(const Geom& g, Scratch s, cudaStream_t st);
+// perm from keys and ranks: the keys of step ctl->t + 1, or s.key when ctl is null
+void launch_scatter(const Geom& g, Scratch s, const Ctl* ctl, cudaStream_t st);
 // periodic boxes without thermostat or angular-momentum correction (fp64_dense_collide):
 // cell_frame here, then launch_rotate_fp64; otherwise one thread per cell here and no
 // rotate launch
@@ -126,7 +129,12 @@ bool fp64_dense_collide(const Geom& g, const Scratch& s);
 // dst[j] = m_by_id[id[j]]: particle masses into storage order
 void launch_gather_masses(int64_t n, const double* m_by_id, const int32_t* id, double* dst, cudaStream_t st);
 void launch_collide_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st, Fp64Mass ms);
+// The dense pair's rotation of step ctl->t, launched after that step's end_step (so ctl->cur
+// is the buffer set the particles end in); the last step of every mpcd_step call.
 void launch_rotate_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st, Fp64Mass ms);
+// The rotation of step ctl->t fused with the streaming and binning of step ctl->t + 1 (dense
+// pair, every step of an mpcd_step call after its first).
+void launch_rotate_stream_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cudaStream_t st, Fp64Mass ms);
 // one thread per cell for every box kind (no frame buffer needed)
 void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st,
                                  Fp64Mass ms = Fp64Mass{});

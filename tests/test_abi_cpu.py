@@ -59,12 +59,12 @@ def test_tuning_layout_matches_c(tmp_path):
     prog = tmp_path / "t.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mpcd.h"\n'
                     'int main(void){printf("%zu %zu %zu\\n", sizeof(mpcd_tuning), offsetof(mpcd_tuning, resort_k),'
-                    ' offsetof(mpcd_tuning, reserved)); return 0;}\n')
+                    ' offsetof(mpcd_tuning, fuse)); return 0;}\n')
     exe = tmp_path / "t"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     T = abi.Tuning
-    assert got == [__import__("ctypes").sizeof(T), T.resort_k.offset, T.reserved.offset]
+    assert got == [__import__("ctypes").sizeof(T), T.resort_k.offset, T.fuse.offset]
 
 
 def test_ensemble_arguments_checked_on_host(libpath):

@@ -43,7 +43,7 @@ def angular_multiplier(p, rr, ref, m=None):
     return mult
 
 
-def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True, masses=None):
+def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True, masses=None, displacement_scale=False):
     """Advance the library and the oracle from the same state (and per-particle masses, in
     particle-id order); compare after every step."""
     box = abi.Box(p)
@@ -63,7 +63,8 @@ def run_pair(orc, p, r, v, steps, t0=0, check_sort_every=True, masses=None):
             rr, vr = st.by_id()
             if p.angular:
                 mult = angular_multiplier(p, rr, ref, masses)
-            assert_state_close(rg, vg, rr, vr, p, tol=1e-12 * mult, what="step %d" % (t0 + k + 1))
+            r_scale = np.abs(vr).max(axis=1) * p.dt if displacement_scale else None
+            assert_state_close(rg, vg, rr, vr, p, tol=1e-12 * mult, what="step %d" % (t0 + k + 1), r_scale=r_scale)
             if p.angular:  # restart both sides from the oracle's state: one-step comparisons
                 box.set_state(rr, vr, st.t)
                 st = orc.presort(op, orc.State(rr, vr, t=st.t, m=masses))
@@ -232,7 +233,10 @@ def test_graph_and_timed_paths_agree():
             outs.append(box.state())
             if timed:
                 t = abi.mpcd_timing_read(box.h)
-                assert t["collide"][1] == 7 and t["rotate"][1] == 7 and t["scan"][1] == 21
+                # one mpcd_step(7) call: the first step streams alone, the next six fuse the
+                # previous rotation with their streaming, and the last rotation runs alone
+                assert t["collide"][1] == 7 and t["scan"][1] == 21
+                assert t["stream_bin"][1] == 1 and t["rotate_stream"][1] == 6 and t["rotate"][1] == 1
                 assert all(ms >= 0 for ms, _ in t.values())
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
 
@@ -355,10 +359,32 @@ def test_fast_particles_fallback_sums_in_storage_order(orc):
     cell is summed in plain FP64 with its members in storage order, the oracle's order, so
     the result matches the oracle and repeats bit for bit although the counting atomics
     hand out the slots in a different order on every run.  No re-sort (k = 0): the cells'
-    entries arrive in atomic order every step."""
+    entries arrive in atomic order every step.  A fast particle crosses the box about a
+    thousand times per step, so its position bound scales with its displacement |v| dt."""
     p = abi.make_params((6, 6, 6), seed=71, resort_k=0)
     n = int(round(p.ppc * 216))
     r, v = inputs.uniform_gaussian_state((6, 6, 6), n, 72)
     v[::97, 0] = 7.0e4 * np.where(np.arange(0, n, 97) % 2 == 0, 1.0, -1.0)   # > 2^16
-    outs = [run_pair(orc, p, r, v, steps=4)[0] for _ in range(2)]
+    outs = [run_pair(orc, p, r, v, steps=4, displacement_scale=True)[0] for _ in range(2)]
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(angular=1), dict(masses=True), dict(g=(0.01, 0.0, -0.02), a=0.7)],
+                         ids=["plain", "angular", "masses", "force_a_non_pow2"])
+def test_fused_and_separate_passes_identical(kw):
+    """The tuning's fuse switch only changes how the rotation is scheduled (in the next step's
+    streaming pass, or in a pass of its own): identical bits, across re-sorts and across
+    several mpcd_step calls."""
+    kw = dict(kw)
+    masses = kw.pop("masses", False)
+    p = abi.make_params((10, 9, 8), resort_k=3, seed=91, **kw)
+    outs = []
+    for fuse in (1, 0):
+        with abi.Box(p) as box:
+            abi.mpcd_set_tuning(box.h, fuse=fuse)
+            if masses:
+                box.set_masses(np.random.default_rng(4).uniform(0.5, 3.0, box.n))
+            for n in (1, 3, 4, 2):
+                box.step(n)
+            outs.append(box.state())
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
