@@ -79,7 +79,7 @@ NCU_TRAFFIC = {("mixed", "collide"): (72.07, "profiles/mixed_L128_collide_stream
 # channel with each cell thermostat, the angular-momentum-conserving collision and per-particle
 # masses
 FORMS = ("mixed_L256", "batched_256", "poiseuille_256x64x64", "poiseuille_256x64x64_mbs", "fp64_L128_angular",
-         "mixed_L128_angular", "fp64_L128_masses")
+         "mixed_L128_angular", "fp64_L128_masses", "mixed_L128_masses")
 
 
 # What each form reaches against the FP64 oracle (the parity and error-report tests), stated
@@ -93,6 +93,7 @@ FORM_ACCURACY = {
     "fp64_L128_angular": "FP64: 1e-12 against the oracle (omega scaled by the inertia tensor's condition)",
     "mixed_L128_angular": "mixed: per-cell momentum and angular momentum conserved to FP32 rounding",
     "fp64_L128_masses": "FP64: 1e-12 against the oracle",
+    "mixed_L128_masses": "mixed with FP32 masses: one-step bounds as mixed_L256 against the mass-weighted oracle",
 }
 
 

@@ -137,18 +137,33 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v);
  * is visible only through mpcd_debug_sort.  Synchronises. */
 int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64_t t);
 
-/* Per-particle masses (the m of the cell sums sum m v and sum m, Sec. 3.3 Listing 4), FP64
- * form: m[n] in particle-id order, every value finite and > 0, n = mpcd_num_particles.
+/* Per-particle masses (the m of the cell sums sum m v and sum m, Sec. 3.3 Listing 4):
+ * m[n] in particle-id order, every value finite and > 0, n = mpcd_num_particles.  The mixed
+ * form keeps them in FP32 (each value rounded once; mpcd_get_masses returns the rounded
+ * values), sums the FP32 products m v exactly, and takes every cell through its per-cell
+ * path; with angular-momentum conservation it rejects masses (MPCD_ERR_ARG).
  * They weight the centre-of-mass velocity, the moments, the thermostat's kinetic energy and
  * the angular-momentum correction (whose centre becomes mass-weighted); the rotation of
  * v - u keeps sum m v and sum m v^2 / 2.  Virtual wall particles and the initial velocities
  * keep params.mass.  Masses follow their particles through re-sorts and mpcd_set_state.
  * m = NULL restores the box mass.
- * Errors: MPCD_ERR_ARG (mixed form: its 32-byte record has no field for a mass; n != N; a
- * mass not finite or <= 0, named in the message).  Synchronises. */
+ * Errors: MPCD_ERR_ARG (n != N; a mass not finite or <= 0, named in the message; the mixed
+ * form with angular-momentum conservation).  Synchronises. */
 int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m);
 /* The masses in particle-id order (params.mass everywhere when none were set). */
 int mpcd_get_masses(mpcd_t* h, double* m);
+
+/* Coupling hook: an external momentum source acting on the fluid between steps, the way an
+ * embedded solute (for instance a molecular-dynamics body, the coupling the paper names as
+ * future work in Sec. 5) exchanges momentum with the solvent.  Adds dp_i / m_i to the
+ * velocity of every particle i, with dp[n * 3] in particle-id order (FP64) and m_i the
+ * particle's mass (mpcd_set_masses) or its box's mass.  FP64 form: v + dp / m, each operation
+ * rounded once; mixed form: the FP32 velocity becomes the FP32 rounding of v + dp / m.
+ * n must equal mpcd_num_particles.  The device variant is enqueued on the handle's stream;
+ * the host one copies dp to the device first and synchronises.
+ * Errors: MPCD_ERR_ARG (n != N, NULL). */
+int mpcd_add_momentum(mpcd_t* h, int64_t n, const double* dp);
+int mpcd_add_momentum_device(mpcd_t* h, int64_t n, const double* dp_dev);
 
 /* Same as mpcd_get_state / mpcd_set_state with device arrays.  get_state_device is enqueued
  * on the handle's stream without a host synchronisation; set_state_device checks the state

@@ -30,6 +30,7 @@ EXPORTS = [
     "mpcd_cell_moments", "mpcd_debug_sort", "mpcd_timing", "mpcd_timing_read", "mpcd_launch_count",
     "mpcd_last_error", "mpcd_version", "mpcd_step_fp64_noalloc", "mpcd_box_offsets", "mpcd_get_tuning",
     "mpcd_set_tuning", "mpcd_autotune", "mpcd_set_masses", "mpcd_get_masses", "mpcd_measure_fp64_rate",
+    "mpcd_add_momentum", "mpcd_add_momentum_device",
 ]
 MPCD_NOALLOC_MAX_PARTICLES = 1 << 19
 MPCD_NOALLOC_MAX_CELLS = 1 << 17
@@ -150,6 +151,8 @@ def lib():
                 "mpcd_last_error": ([H], ctypes.c_char_p),
                 "mpcd_version": ([], ctypes.c_char_p),
                 "mpcd_measure_fp64_rate": ([dp], ctypes.c_int),
+                "mpcd_add_momentum": ([H, i64, dp], ctypes.c_int),
+                "mpcd_add_momentum_device": ([H, i64, dp], ctypes.c_int),
                 "mpcd_step_fp64_noalloc": ([ctypes.POINTER(Params), i64, i64] + [dp] * 6 + [ctypes.c_void_p],
                                            ctypes.c_int),
                 "mpcd_box_offsets": ([H, dp, dp], ctypes.c_int),
@@ -318,6 +321,18 @@ def mpcd_last_error(h=None) -> str:
 
 def mpcd_version() -> str:
     return lib().mpcd_version().decode()
+
+
+def mpcd_add_momentum(h, dp):
+    """v_i += dp_i / m_i for every particle (dp: (N, 3) FP64 in particle-id order, host or device)."""
+    n = mpcd_num_particles(h)
+    if hasattr(dp, "data_ptr"):
+        assert tuple(dp.shape) == (n, 3) and dp.is_contiguous()
+        return _check(lib().mpcd_add_momentum_device(h, n, dp.data_ptr()), h)
+    a = np.ascontiguousarray(dp, dtype=np.float64)
+    if a.shape != (n, 3):
+        raise ValueError("dp must have shape (N, 3)")
+    return _check(lib().mpcd_add_momentum(h, n, a.ctypes.data), h)
 
 
 def mpcd_measure_fp64_rate() -> float:

@@ -68,6 +68,8 @@ struct mpcd_s {
   double* host_stage = nullptr;  // 6 N doubles for the host get/set_state copies, made on first use
   double* mass_buf[3] = {};  // FP64 particle masses: storage order (two buffer sets), id order
   Fp64Mass f64m{};           // points at mass_buf[0..1] while masses are set
+  float* mix_mass_buf[2] = {};  // mixed form: FP32 masses in the storage order of each record buffer
+  MixMass mixm{};               // points at mix_mass_buf while masses are set
   bool masses = false;
   Scratch scr{};
   MixBufs mix{};
@@ -300,7 +302,7 @@ int enqueue_piece(mpcd_t* h, int piece, bool moments, int par = 0) {
          })))
       return rc;
     if ((rc = run_slot(h, kSlotCollide,
-                       [&] { launch_collide_stream_mixed(h->mb, h->mix, m, h->ctl, moments, h->stream); })))
+                       [&] { launch_collide_stream_mixed(h->mb, h->mix, m, h->ctl, moments, h->stream, h->mixm); })))
       return rc;
     if ((rc = run_slot(h, kSlotEndStep, [&] { launch_end_step_mixed(h->mb, h->ctl, h->stream); }))) return rc;
     return MPCD_OK;
@@ -735,28 +737,49 @@ int mpcd_get_state_device(mpcd_t* h, double* r_dev, double* v_dev) {
 int mpcd_set_masses(mpcd_t* h, int64_t n, const double* m) {
   int rc = guard(h);
   if (rc) return rc;
-  if (h->precision != MPCD_FP64)
-    return fail(h, MPCD_ERR_ARG, "particle masses need the FP64 form (the 32-byte mixed record has no field for them)");
+  const bool mixed = h->precision == MPCD_MIXED;
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!m) {
     h->masses = false;
     h->f64m.m[0] = h->f64m.m[1] = nullptr;
+    h->mixm.m[0] = h->mixm.m[1] = nullptr;
   } else {
+    if (mixed && h->geom.angular)
+      return fail(h, MPCD_ERR_ARG,
+                  "particle masses with angular-momentum conservation need the FP64 form (MPCD_FP64)");
+    std::vector<double> m32;
     for (int64_t i = 0; i < n; ++i)
-      if (!(m[i] > 0.0) || !std::isfinite(m[i]))
+      if (!(m[i] > 0.0) || !std::isfinite(m[i]) || (mixed && !(static_cast<float>(m[i]) > 0.0f)) ||
+          (mixed && !std::isfinite(static_cast<float>(m[i]))))
         return fail(h, MPCD_ERR_ARG, "masses must be finite and > 0 (particle " + std::to_string(i) + ")");
-    for (int k = 0; k < 3; ++k)
-      if (!h->mass_buf[k] && (rc = dalloc(h, &h->mass_buf[k], n > 0 ? n : 1))) return rc;
+    if (mixed) {  // the mixed form keeps FP32 masses; get_masses reports those values
+      m32.resize((size_t)n);
+      for (int64_t i = 0; i < n; ++i) m32[(size_t)i] = static_cast<double>(static_cast<float>(m[i]));
+      m = m32.data();
+    }
+    if (!h->mass_buf[2] && (rc = dalloc(h, &h->mass_buf[2], n > 0 ? n : 1))) return rc;
+    for (int k = 0; k < 2; ++k) {
+      if (!mixed && !h->mass_buf[k] && (rc = dalloc(h, &h->mass_buf[k], n > 0 ? n : 1))) return rc;
+      if (mixed && !h->mix_mass_buf[k] && (rc = dalloc(h, &h->mix_mass_buf[k], n > 0 ? n : 1))) return rc;
+    }
     MPCD_TRY(h, cudaMemcpyAsync(h->mass_buf[2], m, sizeof(double) * (size_t)n, cudaMemcpyHostToDevice, h->stream));
     // into the storage order of the current buffer set; a re-sort carries them along
-    launch_gather_masses(n, h->mass_buf[2], h->f64.id[h->cur], h->mass_buf[h->cur], h->stream);
+    if (mixed)
+      launch_gather_masses_mixed(n, h->mix.rec[h->cur], h->mass_buf[2], h->mix_mass_buf[h->cur], h->stream);
+    else
+      launch_gather_masses(n, h->mass_buf[2], h->f64.id[h->cur], h->mass_buf[h->cur], h->stream);
     MPCD_TRY(h, cudaGetLastError());
     h->launches += 1;
     h->masses = true;
-    h->f64m.m[0] = h->mass_buf[0];
-    h->f64m.m[1] = h->mass_buf[1];
+    if (mixed) {
+      h->mixm.m[0] = h->mix_mass_buf[0];
+      h->mixm.m[1] = h->mix_mass_buf[1];
+    } else {
+      h->f64m.m[0] = h->mass_buf[0];
+      h->f64m.m[1] = h->mass_buf[1];
+    }
   }
-  h->per_step[kSlotRotate] = h->per_step[kSlotRotateStream] = (!h->geom.walls && !h->geom.thermostat) ? 1 : 0;
+  if (!mixed) h->per_step[kSlotRotate] = h->per_step[kSlotRotateStream] = (!h->geom.walls && !h->geom.thermostat) ? 1 : 0;
   drop_graph(h);  // the step graph holds the buffer pointers and the kernel choice
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   return MPCD_OK;
@@ -833,7 +856,9 @@ int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const doubl
   else
     launch_set_state_fp64(h->geom, h->f64, r_dev, v_dev, h->stream);
   MPCD_TRY(h, cudaGetLastError());
-  if (h->masses)  // the new storage is in particle-id order
+  if (h->masses && h->precision == MPCD_MIXED)  // the new records are in particle-id order
+    launch_gather_masses_mixed(n, h->mix.rec[0], h->mass_buf[2], h->mix_mass_buf[0], h->stream);
+  else if (h->masses)
     MPCD_TRY(h, cudaMemcpyAsync(h->mass_buf[0], h->mass_buf[2], sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice,
                                 h->stream));
   h->mixed_keys_valid = false;
@@ -866,6 +891,33 @@ int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64
   rc = mpcd_set_state_device(h, n, scratch, scratch + 3 * n, t);
   if (rc) return rc;
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  return MPCD_OK;
+}
+
+int mpcd_add_momentum_device(mpcd_t* h, int64_t n, const double* dp_dev) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
+  if (!dp_dev && n > 0) return fail(h, MPCD_ERR_ARG, "NULL input");
+  if (h->precision == MPCD_MIXED)
+    launch_add_momentum_mixed(h->mb, h->mix, h->cur, h->mixm, dp_dev, h->stream);
+  else
+    launch_add_momentum_fp64(h->geom, h->f64, h->cur, h->f64m, dp_dev, h->stream);
+  MPCD_TRY(h, cudaGetLastError());
+  h->launches += 1;
+  return MPCD_OK;
+}
+
+int mpcd_add_momentum(mpcd_t* h, int64_t n, const double* dp) {
+  int rc = guard(h);
+  if (rc) return rc;
+  if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
+  if (!dp && n > 0) return fail(h, MPCD_ERR_ARG, "NULL input");
+  double* scratch = nullptr;  // the increments are uploaded into the staging buffer
+  if ((rc = host_stage(h, &scratch))) return rc;
+  MPCD_TRY(h, cudaMemcpyAsync(scratch, dp, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, h->stream));
+  if ((rc = mpcd_add_momentum_device(h, n, scratch))) return rc;
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));  // the staging buffer is reused by the next host call
   return MPCD_OK;
 }
 

@@ -985,7 +985,23 @@ __global__ void __launch_bounds__(kThreads) k_permute_fp64(int64_t n, const int3
   }
 }
 
+// v += dp / m for every storage slot (dp by particle id; m the slot's mass or the box mass).
+__global__ void __launch_bounds__(kThreads) k_add_momentum_fp64(Geom g, Fp64Bufs b, int cur,
+                                                                const double* __restrict__ m,
+                                                                const double* __restrict__ dp) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < g.n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = b.id[cur][s];
+    const double mi = m ? m[s] : g.mass;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) b.v[cur][d][s] = __dadd_rn(b.v[cur][d][s], __ddiv_rn(dp[3 * i + d], mi));
+  }
+}
+
 }  // namespace
+
+void launch_add_momentum_fp64(const Geom& g, Fp64Bufs b, int cur, Fp64Mass ms, const double* dp, cudaStream_t st) {
+  if (g.n > 0) k_add_momentum_fp64<<<grid_for(g.n), kThreads, 0, st>>>(g, b, cur, ms.m[cur], dp);
+}
 
 int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaStream_t st) {
   s.cursor = nullptr;  // ranks from the counting atomics

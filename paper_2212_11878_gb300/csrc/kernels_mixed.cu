@@ -1410,7 +1410,39 @@ __global__ void __launch_bounds__(kThreads) k_get_state_mixed(MixBatch mb, const
     v[3 * p + 2] = q.vz;
   }
 }
+// Masses (by particle id, FP64) into the storage order of a record buffer, rounded to FP32.
+__global__ void __launch_bounds__(kThreads) k_gather_masses_mixed(int64_t n, const MixRec* __restrict__ rec,
+                                                                  const double* __restrict__ m_by_id,
+                                                                  float* __restrict__ dst) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    dst[j] = __double2float_rn(m_by_id[rec[j].id]);
+}
+
+// v += dp / m for every record (dp by particle id); the FP32 velocity becomes the FP32
+// rounding of the FP64 sum.
+__global__ void __launch_bounds__(kThreads) k_add_momentum_mixed(MixBatch mb, MixRec* __restrict__ rec,
+                                                                 const float* __restrict__ m,
+                                                                 const double* __restrict__ dp) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < mb.n; j += (int64_t)gridDim.x * blockDim.x) {
+    MixRec r = load_rec(rec + j);
+    const int64_t i = r.id;
+    const double mi = m ? static_cast<double>(m[j]) : mb.boxes[box_of(mb.pbase, mb.nbox, i)].mass;
+    r.vx = __double2float_rn(static_cast<double>(r.vx) + dp[3 * i] / mi);
+    r.vy = __double2float_rn(static_cast<double>(r.vy) + dp[3 * i + 1] / mi);
+    r.vz = __double2float_rn(static_cast<double>(r.vz) + dp[3 * i + 2] / mi);
+    store_rec(rec + j, r);
+  }
+}
+
 }  // namespace
+
+void launch_gather_masses_mixed(int64_t n, const MixRec* rec, const double* m_by_id, float* dst, cudaStream_t st) {
+  if (n > 0) k_gather_masses_mixed<<<grid_for(n), kThreads, 0, st>>>(n, rec, m_by_id, dst);
+}
+
+void launch_add_momentum_mixed(const MixBatch& mb, MixBufs b, int cur, MixMass ms, const double* dp, cudaStream_t st) {
+  if (mb.n > 0) k_add_momentum_mixed<<<grid_for(mb.n), kThreads, 0, st>>>(mb, b.rec[cur], ms.m[cur], dp);
+}
 
 void mixed_box_shifts(const Geom& g, int64_t t, BoxShift* out) {
   grid_shift(g.seed, t + 1, g.a, g.walls, out->s);
@@ -1528,6 +1560,160 @@ __global__ void __launch_bounds__(128) k_collide_direct_mixed(MixBatch mb, MixBu
   }
 }
 
+// ---- per-particle masses in the mixed form (Listing 4 sums m v and m; reading R24) ----
+// The masses are FP32 values in storage order beside the records (two buffer sets, moved with
+// them).  Each product m_j v_j is rounded once in FP32 and summed exactly on the fixed-point
+// grids, as are the m_j, so the member order does not matter: P = sum m v, M = sum m,
+// u = P / M (with the virtual wall particles of a cut cell, which keep the box mass), and
+// the energy-restoring rescale and the thermostats weight each member's terms by m_j.
+template <int THERMO>
+__device__ __forceinline__ float cell_df_mass(const Geom& g, int n, long long dE, long long Ea, bool ok, int64_t t1,
+                                              int64_t cell) {
+  if (!ok || Ea <= 0) return 0.0f;
+  const float ea = ll_to_float(Ea) * 0x1.0p-30f;  // sum m |w|^2
+  if (THERMO && n >= 2) {
+    const float dof = THERMO == 2 ? 2.0f * mbs_gamma_f32(g.seed, t1, cell, 1.5f * static_cast<float>(n - 1))
+                                  : 3.0f * static_cast<float>(n - 1);
+    return sqrtf(dof * g.kTf / ea) - 1.0f;
+  }
+  return 0.5f * (ll_to_float(dE) * 0x1.0p-44f) / ea;
+}
+
+template <int WALLS, int THERMO, int MOMENTS>
+__device__ void mixed_collide_cell_mass(const Geom& g, MixRec* rec, const float* __restrict__ m, int n, int64_t c,
+                                        int64_t t1, double shift_z, double* moments) {
+  long long P[3] = {0, 0, 0}, M = 0, E2 = 0;
+  bool ok = n < 8192;
+  for (int j = 0; j < n; ++j) {
+    const float mj = m[j], a = rec[j].vx, b = rec[j].vy, cz = rec[j].vz;
+    ok &= fx_add<kFixV>(P[0], __fmul_rn(mj, a)) & fx_add<kFixV>(P[1], __fmul_rn(mj, b)) &
+          fx_add<kFixV>(P[2], __fmul_rn(mj, cz)) & fx_add<kFixV>(M, mj);
+    if (MOMENTS) ok &= fx_add<kFixV2>(E2, __fmul_rn(mj, fmaf(a, a, fmaf(b, b, __fmul_rn(cz, cz)))));
+  }
+  if (MOMENTS) {
+    double* mo = moments + 5 * c;
+    mo[0] = __ll2double_rn(M) * 0x1.0p-32;
+    mo[1] = __ll2double_rn(P[0]) * 0x1.0p-32;
+    mo[2] = __ll2double_rn(P[1]) * 0x1.0p-32;
+    mo[3] = __ll2double_rn(P[2]) * 0x1.0p-32;
+    mo[4] = 0.5 * __ll2double_rn(E2) * 0x1.0p-30;
+  }
+  if (n == 0 || M <= 0) return;
+  CellFrame f;
+  f.df = 0.0f;
+  const float Mf = ll_to_float(M);
+  f.u[0] = ll_to_float(P[0]) / Mf;
+  f.u[1] = ll_to_float(P[1]) / Mf;
+  f.u[2] = ll_to_float(P[2]) / Mf;
+  bool virt = false;
+  if (WALLS) {
+    const int64_t layer = c / ((int64_t)g.L[0] * g.L[1]);
+    if (shift_z > 0.0 && (layer == 0 || layer == g.L[2]) && (double)n < g.ppc) {
+      // R13: virtual particles of the box mass fill the cut cell to ppc (FP64, wall cells only)
+      const double Mv = (g.ppc - (double)n) * g.mass;
+      const u64x4 w = draw(g.seed, static_cast<uint64_t>(t1), static_cast<uint64_t>(c), kTagWall);
+      double g0, g1, g2, g3;
+      gauss_pair(w.x, w.y, g0, g1);
+      gauss_pair(w.z, w.w, g2, g3);
+      const double sd = sqrt(Mv * g.kT);
+      const double Mt = __ll2double_rn(M) * 0x1.0p-32 + Mv;
+      f.u[0] = static_cast<float>((__ll2double_rn(P[0]) * 0x1.0p-32 + sd * g0) / Mt);
+      f.u[1] = static_cast<float>((__ll2double_rn(P[1]) * 0x1.0p-32 + sd * g1) / Mt);
+      f.u[2] = static_cast<float>((__ll2double_rn(P[2]) * 0x1.0p-32 + sd * g2) / Mt);
+      virt = true;
+    }
+  }
+  if (!(n >= 2 || virt) || !ok) return;
+  frame_f32(g, t1, c, f.R);
+  long long dE = 0, Ea = 0;
+  bool oke = n < 512;
+  for (int j = 0; j < n; ++j) {
+    float w[3] = {rec[j].vx, rec[j].vy, rec[j].vz};
+    const float term = rotate_relative(f, w);
+    rec[j].vx = w[0];
+    rec[j].vy = w[1];
+    rec[j].vz = w[2];
+    oke &= fx_add<kFixDE>(dE, __fmul_rn(m[j], term)) & fx_add<kFixV2>(Ea, __fmul_rn(m[j], sq3(w)));
+  }
+  const float df = cell_df_mass<THERMO>(g, n, dE, Ea, oke, t1, c);
+  for (int j = 0; j < n; ++j) {
+    rec[j].vx = __fadd_rn(f.u[0], fmaf(df, rec[j].vx, rec[j].vx));
+    rec[j].vy = __fadd_rn(f.u[1], fmaf(df, rec[j].vy, rec[j].vy));
+    rec[j].vz = __fadd_rn(f.u[2], fmaf(df, rec[j].vz, rec[j].vz));
+  }
+}
+
+// A warp per group of cells, a lane per cell: each cell's records and masses are gathered
+// through perm, streamed and written in cell order to the other buffer set, collided there
+// with their masses, and given the next step's keys and counts (as collide_group_direct).
+template <int WALLS, int FORCE, int THERMO, int MOMENTS>
+__global__ void __launch_bounds__(128) k_collide_mass_mixed(MixBatch mb, MixBufs b, MixScratch s, Ctl* __restrict__ ctl,
+                                                            MixMass ms) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  const int64_t t1 = ctl->t + 1;
+  const int cur = ctl->cur, nxt = cur ^ 1;
+  const MixRec* __restrict__ src = b.rec[cur];
+  MixRec* __restrict__ dst = b.rec[nxt];
+  const float* __restrict__ msrc = ms.m[cur];
+  float* __restrict__ mdst = ms.m[nxt];
+  for (int64_t gi = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5; gi < mb.ngroups; gi += warps) {
+    const MixGroup d = mb.groups[gi];
+    const Geom& g = mb.boxes[d.box];
+    const BoxShift* shp = mb.shifts + d.box;
+    const float sf[3] = {shp->sf_next[0], shp->sf_next[1], shp->sf_next[2]};
+    const int cbase = static_cast<int>(g.cbase);
+    for (int64_t c = d.c0 + lane; c < d.c0 + d.ncells; c += 32) {
+      const int o = s.offset[c];
+      const int n = s.offset[c + 1] - o;
+      const int32_t* pm = s.perm + o;
+      for (int j = 0; j < n; ++j) {
+        MixRec r = load_rec(src + pm[j]);
+        stream_record<WALLS, FORCE>(g, r);
+        dst[o + j] = r;
+        mdst[o + j] = msrc[pm[j]];
+      }
+      mixed_collide_cell_mass<WALLS, THERMO, MOMENTS>(g, dst + o, mdst + o, n, c - cbase, t1, shp->s[2],
+                                                      MOMENTS ? s.moments + 5 * (int64_t)cbase : nullptr);
+      for (int j = 0; j < n; ++j) {
+        const int k = cbase + next_key<WALLS, FORCE>(g, dst[o + j], sf);
+        s.key[nxt][o + j] = k;
+        atomicAdd(&s.count[nxt][k], 1);
+      }
+    }
+  }
+}
+
+template <int WALLS, int FORCE, int THERMO, int MOMENTS>
+void launch_mass_t(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, MixMass ms, cudaStream_t st) {
+  int64_t grid = (static_cast<int64_t>(mb.ngroups) + 3) / 4;
+  if (grid == 0) return;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_collide_mass_mixed<WALLS, FORCE, THERMO, MOMENTS><<<static_cast<unsigned>(grid), 128, 0, st>>>(mb, b, s, ctl, ms);
+}
+
+template <int WALLS, int FORCE>
+void launch_mass_wf(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, MixMass ms, bool moments, cudaStream_t st) {
+  switch (2 * mb.thermostat + (moments ? 1 : 0)) {
+    case 0: return launch_mass_t<WALLS, FORCE, 0, 0>(mb, b, s, ctl, ms, st);
+    case 1: return launch_mass_t<WALLS, FORCE, 0, 1>(mb, b, s, ctl, ms, st);
+    case 2: return launch_mass_t<WALLS, FORCE, 1, 0>(mb, b, s, ctl, ms, st);
+    case 3: return launch_mass_t<WALLS, FORCE, 1, 1>(mb, b, s, ctl, ms, st);
+    case 4: return launch_mass_t<WALLS, FORCE, 2, 0>(mb, b, s, ctl, ms, st);
+    default: return launch_mass_t<WALLS, FORCE, 2, 1>(mb, b, s, ctl, ms, st);
+  }
+}
+
+void launch_collide_mass(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, MixMass ms, bool moments,
+                         cudaStream_t st) {
+  if (mb.walls)
+    launch_mass_wf<1, 1>(mb, b, s, ctl, ms, moments, st);
+  else if (mb.force)
+    launch_mass_wf<0, 1>(mb, b, s, ctl, ms, moments, st);
+  else
+    launch_mass_wf<0, 0>(mb, b, s, ctl, ms, moments, st);
+}
+
 template <int FORCE, int THERMO, int MOMENTS>
 void launch_direct_t(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cudaStream_t st) {
   int64_t grid = (static_cast<int64_t>(mb.ngroups) + 3) / 4;
@@ -1606,8 +1792,11 @@ cudaError_t prepare_collide_mixed() {
   return e;
 }
 
-void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st) {
-  if (mb.angular)
+void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st,
+                                 MixMass ms) {
+  if (ms.m[0])
+    launch_collide_mass(mb, b, s, ctl, ms, moments, st);
+  else if (mb.angular)
     launch_collide_direct(mb, b, s, ctl, moments, st);
   else if (mb.warps == 2)
     (void)launch_collide_w<2>(mb, b, s, ctl, moments, st, false);

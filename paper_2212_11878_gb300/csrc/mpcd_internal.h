@@ -84,6 +84,12 @@ struct MixBufs {
   MixRec* rec[2];
 };
 
+// Per-particle masses of the mixed form (FP32) in the storage order of each record buffer
+// (null: every particle has its box's mass).  A separate, last kernel argument, like Fp64Mass.
+struct MixMass {
+  float* m[2];
+};
+
 // Scratch of the mixed step.  key/count are double-buffered: step t's collide kernel writes
 // the keys and counts of step t + 1 for the records it writes; the scatter takes each
 // particle's place in its cell from the per-cell cursor.
@@ -144,6 +150,8 @@ void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st);
 // buffer set 1 with the ids and masses; returns the number of kernels launched.
 int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
+// v += dp / m per particle (dp[3 N] by particle id, m its mass or the box mass)
+void launch_add_momentum_fp64(const Geom& g, Fp64Bufs b, int cur, Fp64Mass ms, const double* dp, cudaStream_t st);
 void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st);
 
 // ---- mixed form (kernels_mixed.cu); one box or an ensemble of independent boxes ----
@@ -195,7 +203,9 @@ void launch_bin_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, cud
 // Set up the collide kernels on the current device (shared-memory limit, persistent grid);
 // call once per device before the first launch, outside stream capture.
 cudaError_t prepare_collide_mixed();
-void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st);
+// With masses (ms.m[0] non-null) every group takes the per-cell path with mass-weighted sums.
+void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st,
+                                 MixMass ms = MixMass{});
 void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st);
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
                            cudaStream_t st);
@@ -203,6 +213,9 @@ void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset,
 void launch_group_bounds(const MixBatch& mb, const MixGroupSpec* spec, const int32_t* offset, MixGroup* groups,
                          cudaStream_t st);
 void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, double* v, cudaStream_t st);
+// masses by particle id into the FP32 storage-order array of record buffer rec
+void launch_gather_masses_mixed(int64_t n, const MixRec* rec, const double* m_by_id, float* dst, cudaStream_t st);
+void launch_add_momentum_mixed(const MixBatch& mb, MixBufs b, int cur, MixMass ms, const double* dp, cudaStream_t st);
 void launch_set_state_mixed(const MixBatch& mb, MixBufs b, const double* r, const double* v, cudaStream_t st);
 // First invalid particle of a state (position outside its box, non-finite velocity) into
 // *bad, which the caller sets to ~0 first: per box of *mb, or for the single box g if mb is NULL.

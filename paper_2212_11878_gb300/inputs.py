@@ -35,7 +35,7 @@ class Workload:
     g: tuple = (0.0, 0.0, 0.0)
     thermostat: int = 0
     angular: int = 0
-    mass_range: tuple = ()           # per-particle masses uniform in this range (times m), FP64 form
+    mass_range: tuple = ()           # per-particle masses uniform in this range (times m)
     steps: int = 100
     notes: str = ""
 
@@ -80,6 +80,9 @@ WORKLOADS = {
     "mixed_L128_angular": Workload("mixed_L128_angular", (128, 128, 128), seed=BASE_SEED + 2, steps=500,
                                    precision="mixed", resort_k=1, angular=1,
                                    notes="angular-momentum-conserving collision, mixed form (per-cell path)"),
+    "mixed_L128_masses": Workload("mixed_L128_masses", (128, 128, 128), seed=BASE_SEED + 2, steps=500,
+                                  precision="mixed", resort_k=1, mass_range=(0.5, 4.0),
+                                  notes="per-particle masses 0.5-4 m, mixed form (FP32 masses, per-cell path)"),
     "poiseuille_256x64x64_mbs": Workload("poiseuille_256x64x64_mbs", (256, 64, 64), ppc=20.0, seed=BASE_SEED + 3,
                                          steps=20000, precision="mixed", resort_k=1, walls_z=1,
                                          g=(1e-3, 0.0, 0.0), thermostat=2,

@@ -149,8 +149,8 @@ def test_particle_masses_api():
         for bad in (np.full(n, -1.0), np.full(n, np.nan), np.ones(n - 1)):
             with pytest.raises((abi.MpcdError, ValueError)):
                 box.set_masses(bad)
-    with abi.Box(abi.make_params((4, 4, 4), precision="mixed")) as mixed:
-        with pytest.raises(abi.MpcdError) as ei:
+    with abi.Box(abi.make_params((4, 4, 4), precision="mixed", angular=1)) as mixed:
+        with pytest.raises(abi.MpcdError) as ei:  # masses with angular conservation: FP64 form only
             mixed.set_masses(np.ones(mixed.n))
         assert ei.value.code == abi.MPCD_ERR_ARG
 
@@ -388,3 +388,26 @@ def test_fused_and_separate_passes_identical(kw):
                 box.step(n)
             outs.append(box.state())
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+@pytest.mark.parametrize("masses", [False, True])
+def test_add_momentum_fp64_exact(masses):
+    """The coupling hook: v_i + dp_i / m_i, each operation rounded once (numpy's IEEE
+    arithmetic gives the same bits), by particle id whatever the storage order; the host and
+    the device entry points agree."""
+    torch = pytest.importorskip("torch")
+    p = abi.make_params((8, 7, 6), seed=5, resort_k=2)
+    with abi.Box(p) as box:
+        m = np.random.default_rng(2).uniform(0.5, 3.0, box.n) if masses else None
+        if masses:
+            box.set_masses(m)
+        box.step(3)  # storage re-sorted
+        r0, v0 = box.state()
+        dp = np.random.default_rng(3).normal(0.0, 0.1, (box.n, 3))
+        abi.mpcd_add_momentum(box.h, dp)
+        r1, v1 = box.state()
+        mm = (m if masses else np.full(box.n, p.mass))[:, None]
+        assert np.array_equal(r1, r0) and np.array_equal(v1, v0 + dp / mm)
+        abi.mpcd_add_momentum(box.h, torch.from_numpy(-dp).to("cuda"))
+        box.sync()
+        assert np.array_equal(box.state()[1], v1 + (-dp) / mm)

@@ -350,3 +350,101 @@ def test_set_state_rejects_invalid_input(precision):
                     abi.mpcd_set_state_device(box.h, rd, vd, 0)
             r1, v1 = box.state()
             assert np.array_equal(r1, r0) and np.array_equal(v1, v0)
+
+
+MASS_CASES = [dict(L=(10, 9, 8)), dict(L=(9, 8, 7), g=(0.02, 0.0, 0.01)), dict(L=(10, 9, 8), thermostat=1, kT=1.3),
+              dict(L=(11, 9, 8), thermostat=2, kT=1.3), dict(L=(9, 8, 10), walls_z=1, g=(0.02, 0.01, 0.0)),
+              dict(L=(8, 9, 12), walls_z=1, g=(0.01, 0.0, 0.0), thermostat=2, ppc=15)]
+
+
+@pytest.mark.parametrize("case", MASS_CASES, ids=["periodic", "force", "thermostat", "mbs", "walls_force",
+                                                   "walls_mbs"])
+def test_one_step_with_masses_against_fp64_oracle(orc, case):
+    """Per-particle masses in the mixed form (FP32 masses 0.5 to 4 m, mass-weighted exact
+    sums): one step from a state and masses both forms represent exactly, against the oracle's
+    mass-weighted step, at the mixed form's one-step bounds."""
+    from parity import assert_mixed_one_step
+    p = mixed_params(seed=15, **case)
+    L = tuple(p.L)
+    n = int(round(p.ppc * np.prod(L)))
+    r0, v0 = quantize(*inputs.uniform_gaussian_state(L, n, 23, a=p.a), L, p.a)
+    m = np.random.default_rng(9).uniform(0.5, 4.0, n).astype(np.float32).astype(np.float64) * p.mass
+    with abi.Box(p) as box:
+        box.set_state(r0, v0, 4)
+        box.set_masses(m)
+        assert np.array_equal(abi.mpcd_get_masses(box.h), m)
+        box.step(1)
+        dbg = box.debug_sort()
+        rg, vg = box.state()
+    st = orc.State(r0, v0, t=4, m=m)
+    ref = orc.step(oracle_params(orc, p), st, debug=True)
+    rr, vr = st.by_id()
+    kg = np.empty(n, np.int64)
+    kg[dbg["ids"]] = dbg["keys"]
+    ko = np.empty(n, np.int64)
+    ko[ref["ids"]] = ref["keys"]
+    C = int(np.prod(L)) if not p.walls_z else L[0] * L[1] * (L[2] + 1)
+    assert_mixed_one_step(p, kg, ko, rg, vg, rr, vr, ref["shift"], C, what=str(case))
+
+
+def test_masses_mixed_api_and_conservation():
+    """Masses follow their particles through steps and set_state; the mass-weighted momentum
+    and kinetic energy are conserved (FP32 rounding); None restores the box mass: the same
+    bits as a box that never had masses."""
+    p = mixed_params((12, 12, 12), seed=31)
+    with abi.Box(p) as box, abi.Box(p) as plain:
+        m = np.random.default_rng(8).uniform(0.5, 3.0, box.n).astype(np.float32).astype(np.float64)
+        box.set_masses(m)
+        r0, v0 = box.state()
+        P0, E0 = (m[:, None] * v0).sum(axis=0), 0.5 * (m * (v0 * v0).sum(axis=1)).sum()
+        box.step(20)
+        r1, v1 = box.state()
+        assert np.array_equal(abi.mpcd_get_masses(box.h), m)
+        P1, E1 = (m[:, None] * v1).sum(axis=0), 0.5 * (m * (v1 * v1).sum(axis=1)).sum()
+        assert np.abs(P1 - P0).max() < 1e-4 * np.abs(m[:, None] * v0).sum() / 3
+        assert abs(E1 / E0 - 1) < 1e-5
+        box.set_state(r1, v1, 20)
+        assert np.array_equal(abi.mpcd_get_masses(box.h), m)
+        r0, v0 = plain.state()
+        box.set_state(r0, v0, 0)
+        box.set_masses(None)
+        box.step(3)
+        plain.step(3)
+        assert np.array_equal(box.state()[1], plain.state()[1])
+
+
+def test_ensemble_with_masses_equals_boxes_alone():
+    boxes = [dict(L=(8, 8, 8), ppc=10, alpha_deg=130, dt=0.1, seed=401),
+             dict(L=(12, 10, 8), ppc=6, alpha_deg=95, dt=0.2, seed=402, g=(0.01, 0.0, 0.0))]
+    params = [abi.make_params(precision="mixed", thermostat=1, **k) for k in boxes]
+    with abi.Box(batch=params) as ens:
+        pb, _ = abi.mpcd_box_offsets(ens.h)
+        m = np.random.default_rng(5).uniform(0.5, 2.0, ens.n).astype(np.float32).astype(np.float64)
+        ens.set_masses(m)
+        ens.step(6)
+        r, v = ens.state()
+    for b, p in enumerate(params):
+        with abi.Box(p) as one:
+            one.set_masses(m[pb[b]:pb[b + 1]])
+            one.step(6)
+            r1, v1 = one.state()
+        assert np.array_equal(r[pb[b]:pb[b + 1]], r1) and np.array_equal(v[pb[b]:pb[b + 1]], v1), b
+
+
+@pytest.mark.parametrize("masses", [False, True])
+def test_add_momentum_mixed(masses):
+    """The coupling hook in the mixed form: the FP32 velocity becomes the FP32 rounding of
+    v + dp / m (v and m the stored FP32 values), by particle id."""
+    p = mixed_params((9, 8, 7), seed=13)
+    with abi.Box(p) as box:
+        m = np.random.default_rng(2).uniform(0.5, 3.0, box.n).astype(np.float32).astype(np.float64) if masses else None
+        if masses:
+            box.set_masses(m)
+        box.step(2)
+        r0, v0 = box.state()
+        dp = np.random.default_rng(3).normal(0.0, 0.1, (box.n, 3))
+        abi.mpcd_add_momentum(box.h, dp)
+        r1, v1 = box.state()
+    mm = (m if masses else np.full(len(v0), p.mass))[:, None]
+    assert np.array_equal(r1, r0)
+    assert np.array_equal(v1, (v0 + dp / mm).astype(np.float32).astype(np.float64))
