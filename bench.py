@@ -69,6 +69,9 @@ MIXED_BYTES = {
     "scatter": (12.0, 4.0),
     "collide": (4.0 + 32.0 + 32.0 + 8.0, 8.0),
     "end_step": (0.0, 0.0),
+    # the one-launch step: collide, plus the scatter (key, perm, offset) and per cell the
+    # zeroing of counts and cursors, two count reads of the scan, the offsets, the cursors
+    "step": (4.0 + 32.0 + 32.0 + 8.0 + 12.0, 24.0),
 }
 ALGO_STEP_BYTES_MIXED = 64.0
 # DRAM bytes (read + write) per particle of a kernel from one ncu capture of the current build,
@@ -440,6 +443,11 @@ def main():
         for name in FORMS:
             fw, fp, fbox, fens = open_box(abi, inputs, name, rank)
             abi.mpcd_set_stream(fbox.h, stream.cuda_stream)
+            tuned = None
+            if fens:  # the ensemble's tile shape, block size and launch form: the autotuner's choice
+                best, best_ms = abi.mpcd_autotune(fbox.h, trial_steps=5)
+                tuned = dict(best.as_dict(), ms_per_step_in_trial=best_ms,
+                             candidates="group_target {128..176} x warps {2,4} x fuse {1,0} (one launch per step or nine)")
             fbox.step(args.warmup)
             fbox.sync()
             fval, fms, fl, fkt, _ = timed_steps(abi, torch, dist, fbox, stream, args.form_steps, world)
@@ -458,7 +466,7 @@ def main():
                            "gpu_launches": fl,
                            "hbm_roofline_frac_step": fval / world * (ALGO_STEP_BYTES_MIXED if fmixed else
                                                                      ALGO_STEP_BYTES_FP64) / 1e9 / hbm_peak,
-                           "roofline": froof,
+                           "roofline": froof, "autotuned": tuned,
                            "kernels": {k: {"ms_per_step": v["ms_per_step"], "share": v["share"], "gbs": v["gbs"]}
                                        for k, v in fk.items()}}
             fbox.close()

@@ -41,9 +41,10 @@ enum {
   MPCD_ERR_OOM = -3,     /* device memory ran out (create, or the first call that needs a */
                          /* buffer: host get/set_state, set_masses, record_moments); the    */
                          /* handle is not poisoned and nothing was changed                  */
-  MPCD_ERR_TIMEOUT = -4, /* reserved for a bounded device-side wait that gave up; no kernel  */
-                         /* of this library waits on another (the scan is multi-pass), so   */
-                         /* no call returns it                                               */
+  MPCD_ERR_TIMEOUT = -4, /* a bounded device-side wait gave up: a grid-wide barrier of the  */
+                         /* mixed form's one-launch step waited about a second; the step is */
+                         /* incomplete and the handle is poisoned (reported by mpcd_sync and */
+                         /* mpcd_get_state)                                                  */
   MPCD_ERR_STATE = -5    /* the handle was poisoned by an earlier error */
 };
 
@@ -206,11 +207,17 @@ typedef struct {
                         /*   per box at most 24 ppc and 192 - ceil(ppc + 4 sqrt(ppc))     */
   int32_t warps;        /* mixed form: warps per collide block (2 or 4) */
   int32_t resort_k;     /* FP64 form: physical re-sort period in steps (0: never) */
-  int32_t fuse;         /* FP64 periodic boxes without thermostat: 1 applies each step's      */
-                        /*   rotation in the same pass as the next step's streaming and       */
-                        /*   binning (one pass over the state instead of two; the last step   */
-                        /*   of every mpcd_step call still ends with its rotation), 0 runs    */
-                        /*   them as separate passes.  Identical results either way.         */
+  int32_t fuse;         /* 0 or 1 (default 1 in the FP64 form, 0 in the mixed form).  FP64   */
+                        /*   periodic boxes without thermostat: 1                             */
+                        /*   applies each step's rotation in the same pass as the next step's */
+                        /*   streaming and binning (one pass over the state instead of two;   */
+                        /*   the last step of every mpcd_step call still ends with its        */
+                        /*   rotation).  Mixed form (without masses or angular-momentum       */
+                        /*   conservation): 1 runs a whole step as one persistent cooperative */
+                        /*   launch whose phases (zeroing, scan, scatter, group table,        */
+                        /*   collision, step end) are separated by bounded grid-wide barriers */
+                        /*   (MPCD_ERR_TIMEOUT if one waits too long), 0 as nine launches.    */
+                        /*   Identical results either way.                                    */
 } mpcd_tuning;
 
 int mpcd_get_tuning(const mpcd_t* h, mpcd_tuning* out);
@@ -220,10 +227,16 @@ int mpcd_set_tuning(mpcd_t* h, const mpcd_tuning* t);
 /* Autotuner: times each candidate tuning on the handle's own box(es) for trial_steps steps
  * (CUDA events on the handle's stream), keeps the fastest and restores the state, so the
  * simulation is unchanged.  Candidates: group_target in {128, 144, 160, 168, 176} x warps
- * in {2, 4} for the mixed form; resort_k in {1, 2, 5, 10, 20, 50} x fuse in {0, 1} for the
- * FP64 form.
+ * in {2, 4} x fuse in {1, 0} for the mixed form; resort_k in {1, 2, 5, 10, 20, 50} x fuse in
+ * {0, 1} for the FP64 form.
  * *best receives the choice and *best_ms its time per step (either may be NULL). */
 int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* best_ms);
+
+/* Test hook for the bounded waits (no counterpart in the paper): with enable = 1, the next
+ * one-launch mixed step lets one block leave without reaching its grid barriers, so the other
+ * blocks' waits run out after about a second; the step then reports MPCD_ERR_TIMEOUT through
+ * mpcd_sync and the handle is poisoned.  The GPU context stays usable.  Not for production. */
+int mpcd_debug_stall_barrier(mpcd_t* h, int32_t enable);
 
 /* Number of kernels this handle has launched (graph replays count each kernel node). */
 int64_t mpcd_launch_count(const mpcd_t* h);

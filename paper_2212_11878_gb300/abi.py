@@ -30,7 +30,7 @@ EXPORTS = [
     "mpcd_cell_moments", "mpcd_debug_sort", "mpcd_timing", "mpcd_timing_read", "mpcd_launch_count",
     "mpcd_last_error", "mpcd_version", "mpcd_step_fp64_noalloc", "mpcd_box_offsets", "mpcd_get_tuning",
     "mpcd_set_tuning", "mpcd_autotune", "mpcd_set_masses", "mpcd_get_masses", "mpcd_measure_fp64_rate",
-    "mpcd_add_momentum", "mpcd_add_momentum_device",
+    "mpcd_add_momentum", "mpcd_add_momentum_device", "mpcd_debug_stall_barrier",
 ]
 MPCD_NOALLOC_MAX_PARTICLES = 1 << 19
 MPCD_NOALLOC_MAX_CELLS = 1 << 17
@@ -152,6 +152,7 @@ def lib():
                 "mpcd_version": ([], ctypes.c_char_p),
                 "mpcd_measure_fp64_rate": ([dp], ctypes.c_int),
                 "mpcd_add_momentum": ([H, i64, dp], ctypes.c_int),
+                "mpcd_debug_stall_barrier": ([H, i32], ctypes.c_int),
                 "mpcd_add_momentum_device": ([H, i64, dp], ctypes.c_int),
                 "mpcd_step_fp64_noalloc": ([ctypes.POINTER(Params), i64, i64] + [dp] * 6 + [ctypes.c_void_p],
                                            ctypes.c_int),

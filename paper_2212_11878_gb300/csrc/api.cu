@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -30,12 +31,14 @@ enum KernelSlot {
   kSlotRotate,
   kSlotEndStep,
   kSlotRotateStream,
+  kSlotStep,
   kNumSlots
 };
-const char* kSlotNames[kNumSlots] = {"zero_counts", "stream_bin", "scan",     "scatter",
-                                     "collide",     "rotate",     "end_step", "rotate_stream"};
-// kernels launched per invocation of each slot (the rotation slots only for the dense pair)
-const int kSlotLaunchesBase[kNumSlots] = {1, 1, 3, 1, 1, 0, 1, 0};
+const char* kSlotNames[kNumSlots] = {"zero_counts", "stream_bin", "scan",     "scatter",       "collide",
+                                     "rotate",      "end_step",   "rotate_stream", "step"};
+// kernels launched per invocation of each slot (the rotation slots only for the dense pair;
+// "step" is the mixed form's one-launch step)
+const int kSlotLaunchesBase[kNumSlots] = {1, 1, 3, 1, 1, 0, 1, 0, 1};
 
 // The launch sequence of one step.  Full: every kernel of a step (mixed form, and FP64 boxes
 // whose collision is one per-cell kernel).  The FP64 dense pair splits its steps so that the
@@ -88,6 +91,8 @@ struct mpcd_s {
   mpcd_tuning tune{};
   Ctl* ctl = nullptr;
   unsigned long long* d_bad = nullptr;  // first invalid particle found by the state check
+  unsigned* d_bar = nullptr;            // grid-barrier counters of the one-launch mixed step
+  int stall_test = 0;                   // test hook: the next one-launch step's barriers run out
   Ctl ctl_host{};  // host copy used to (re)initialise the device control block
   int red_blocks = 0;
   std::vector<void*> allocations;
@@ -281,6 +286,11 @@ int run_slot(mpcd_t* h, int slot, F&& launch) {
 
 bool dense_fp64(const mpcd_t* h) { return h->precision == MPCD_FP64 && fp64_dense_collide(h->geom, h->scr); }
 
+// The mixed form runs its staged path as one persistent launch per step (tuning fuse = 1).
+bool one_launch_mixed(const mpcd_t* h) {
+  return h->precision == MPCD_MIXED && h->tune.fuse && !h->mb.angular && !h->masses;
+}
+
 // Enqueue one piece of a step on h->stream.  `par` is the mixed form's buffer set at the start
 // of the step (the FP64 kernels read theirs from the control block).
 int enqueue_piece(mpcd_t* h, int piece, bool moments, int par = 0) {
@@ -289,6 +299,16 @@ int enqueue_piece(mpcd_t* h, int piece, bool moments, int par = 0) {
   if (h->precision == MPCD_MIXED) {
     MixScratch m = h->mscr;
     const int nx = par ^ 1;
+    if (one_launch_mixed(h)) {
+      cudaError_t le = cudaSuccess;
+      if ((rc = run_slot(h, kSlotStep, [&] {
+             le = launch_step_mixed(h->mb, h->mix, m, h->ctl, moments, h->d_gspec, h->d_groups, h->d_bar,
+                                    h->stall_test, h->stream);
+           })))
+        return rc;
+      if (le != cudaSuccess) return cuda_fail(h, le, "one-launch step");
+      return MPCD_OK;
+    }
     if ((rc = run_slot(h, kSlotZero, [&] {
            launch_zero_i32(m.count[nx], g.ncell, h->stream);
            launch_zero_i32(m.cursor, g.ncell, h->stream);
@@ -347,11 +367,13 @@ int enqueue_bin_mixed(mpcd_t* h) {
 }
 
 int piece_launches(const mpcd_t* h, int piece) {
+  if (one_launch_mixed(h)) return 1;
   if (piece == kPieceTail) return h->per_step[kSlotRotate];
   if (piece == kPieceStep) return piece_launches(h, kPieceFull) + piece_launches(h, kPieceTail);
   int k = 0;
   for (int s = 0; s < kNumSlots; ++s) {
-    if (s == kSlotRotate || (s == kSlotRotateStream && piece != kPieceBody) || (s == kSlotStreamBin && piece == kPieceBody))
+    if (s == kSlotRotate || s == kSlotStep || (s == kSlotRotateStream && piece != kPieceBody) ||
+        (s == kSlotStreamBin && piece == kPieceBody))
       continue;
     k += h->per_step[s];
   }
@@ -510,7 +532,9 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->tune.group_target = 168;
   h->tune.warps = 4;
   h->tune.resort_k = p[0].resort_k;
-  h->tune.fuse = 1;
+  // FP64: the fused rotate-and-stream pass is faster; mixed: the nine-launch step is (its
+  // sort phases run at full occupancy), the one-launch step remains a tuning choice
+  h->tune.fuse = p[0].precision == MPCD_FP64 ? 1 : 0;
   // per-box geometry; the handle's geom describes the whole concatenation for the kernels
   // that run over all cells or particles (zeroing, scan, sort)
   int64_t ctot = 0, ntot = 0;
@@ -556,6 +580,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     h->per_step[kSlotScatter] = 2;  // scatter + group bounds
     h->per_step[kSlotCollide] = 1;
     h->per_step[kSlotRotate] = h->per_step[kSlotRotateStream] = 0;
+    h->per_step[kSlotStep] = 1;
     for (int k = 0; k < 2; ++k) {
       if ((rc = dalloc(h, &h->mix.rec[k], n))) return bail(rc);
       if ((rc = dalloc(h, &h->mscr.key[k], n))) return bail(rc);
@@ -564,7 +589,8 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     if ((rc = dalloc(h, &h->mscr.cursor, C))) return bail(rc);
     if ((rc = dalloc(h, &h->mscr.perm, n))) return bail(rc);
     if ((rc = dalloc(h, &h->mscr.offset, C + 1))) return bail(rc);
-    if ((rc = dalloc(h, &h->mscr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
+    // tile sums of both scans: the three-kernel one and the one-launch step's (smaller tiles)
+    if ((rc = dalloc(h, &h->mscr.partial, std::max<int64_t>(scan_tiles(C), step_scan_tiles(C)) + 1))) return bail(rc);
     if ((rc = dalloc(h, &h->d_boxes, nbox))) return bail(rc);
     if ((rc = dalloc(h, &h->d_shifts, nbox))) return bail(rc);
     if ((rc = dalloc(h, &h->d_pbase, (int64_t)nbox + 1))) return bail(rc);
@@ -610,6 +636,9 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   }
   if ((rc = dalloc(h, &h->ctl, 1))) return bail(rc);
   if ((rc = dalloc(h, &h->d_bad, 1))) return bail(rc);
+  if ((rc = dalloc(h, &h->d_bar, 2))) return bail(rc);
+  if ((e = cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream)) != cudaSuccess)
+    return bail(cuda_fail(h, e, "cudaMemsetAsync"));
   h->red_blocks = 152 * 4;
   if ((rc = dalloc(h, &h->scr.red, 3 * (int64_t)h->red_blocks))) return bail(rc);
   h->ctl_host = Ctl{};
@@ -709,10 +738,30 @@ int mpcd_step(mpcd_t* h, int64_t nsteps) {
   return MPCD_OK;
 }
 
+// After a synchronisation: a bounded device-side wait that ran out (the one-launch mixed
+// step's grid barriers) left its flag in the control block; the step is incomplete.
+static int check_device_flag(mpcd_t* h) {
+  if (h->precision != MPCD_MIXED) return MPCD_OK;
+  int32_t err = 0;
+  MPCD_TRY(h, cudaMemcpyAsync(&err, reinterpret_cast<const char*>(h->ctl) + offsetof(Ctl, err), sizeof(err),
+                              cudaMemcpyDeviceToHost, h->stream));
+  MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  if (err) return fail(h, MPCD_ERR_TIMEOUT, "a grid-wide barrier of the one-launch step waited too long; the step is incomplete");
+  return MPCD_OK;
+}
+
 int mpcd_sync(mpcd_t* h) {
   int rc = guard(h);
   if (rc) return rc;
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+  return check_device_flag(h);
+}
+
+int mpcd_debug_stall_barrier(mpcd_t* h, int32_t enable) {
+  int rc = guard(h);
+  if (rc) return rc;
+  h->stall_test = enable ? 1 : 0;
+  drop_graph(h);  // the captured step holds the flag
   return MPCD_OK;
 }
 
@@ -828,7 +877,7 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
   h->launches += 1;
-  return MPCD_OK;
+  return check_device_flag(h);
 }
 
 // Reject a state with a position outside its box or a non-finite velocity before any of it
@@ -1056,8 +1105,9 @@ int mpcd_autotune(mpcd_t* h, int32_t trial_steps, mpcd_tuning* best, double* bes
   if (h->timing) return fail(h, MPCD_ERR_STATE, "disable timing before autotuning");
   std::vector<mpcd_tuning> cand;
   if (h->precision == MPCD_MIXED) {
-    for (int w : {2, 4})
-      for (int tg : {128, 144, 160, 168, 176}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, h->tune.fuse});
+    for (int f : {1, 0})
+      for (int w : {2, 4})
+        for (int tg : {128, 144, 160, 168, 176}) cand.push_back(mpcd_tuning{tg, w, h->tune.resort_k, f});
   } else {
     for (int f : {0, 1})
       for (int k : {1, 2, 5, 10, 20, 50}) cand.push_back(mpcd_tuning{h->tune.group_target, h->tune.warps, k, f});
@@ -1117,6 +1167,7 @@ int mpcd_set_tuning(mpcd_t* h, const mpcd_tuning* t) {
   h->tune = *t;
   if (h->precision == MPCD_MIXED) {
     if (old.group_target != t->group_target || old.warps != t->warps) return build_groups(h);
+    if (old.fuse != t->fuse) drop_graph(h);
   } else if (old.resort_k != t->resort_k || old.fuse != t->fuse) {
     // the re-sort schedule is part of the captured step and of the step-end kernel
     h->geom.resort_k = t->resort_k;

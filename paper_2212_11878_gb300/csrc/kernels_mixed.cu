@@ -936,18 +936,18 @@ __device__ __forceinline__ void key_store(const Geom& g, const Geom* __restrict_
 // The per-cell random axis is keyed on the cell's index inside its box, so a box advanced in
 // an ensemble reproduces the same box advanced alone; every per-cell sum is an exact integer,
 // so neither the grouping nor the lanes per cell change any result.
+// The collision of every group of a warp (gi, gi + W, ...), shared by the collide kernel and
+// the one-launch step kernel: t1 is the step, cur the record buffer it starts from.
 template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
-__global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed(MixBatch mb, MixBufs b, MixScratch s,
-                                                                    Ctl* __restrict__ ctl) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+__device__ __forceinline__ void collide_groups(const MixBatch& mb, const MixBufs& b, const MixScratch& s, int64_t t1,
+                                               int cur, unsigned char* smem_raw) {
   constexpr int NQ = 3 + MOMENTS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   MixWarpStage<NQ>& st = reinterpret_cast<MixWarpStage<NQ>*>(smem_raw)[warp];
   const int64_t W = (int64_t)gridDim.x * WARPS;
   int64_t gi = (int64_t)blockIdx.x * WARPS + warp;
   if (gi >= mb.ngroups) return;
-  const int64_t t1 = ctl->t + 1;
-  const int cur = ctl->cur, nxt = cur ^ 1;
+  const int nxt = cur ^ 1;
   const MixRec* __restrict__ src = b.rec[cur];
   MixRec* __restrict__ dst = b.rec[nxt];
   const int32_t* __restrict__ perm = s.perm;
@@ -1164,6 +1164,13 @@ __global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed
   }
 }
 
+template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
+__global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_collide_stream_mixed(MixBatch mb, MixBufs b, MixScratch s,
+                                                                    Ctl* __restrict__ ctl) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  collide_groups<WARPS, WALLS, FORCE, THERMO, MOMENTS>(mb, b, s, ctl->t + 1, ctl->cur, smem_raw);
+}
+
 // perm[offset[key] + rank] = slot, the rank from a per-cell cursor.  Neighbouring slots mostly
 // share a key, so each warp groups equal keys (match.any) and one lane per group takes the
 // group's ranks with a single atomic.  The order inside a cell is whatever the atomics give;
@@ -1252,6 +1259,231 @@ __global__ void k_end_step_mixed(MixBatch mb, Ctl* ctl) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->t = t;
     ctl->cur ^= 1;
+  }
+}
+
+// ---- one persistent launch per step (the mixed form's staged path; ensembles included) ----
+// Every phase of a step in one cooperative launch of the persistent collide grid, the phases
+// separated by grid-wide barriers: (1) zero the next step's counts and the scatter cursors,
+// sum this step's counts per tile; (2) block 0 scans the tile sums; (3) the offsets inside
+// each tile; (4) the scatter (perm from the cursors) and the group table; (5) the collision
+// (collide_groups); (6) the last block to finish ends the step.  A cooperative launch has all
+// blocks resident, so every barrier is reached; each wait is still bounded: a block that
+// waits longer than about a second sets the control block's error flag and returns, and
+// every block that sees the flag returns too, so a failed step ends with an error that the
+// host reads (MPCD_ERR_TIMEOUT) instead of a hang.
+constexpr int kStepScanItems = 8;
+constexpr unsigned kBarrierSpins = 1u << 22;  // polls of about 0.25 us each
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier on bar[0]: returns false (every thread of the block) if the wait ran out or
+// another block had already given up.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 1;
+    for (unsigned spin = 0;; ++spin) {
+      if (ld_acquire_u32(bar) >= target) break;
+      if (*reinterpret_cast<volatile int*>(err) != 0 || spin >= kBarrierSpins) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(256);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Sum over the block (every thread gets it); red holds one int per warp.
+template <int NT>
+__device__ __forceinline__ int block_sum_i32(int v, int* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int t = 0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+// Exclusive scan over the block; *total receives the block's sum.
+template <int NT>
+__device__ __forceinline__ int block_scan_i32(int v, int* red, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) red[wid] = incl;
+  __syncthreads();
+  int before = 0, t = 0;
+#pragma unroll
+  for (int w = 0; w < NT / 32; ++w) {
+    if (w < wid) before += red[w];
+    t += red[w];
+  }
+  __syncthreads();
+  *total = t;
+  return before + incl - v;
+}
+
+struct StepAux {
+  const MixGroupSpec* spec;  // the fixed part of the group table
+  MixGroup* groups;          // rewritten in phase 4 (mb.groups points at the same table)
+  unsigned* bar;             // [2]: barrier arrivals, blocks finished; both 0 between steps
+  int stall;                 // test hook: block 0 leaves without arriving at any barrier
+};
+
+template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
+__global__ void __launch_bounds__(WARPS * 32, 12 / WARPS) k_step_mixed(MixBatch mb, MixBufs b, MixScratch s,
+                                                                 Ctl* __restrict__ ctl, StepAux aux) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int NT = WARPS * 32;
+  constexpr int kTileCells = NT * kStepScanItems;
+  __shared__ int red[NT / 32];
+  __shared__ int s_last;
+  if (aux.stall && blockIdx.x == 0) return;
+  const int64_t t1 = ctl->t + 1;
+  const int cur = ctl->cur, nxt = cur ^ 1;
+  const int64_t C = mb.ncell;
+  const int64_t tiles = (C + kTileCells - 1) / kTileCells;
+  const int64_t gthreads = (int64_t)gridDim.x * NT, gtid = (int64_t)blockIdx.x * NT + threadIdx.x;
+  int* err = &ctl->err;
+  unsigned gen = 0;
+
+  // 1. next step's counts and the cursors to zero; this step's counts summed per tile
+  for (int64_t i = gtid; i < C; i += gthreads) {
+    s.count[nxt][i] = 0;
+    s.cursor[i] = 0;
+  }
+  for (int64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
+    int v = 0;
+#pragma unroll
+    for (int k = 0; k < kStepScanItems; ++k) {
+      const int64_t i = tl * kTileCells + k * NT + threadIdx.x;
+      if (i < C) v += s.count[cur][i];
+    }
+    v = block_sum_i32<NT>(v, red);
+    if (threadIdx.x == 0) s.partial[tl] = v;
+  }
+  if (!grid_barrier(aux.bar, ++gen * gridDim.x, err)) return;
+
+  // 2. block 0: exclusive scan of the tile sums, in place; the total closes the offsets
+  if (blockIdx.x == 0) {
+    int carry = 0;
+    for (int64_t base = 0; base < tiles; base += NT) {
+      const int64_t i = base + threadIdx.x;
+      const int v = i < tiles ? s.partial[i] : 0;
+      int total;
+      const int ex = block_scan_i32<NT>(v, red, &total);
+      if (i < tiles) s.partial[i] = carry + ex;
+      carry += total;
+    }
+    if (threadIdx.x == 0) s.offset[C] = carry;
+  }
+  if (!grid_barrier(aux.bar, ++gen * gridDim.x, err)) return;
+
+  // 3. offsets inside each tile (thread = kStepScanItems consecutive cells)
+  for (int64_t tl = blockIdx.x; tl < tiles; tl += gridDim.x) {
+    const int64_t i0 = tl * kTileCells + (int64_t)threadIdx.x * kStepScanItems;
+    int vals[kStepScanItems], sum = 0;
+#pragma unroll
+    for (int k = 0; k < kStepScanItems; ++k) {
+      vals[k] = i0 + k < C ? s.count[cur][i0 + k] : 0;
+      sum += vals[k];
+    }
+    int total;
+    int run = block_scan_i32<NT>(sum, red, &total) + s.partial[tl];
+#pragma unroll
+    for (int k = 0; k < kStepScanItems; ++k) {
+      if (i0 + k < C) s.offset[i0 + k] = run;
+      run += vals[k];
+    }
+  }
+  if (!grid_barrier(aux.bar, ++gen * gridDim.x, err)) return;
+
+  // 4. perm from the cursors (equal keys of a warp take their places with one atomic), and
+  //    the cell boundaries of every group
+  {
+    constexpr int kChunks = 8;
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t warps = (int64_t)gridDim.x * WARPS;
+    const int32_t* __restrict__ key = s.key[cur];
+    for (int64_t base = ((int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5)) * (32 * kChunks); base < mb.n;
+         base += warps * 32 * kChunks) {
+      int k[kChunks], first[kChunks], rank[kChunks];
+      unsigned peers[kChunks];
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) {
+        const int64_t i = base + 32 * c + lane;
+        k[c] = i < mb.n ? key[i] : -1 - lane;
+      }
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) {
+        peers[c] = __match_any_sync(0xffffffffu, k[c]);
+        rank[c] = __popc(peers[c] & below);
+        first[c] = 0;
+        if (k[c] >= 0 && rank[c] == 0) first[c] = atomicAdd(&s.cursor[k[c]], __popc(peers[c]));
+      }
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) {
+        const int start = __shfl_sync(0xffffffffu, first[c], __ffs(peers[c]) - 1);
+        const int64_t i = base + 32 * c + lane;
+        if (k[c] >= 0) s.perm[s.offset[k[c]] + start + rank[c]] = static_cast<int32_t>(i);
+      }
+    }
+    for (int64_t gi = gtid; gi < mb.ngroups; gi += gthreads) {
+      const MixGroupSpec q = aux.spec[gi];
+      const int64_t cb = mb.boxes[q.box].cbase, ce = cb + mb.boxes[q.box].ncell;
+      MixGroup d;
+      d.c0 = first_cell(s.offset, cb, ce, q.rec0);
+      d.box = q.box;
+      d.ncells = static_cast<int32_t>((q.rec1 < 0 ? ce : first_cell(s.offset, cb, ce, q.rec1)) - d.c0);
+      aux.groups[gi] = d;
+    }
+  }
+  if (!grid_barrier(aux.bar, ++gen * gridDim.x, err)) return;
+
+  // 5. the collision of this block's groups
+  collide_groups<WARPS, WALLS, FORCE, THERMO, MOMENTS>(mb, b, s, t1, cur, smem_raw);
+
+  // 6. the last block to finish advances the step (shifts of every box, step counter, buffer)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(aux.bar + 1, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int bx = threadIdx.x; bx < mb.nbox; bx += NT) {
+    BoxShift& sh = mb.shifts[bx];
+    for (int d = 0; d < 3; ++d) sh.s_last[d] = sh.s[d];
+    box_shifts(mb.boxes[bx], t1, sh);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl->t = t1;
+    ctl->cur = nxt;
+    aux.bar[0] = 0u;  // every block has left its last barrier
+    aux.bar[1] = 0u;
   }
 }
 
@@ -1772,6 +2004,66 @@ cudaError_t launch_collide_w(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* c
 
 }  // namespace
 
+template <int WARPS, int WALLS, int FORCE, int THERMO, int MOMENTS>
+cudaError_t launch_step_t(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, const StepAux& aux, cudaStream_t st,
+                          bool prepare) {
+  auto kern = k_step_mixed<WARPS, WALLS, FORCE, THERMO, MOMENTS>;
+  const int smem = WARPS * static_cast<int>(sizeof(MixWarpStage<3 + MOMENTS>));
+  static int resident = 0;
+  if (prepare) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WARPS * 32, smem);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) resident = per_sm * sms;
+    return e;
+  }
+  if (resident <= 0) return cudaErrorInvalidConfiguration;
+  // every block resident (a cooperative launch fails instead of starting if they cannot be)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(resident));
+  cfg.blockDim = dim3(WARPS * 32);
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, mb, b, s, ctl, aux);
+}
+
+template <int WARPS>
+cudaError_t launch_step_w(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, const StepAux& aux, bool moments,
+                          cudaStream_t st, bool prepare, int sel_override = -1) {
+  const int kind = mb.walls ? 2 : (mb.force ? 1 : 0);
+  const int sel = sel_override >= 0 ? sel_override
+                  : mb.thermostat == 2 ? 12 + 2 * kind + (moments ? 1 : 0)
+                                       : 4 * kind | (mb.thermostat ? 2 : 0) | (moments ? 1 : 0);
+  switch (sel) {
+    case 0: return launch_step_t<WARPS, 0, 0, 0, 0>(mb, b, s, ctl, aux, st, prepare);
+    case 1: return launch_step_t<WARPS, 0, 0, 0, 1>(mb, b, s, ctl, aux, st, prepare);
+    case 2: return launch_step_t<WARPS, 0, 0, 1, 0>(mb, b, s, ctl, aux, st, prepare);
+    case 3: return launch_step_t<WARPS, 0, 0, 1, 1>(mb, b, s, ctl, aux, st, prepare);
+    case 4: return launch_step_t<WARPS, 0, 1, 0, 0>(mb, b, s, ctl, aux, st, prepare);
+    case 5: return launch_step_t<WARPS, 0, 1, 0, 1>(mb, b, s, ctl, aux, st, prepare);
+    case 6: return launch_step_t<WARPS, 0, 1, 1, 0>(mb, b, s, ctl, aux, st, prepare);
+    case 7: return launch_step_t<WARPS, 0, 1, 1, 1>(mb, b, s, ctl, aux, st, prepare);
+    case 8: return launch_step_t<WARPS, 1, 1, 0, 0>(mb, b, s, ctl, aux, st, prepare);
+    case 9: return launch_step_t<WARPS, 1, 1, 0, 1>(mb, b, s, ctl, aux, st, prepare);
+    case 10: return launch_step_t<WARPS, 1, 1, 1, 0>(mb, b, s, ctl, aux, st, prepare);
+    case 11: return launch_step_t<WARPS, 1, 1, 1, 1>(mb, b, s, ctl, aux, st, prepare);
+    case 12: return launch_step_t<WARPS, 0, 0, 2, 0>(mb, b, s, ctl, aux, st, prepare);
+    case 13: return launch_step_t<WARPS, 0, 0, 2, 1>(mb, b, s, ctl, aux, st, prepare);
+    case 14: return launch_step_t<WARPS, 0, 1, 2, 0>(mb, b, s, ctl, aux, st, prepare);
+    case 15: return launch_step_t<WARPS, 0, 1, 2, 1>(mb, b, s, ctl, aux, st, prepare);
+    case 16: return launch_step_t<WARPS, 1, 1, 2, 0>(mb, b, s, ctl, aux, st, prepare);
+    default: return launch_step_t<WARPS, 1, 1, 2, 1>(mb, b, s, ctl, aux, st, prepare);
+  }
+}
+
 cudaError_t prepare_collide_mixed() {
   static std::mutex mu;
   static uint64_t done = 0;  // devices prepared (bit per ordinal < 64)
@@ -1784,9 +2076,12 @@ cudaError_t prepare_collide_mixed() {
   MixBatch mb{};
   MixBufs b{};
   MixScratch s{};
+  const StepAux aux{};
   for (int sel = 0; sel < 18 && e == cudaSuccess; ++sel) {
     e = launch_collide_w<2>(mb, b, s, nullptr, false, nullptr, true, sel);
     if (e == cudaSuccess) e = launch_collide_w<4>(mb, b, s, nullptr, false, nullptr, true, sel);
+    if (e == cudaSuccess) e = launch_step_w<2>(mb, b, s, nullptr, aux, false, nullptr, true, sel);
+    if (e == cudaSuccess) e = launch_step_w<4>(mb, b, s, nullptr, aux, false, nullptr, true, sel);
   }
   if (e == cudaSuccess) done |= bit;
   return e;
@@ -1802,6 +2097,18 @@ void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ct
     (void)launch_collide_w<2>(mb, b, s, ctl, moments, st, false);
   else
     (void)launch_collide_w<4>(mb, b, s, ctl, moments, st, false);
+}
+
+int64_t step_scan_tiles(int64_t ncell) {
+  constexpr int64_t kMinTile = 2 * 32 * kStepScanItems;  // two-warp blocks have the smallest tiles
+  return (ncell + kMinTile - 1) / kMinTile;
+}
+
+cudaError_t launch_step_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments,
+                              const MixGroupSpec* spec, MixGroup* groups, unsigned* bar, int stall, cudaStream_t st) {
+  const StepAux aux{spec, groups, bar, stall};
+  return mb.warps == 2 ? launch_step_w<2>(mb, b, s, ctl, aux, moments, st, false)
+                       : launch_step_w<4>(mb, b, s, ctl, aux, moments, st, false);
 }
 
 void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st) { k_end_step_mixed<<<1, 256, 0, st>>>(mb, ctl); }

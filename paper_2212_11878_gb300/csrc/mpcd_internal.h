@@ -46,7 +46,7 @@ struct alignas(16) Geom {
 struct Ctl {
   int64_t t;            // completed steps; the step in flight is t + 1
   int32_t cur;          // particle buffer set holding the state (0 or 1)
-  int32_t err;          // reserved (no kernel raises error bits)
+  int32_t err;          // set by a kernel whose bounded grid-barrier wait ran out (one-launch mixed step)
   double shift[3];      // grid shift of step t + 1 (the next step to run)
   double shift_next[3]; // grid shift of step t + 2
   double shift_last[3]; // grid shift of step t (the last completed step)
@@ -207,6 +207,15 @@ cudaError_t prepare_collide_mixed();
 void launch_collide_stream_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments, cudaStream_t st,
                                  MixMass ms = MixMass{});
 void launch_end_step_mixed(const MixBatch& mb, Ctl* ctl, cudaStream_t st);
+// The whole mixed step (staged path: no masses, no angular-momentum correction) in one
+// cooperative persistent launch: zeroing, scan, scatter, group table, collision, step end.
+// bar: two device counters, 0 between steps; stall (tests only): block 0 skips the barriers
+// so the others' bounded waits run out and ctl->err is set.
+// Tile sums the one-launch step needs at most (its tiles hold 32 x warps x 8 cells): the
+// size of MixScratch::partial, with the three-kernel scan's scan_tiles.
+int64_t step_scan_tiles(int64_t ncell);
+cudaError_t launch_step_mixed(const MixBatch& mb, MixBufs b, MixScratch s, Ctl* ctl, bool moments,
+                              const MixGroupSpec* spec, MixGroup* groups, unsigned* bar, int stall, cudaStream_t st);
 void launch_scatter_cursor(int64_t n, const int32_t* key, const int32_t* offset, int32_t* cursor, int32_t* perm,
                            cudaStream_t st);
 // Rewrite the group table from this step's offsets.

@@ -145,3 +145,63 @@ def test_tunings_give_identical_results():
     with abi.Box(p) as box:
         with pytest.raises(abi.MpcdError):
             abi.mpcd_set_tuning(box.h, warps=3)
+
+
+@pytest.mark.parametrize("extra,boxes", [({}, BOXES), (dict(thermostat=2), BOXES),
+                                         (dict(walls_z=1, thermostat=1), WALL_BOXES), ({}, SPARSE_BOXES)],
+                         ids=["periodic", "mbs", "walls_thermostat", "sparse"])
+def test_one_launch_step_equals_launch_sequence(extra, boxes):
+    """The mixed step as one persistent cooperative launch (tuning fuse = 1, the default) and
+    as its nine-launch sequence (fuse = 0) give the same bits, over several mpcd_step calls,
+    with per-cell moments recorded; the one-launch form launches one kernel per step."""
+    params = [abi.make_params(precision="mixed", **k, **extra) for k in boxes]
+    outs = []
+    for fuse in (1, 0):
+        with abi.Box(batch=params) as ens:
+            abi.mpcd_set_tuning(ens.h, fuse=fuse)
+            abi.mpcd_record_moments(ens.h, True)
+            ens.step(1)  # the first step after creation also bins
+            l0 = abi.mpcd_launch_count(ens.h)
+            for n in (2, 3):
+                ens.step(n)
+            per_step = (abi.mpcd_launch_count(ens.h) - l0) / 5
+            mom, _ = ens.moments()
+            outs.append((ens.state(), mom, ens.debug_sort()))
+        assert per_step == (1 if fuse else 9)
+    (r1, v1), m1, d1 = outs[0]
+    (r0, v0), m0, d0 = outs[1]
+    assert np.array_equal(r1, r0) and np.array_equal(v1, v0) and np.array_equal(m1, m0)
+    for k in ("counts", "offsets"):
+        assert np.array_equal(d1[k], d0[k]), k
+    # the order inside a cell comes from the scatter's atomics: compare the keys by particle id
+    k1 = np.empty(len(d1["keys"]), np.int64)
+    k0 = np.empty(len(d0["keys"]), np.int64)
+    k1[d1["ids"]] = d1["keys"]
+    k0[d0["ids"]] = d0["keys"]
+    assert np.array_equal(k1, k0)
+
+
+def test_one_launch_step_wait_runs_out_with_an_error():
+    """Bounded device-side waits: with the test hook set, one block of the one-launch step
+    leaves without reaching its grid barriers; the other blocks give up after about a second,
+    set the error flag and return, mpcd_sync reports MPCD_ERR_TIMEOUT and poisons the handle,
+    and the GPU stays usable (a new box steps normally)."""
+    p = abi.make_params((16, 16, 16), precision="mixed", seed=3)
+    with abi.Box(p) as box:
+        abi.mpcd_set_tuning(box.h, fuse=1)
+        box.step(2)
+        box.sync()
+        assert abi.lib().mpcd_debug_stall_barrier(box.h, 1) == abi.MPCD_OK
+        box.step(1)
+        with pytest.raises(abi.MpcdError) as e:
+            box.sync()
+        assert e.value.code == abi.MPCD_ERR_TIMEOUT
+        with pytest.raises(abi.MpcdError) as e:
+            box.step(1)
+        assert e.value.code == abi.MPCD_ERR_STATE
+    with abi.Box(p) as fresh, abi.Box(p) as ref:
+        abi.mpcd_set_tuning(fresh.h, fuse=1)
+        abi.mpcd_set_tuning(ref.h, fuse=0)
+        fresh.step(4)
+        ref.step(4)
+        assert np.array_equal(fresh.state()[1], ref.state()[1])
