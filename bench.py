@@ -54,9 +54,11 @@ FP64_BYTES = {
 }
 FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # rotate on re-sort steps also moves r and the ids
 FP64_RESORT_EXTRA_FUSED = 4.0 + 8.0     # the fused pass moves r anyway; + the ids and the destination
-# FP64 instructions (DFMA, DADD, DMUL) per launch, as (per particle, per cell): the FP64 form
-# is bound by GB300's FP64 pipe (2 instructions per clock per SM), not by HBM.
-FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 71.0), "rotate": (9.0, 0.0), "rotate_stream": (15.0, 0.0)}
+# FP64-pipe instructions (DFMA, DADD, DSUB, DMUL) per launch, as (per particle, per cell), on
+# GB300's narrow FP64 pipe (2 per clock per SM): streaming 3 DFMA + the 3 DSUB of r - s; the
+# frame applied in float-float arithmetic joins each component with one DADD; cell_frame 71
+# per cell (sums' rounding, u, axis, frame).
+FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 71.0), "rotate": (3.0, 0.0), "rotate_stream": (9.0, 0.0)}
 SMS, FP64_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_GOPS = SMS * FP64_PER_CLK * SM_MAX_MHZ / 1e3   # 629.3 G FP64 instructions/s
 ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step
@@ -355,14 +357,25 @@ def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True, fp64_probe
     dom = max(fp64k, key=lambda k: kernels[k]["ms_per_step"])
     d = kernels[dom]
     tr = NCU_TRAFFIC.get(("fp64", dom))
-    return {"kernel": dom, "bound": "alu", "achieved": d["fp64_gops"], "peak": FP64_PEAK_GOPS,
-            "unit": "G FP64 instructions/s", "frac": d["fp64_gops"] / FP64_PEAK_GOPS,
-            "traffic": tr[0] * n if tr else None, "traffic_source": tr[1] if tr else None,
-            "peak_source": "derived: %d SMs x %d FP64 instructions/clock x %.0f MHz" % (SMS, FP64_PER_CLK, SM_MAX_MHZ),
-            "algo_fp64_ops_per_launch": d["fp64_ops_per_invocation"],
-            "peak_measured": fp64_probe, "frac_of_measured": d["fp64_gops"] / fp64_probe if fp64_probe else None,
-            "peak_measured_source": "mpcd_measure_fp64_rate: chains of independent DFMAs on every SM, this run",
-            "hbm_gbs": d["gbs"], "hbm_frac": d["gbs"] / hbm_peak}
+    alu_frac, hbm_frac = d["fp64_gops"] / FP64_PEAK_GOPS, d["gbs"] / hbm_peak
+    alu = {"fp64_achieved": d["fp64_gops"], "fp64_peak": FP64_PEAK_GOPS, "fp64_unit": "G FP64 instructions/s",
+           "fp64_frac": alu_frac,
+           "fp64_peak_source": "derived: %d SMs x %d FP64 instructions/clock x %.0f MHz" % (SMS, FP64_PER_CLK,
+                                                                                              SM_MAX_MHZ),
+           "algo_fp64_ops_per_launch": d["fp64_ops_per_invocation"],
+           "fp64_peak_measured": fp64_probe, "fp64_frac_of_measured": d["fp64_gops"] / fp64_probe if fp64_probe else None,
+           "fp64_peak_measured_source": "mpcd_measure_fp64_rate: chains of independent DFMAs on every SM, this run"}
+    # the bound is the nearer of the two ceilings (HBM bytes or FP64-pipe instructions)
+    if hbm_frac >= alu_frac:
+        out = {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
+               "frac": hbm_frac, "peak_source": peak_src + " (hbm_gbs)",
+               "algo_bytes_per_launch": d["algo_bytes_per_invocation"]}
+    else:
+        out = {"kernel": dom, "bound": "alu", "achieved": d["fp64_gops"], "peak": FP64_PEAK_GOPS,
+               "unit": "G FP64 instructions/s", "frac": alu_frac, "peak_source": alu["fp64_peak_source"],
+               "algo_bytes_per_launch": d["algo_bytes_per_invocation"]}
+    out.update(traffic=tr[0] * n if tr else None, traffic_source=tr[1] if tr else None, **alu)
+    return out
 
 
 def main():
