@@ -900,18 +900,20 @@ int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const doubl
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!r_dev || !v_dev || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
   if ((rc = check_state(h, r_dev, v_dev))) return rc;
-  if (h->precision == MPCD_MIXED)
+  h->cur = 0;
+  if (h->precision == MPCD_MIXED) {
     launch_set_state_mixed(h->mb, h->mix, r_dev, v_dev, h->stream);
-  else
-    launch_set_state_fp64(h->geom, h->f64, r_dev, v_dev, h->stream);
+    if (h->masses)  // the new records are in particle-id order
+      launch_gather_masses_mixed(n, h->mix.rec[0], h->mass_buf[2], h->mix_mass_buf[0], h->stream);
+  } else if (n > 0) {
+    // straight into cell order (the initial sort, R25) in buffer set 1, masses along
+    h->launches += launch_set_state_sorted_fp64(h->geom, h->f64, h->scr, r_dev, v_dev,
+                                                h->masses ? h->mass_buf[2] : nullptr,
+                                                h->masses ? h->mass_buf[1] : nullptr, h->stream);
+    h->cur = 1;
+  }
   MPCD_TRY(h, cudaGetLastError());
-  if (h->masses && h->precision == MPCD_MIXED)  // the new records are in particle-id order
-    launch_gather_masses_mixed(n, h->mix.rec[0], h->mass_buf[2], h->mix_mass_buf[0], h->stream);
-  else if (h->masses)
-    MPCD_TRY(h, cudaMemcpyAsync(h->mass_buf[0], h->mass_buf[2], sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice,
-                                h->stream));
   h->mixed_keys_valid = false;
-  if ((rc = presort_fp64(h))) return rc;
   h->ctl_host = Ctl{};
   h->ctl_host.t = t;
   h->ctl_host.cur = h->cur;

@@ -942,18 +942,6 @@ __global__ void __launch_bounds__(kThreads) k_get_state_fp64(int64_t n, const do
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_set_state_fp64(int64_t n, const double* __restrict__ r,
-                                                             const double* __restrict__ v, Fp64Bufs b) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      b.r[0][d][i] = r[3 * i + d];
-      b.v[0][d][i] = v[3 * i + d];
-    }
-    b.id[0][i] = static_cast<int32_t>(i);
-  }
-}
-
 // ---- initial cell order (create / set_state) ----
 // Cell key of each current position on the unshifted grid and its arrival rank; positions
 // are only read.
@@ -997,7 +985,52 @@ __global__ void __launch_bounds__(kThreads) k_add_momentum_fp64(Geom g, Fp64Bufs
   }
 }
 
+// The same initial sort straight from a state in particle-id order as N x 3 arrays (a host
+// upload): keys of the unshifted cells, then one gather into buffer set 1 in cell order.
+template <int POW2A>
+__global__ void __launch_bounds__(kThreads) k_presort_keys_aos(Geom g, const double* __restrict__ r, Scratch s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int cx = cell_coord<POW2A>(r[3 * i + 0], 0.0, g, 0);
+    const int cy = cell_coord<POW2A>(r[3 * i + 1], 0.0, g, 1);
+    const int cz = cell_coord<POW2A>(r[3 * i + 2], 0.0, g, 2);
+    const int k = cx + g.L[0] * (cy + g.L[1] * cz);
+    s.key[i] = k;
+    s.rank[i] = atomicAdd(&s.count[k], 1);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gather_state_aos(int64_t n, const int32_t* __restrict__ perm,
+                                                              const double* __restrict__ r, const double* __restrict__ v,
+                                                              Fp64Bufs b, const double* __restrict__ m_by_id,
+                                                              double* __restrict__ m_dst) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = perm[j];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      b.r[1][d][j] = r[3 * i + d];
+      b.v[1][d][j] = v[3 * i + d];
+    }
+    b.id[1][j] = static_cast<int32_t>(i);
+    if (m_by_id) m_dst[j] = m_by_id[i];
+  }
+}
+
 }  // namespace
+
+int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
+                                 const double* m_by_id, double* m_dst, cudaStream_t st) {
+  s.cursor = nullptr;  // ranks from the counting atomics
+  launch_zero_i32(s.count, g.ncell, st);
+  if (g.pow2a)
+    k_presort_keys_aos<1><<<grid_for(g.n), kThreads, 0, st>>>(g, r, s);
+  else
+    k_presort_keys_aos<0><<<grid_for(g.n), kThreads, 0, st>>>(g, r, s);
+  launch_scan(s.count, s.offset, s.partial, g.ncell, st);
+  launch_scatter(g, s, nullptr, st);
+  launch_sort_segments(g, s, st);
+  k_gather_state_aos<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.perm, r, v, b, m_by_id, m_dst);
+  return 8;  // kernels launched: zero, keys, scan (3), scatter, in-cell sort, gather
+}
 
 void launch_add_momentum_fp64(const Geom& g, Fp64Bufs b, int cur, Fp64Mass ms, const double* dp, cudaStream_t st) {
   if (g.n > 0) k_add_momentum_fp64<<<grid_for(g.n), kThreads, 0, st>>>(g, b, cur, ms.m[cur], dp);
@@ -1126,10 +1159,6 @@ void launch_end_step(const Geom& g, Ctl* ctl, cudaStream_t st) { k_end_step<<<1,
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st) {
   k_get_state_fp64<<<grid_for(g.n), kThreads, 0, st>>>(g.n, b.r[cur][0], b.r[cur][1], b.r[cur][2], b.v[cur][0],
                                                         b.v[cur][1], b.v[cur][2], b.id[cur], r, v);
-}
-
-void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st) {
-  k_set_state_fp64<<<grid_for(g.n), kThreads, 0, st>>>(g.n, r, v, b);
 }
 
 }  // namespace mpcd

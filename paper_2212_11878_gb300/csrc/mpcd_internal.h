@@ -149,10 +149,13 @@ void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st);
 // Storage of buffer set 0 into cell order of the unshifted grid (stable by slot), written to
 // buffer set 1 with the ids and masses; returns the number of kernels launched.
 int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaStream_t st);
+// A state in particle-id order (N x 3 arrays r, v; masses m_by_id or null) written straight
+// into buffer set 1 in that cell order (m_dst: the masses in storage order); returns launches.
+int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
+                                 const double* m_by_id, double* m_dst, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
 // v += dp / m per particle (dp[3 N] by particle id, m its mass or the box mass)
 void launch_add_momentum_fp64(const Geom& g, Fp64Bufs b, int cur, Fp64Mass ms, const double* dp, cudaStream_t st);
-void launch_set_state_fp64(const Geom& g, Fp64Bufs b, const double* r, const double* v, cudaStream_t st);
 
 // ---- mixed form (kernels_mixed.cu); one box or an ensemble of independent boxes ----
 // A group of consecutive cells of one box, handled by one warp; rewritten every step
