@@ -121,7 +121,9 @@ int64_t mpcd_steps_done(const mpcd_t* h);    /* steps enqueued since the state w
 int32_t mpcd_num_boxes(const mpcd_t* h);     /* 1 for mpcd_create                          */
 
 /* Copy the state to host arrays r[N*3], v[N*3] (FP64, particle-id order).  Mixed-precision
- * positions are returned as (cell index + offset) * a.  Synchronises.  The first host
+ * positions are returned as (cell index + offset) * a.  Synchronises.  The FP64 form (from
+ * 65,536 particles) gathers the state by particle id in eight chunks and copies each chunk to
+ * the host on a second stream while the next one is gathered.  The first host
  * get/set_state call allocates a device staging buffer of 6 N doubles, kept until
  * mpcd_destroy; if that allocation fails the call returns MPCD_ERR_OOM, changes nothing and
  * leaves the handle usable. */

@@ -69,6 +69,8 @@ struct mpcd_s {
   int64_t n = 0, ncell = 0;
   Fp64Bufs f64{};
   double* host_stage = nullptr;  // 6 N doubles for the host get/set_state copies, made on first use
+  cudaStream_t copy_stream = nullptr;  // FP64 host get_state: chunk copies beside the gathers
+  std::vector<cudaEvent_t> chunk_events;
   double* mass_buf[3] = {};  // FP64 particle masses: storage order (two buffer sets), id order
   Fp64Mass f64m{};           // points at mass_buf[0..1] while masses are set
   float* mix_mass_buf[2] = {};  // mixed form: FP32 masses in the storage order of each record buffer
@@ -689,6 +691,8 @@ int mpcd_destroy(mpcd_t* h) {
     cudaEventDestroy(pt.b);
   }
   for (auto e : h->free_events) cudaEventDestroy(e);
+  for (auto e : h->chunk_events) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   for (void* p : h->allocations) cudaFree(p);
   if (h->own_stream) cudaStreamDestroy(h->own_stream);
   delete h;
@@ -866,6 +870,33 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v) {
   // gather into the staging buffer, then copy to the host
   double* scratch = nullptr;
   if ((rc = host_stage(h, &scratch))) return rc;
+  constexpr int kChunks = 8;
+  if (h->precision == MPCD_FP64 && h->n >= 65536) {
+    // by particle id in chunks: each chunk is gathered (contiguous writes) while the previous
+    // one is copied to the host on a second stream
+    if (!h->copy_stream) {
+      MPCD_TRY(h, cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking));
+      h->chunk_events.assign(kChunks, nullptr);
+      for (auto& ev : h->chunk_events) MPCD_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    const int64_t n = h->n;
+    launch_slot_of(h->geom, h->f64, h->cur, h->scr.rank, h->stream);
+    for (int c = 0; c < kChunks; ++c) {
+      const int64_t p0 = n * c / kChunks, p1 = n * (c + 1) / kChunks;
+      launch_gather_by_id(p0, p1, h->scr.rank, h->f64, h->cur, scratch, scratch + 3 * n, h->stream);
+      MPCD_TRY(h, cudaGetLastError());
+      MPCD_TRY(h, cudaEventRecord(h->chunk_events[c], h->stream));
+      MPCD_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->chunk_events[c], 0));
+      MPCD_TRY(h, cudaMemcpyAsync(r + 3 * p0, scratch + 3 * p0, sizeof(double) * 3 * (size_t)(p1 - p0),
+                                  cudaMemcpyDeviceToHost, h->copy_stream));
+      MPCD_TRY(h, cudaMemcpyAsync(v + 3 * p0, scratch + 3 * n + 3 * p0, sizeof(double) * 3 * (size_t)(p1 - p0),
+                                  cudaMemcpyDeviceToHost, h->copy_stream));
+    }
+    MPCD_TRY(h, cudaStreamSynchronize(h->copy_stream));
+    MPCD_TRY(h, cudaStreamSynchronize(h->stream));
+    h->launches += 1 + kChunks;
+    return MPCD_OK;
+  }
   if (h->precision == MPCD_MIXED)
     launch_get_state_mixed(h->mb, h->mix, h->cur, scratch, scratch + 3 * h->n, h->stream);
   else

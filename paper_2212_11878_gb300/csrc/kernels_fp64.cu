@@ -1015,7 +1015,37 @@ __global__ void __launch_bounds__(kThreads) k_gather_state_aos(int64_t n, const 
   }
 }
 
+// slot_of[id] = storage slot holding that particle.
+__global__ void __launch_bounds__(kThreads) k_slot_of(int64_t n, const int32_t* __restrict__ id,
+                                                     int32_t* __restrict__ slot_of) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+    slot_of[id[s]] = static_cast<int32_t>(s);
+}
+
+// Particles p0 .. p1 - 1 (by id) into N x 3 arrays r, v: contiguous writes, gathered reads.
+__global__ void __launch_bounds__(kThreads) k_gather_by_id(int64_t p0, int64_t p1, const int32_t* __restrict__ slot_of,
+                                                          Fp64Bufs b, int cur, double* __restrict__ r,
+                                                          double* __restrict__ v) {
+  for (int64_t p = p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < p1; p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = slot_of[p];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      r[3 * p + d] = b.r[cur][d][s];
+      v[3 * p + d] = b.v[cur][d][s];
+    }
+  }
+}
+
 }  // namespace
+
+void launch_slot_of(const Geom& g, Fp64Bufs b, int cur, int32_t* slot_of, cudaStream_t st) {
+  if (g.n > 0) k_slot_of<<<grid_for(g.n), kThreads, 0, st>>>(g.n, b.id[cur], slot_of);
+}
+
+void launch_gather_by_id(int64_t p0, int64_t p1, const int32_t* slot_of, Fp64Bufs b, int cur, double* r, double* v,
+                         cudaStream_t st) {
+  if (p1 > p0) k_gather_by_id<<<grid_for(p1 - p0), kThreads, 0, st>>>(p0, p1, slot_of, b, cur, r, v);
+}
 
 int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
                                  const double* m_by_id, double* m_dst, cudaStream_t st) {

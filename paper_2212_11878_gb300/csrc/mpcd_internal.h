@@ -154,6 +154,11 @@ int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaS
 int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
                                  const double* m_by_id, double* m_dst, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
+// slot_of[id] = storage slot (N ints), then the state of particles p0 .. p1 - 1 by id into
+// N x 3 arrays: lets a host copy of the state run in chunks beside the gathers
+void launch_slot_of(const Geom& g, Fp64Bufs b, int cur, int32_t* slot_of, cudaStream_t st);
+void launch_gather_by_id(int64_t p0, int64_t p1, const int32_t* slot_of, Fp64Bufs b, int cur, double* r, double* v,
+                         cudaStream_t st);
 // v += dp / m per particle (dp[3 N] by particle id, m its mass or the box mass)
 void launch_add_momentum_fp64(const Geom& g, Fp64Bufs b, int cur, Fp64Mass ms, const double* dp, cudaStream_t st);
 

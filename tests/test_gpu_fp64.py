@@ -411,3 +411,21 @@ def test_add_momentum_fp64_exact(masses):
         abi.mpcd_add_momentum(box.h, torch.from_numpy(-dp).to("cuda"))
         box.sync()
         assert np.array_equal(box.state()[1], v1 + (-dp) / mm)
+
+
+@pytest.mark.parametrize("L,resort_k", [((40, 40, 40), 3), ((33, 29, 31), 0)])
+def test_host_state_copy_matches_device_copy(L, resort_k):
+    """mpcd_get_state's chunked, overlapped host copy (FP64, 65,536 particles or more; the
+    chunk bounds fall at uneven ids here) returns exactly what mpcd_get_state_device gathers,
+    after re-sorts scrambled the storage order."""
+    torch = pytest.importorskip("torch")
+    p = abi.make_params(L, seed=17, resort_k=resort_k)
+    with abi.Box(p) as box:
+        assert box.n >= 65536
+        box.step(7)
+        rh, vh = box.state()
+        rd = torch.empty((box.n, 3), dtype=torch.float64, device="cuda")
+        vd = torch.empty((box.n, 3), dtype=torch.float64, device="cuda")
+        abi.mpcd_get_state_device(box.h, rd.data_ptr(), vd.data_ptr())
+        box.sync()
+        assert np.array_equal(rh, rd.cpu().numpy()) and np.array_equal(vh, vd.cpu().numpy())
