@@ -243,8 +243,9 @@ int mpcd_debug_stall_barrier(mpcd_t* h, int32_t enable);
 /* Number of kernels this handle has launched (graph replays count each kernel node). */
 int64_t mpcd_launch_count(const mpcd_t* h);
 
-/* Message of the last failure on this handle (or of the last failed create when h is NULL).
- * The string is owned by the library. */
+/* Message of the last failure on this handle, or with h = NULL of the calling thread's last
+ * failure without a handle (create, mpcd_step_fp64_noalloc).  The string is owned by the
+ * library and stays valid until that slot's next failure. */
 const char* mpcd_last_error(const mpcd_t* h);
 
 /* Measurement aid (no counterpart in the paper): this GPU's FP64 fused multiply-add rate,
@@ -285,8 +286,7 @@ const char* mpcd_version(void);
  * module is loaded anew), so that call, too, must come before any stream capture.
  * Errors: MPCD_ERR_ARG, MPCD_ERR_CUDA (also when a CUDA error from earlier work is already
  * pending on this thread: it is left pending, and nothing is launched).  The message is read
- * with mpcd_last_error(NULL), a process-wide slot: callers on several threads see the last
- * failure of any of them. */
+ * with mpcd_last_error(NULL) on the calling thread (one slot per thread). */
 #define MPCD_NOALLOC_MAX_PARTICLES (1 << 19)
 #define MPCD_NOALLOC_MAX_CELLS (1 << 17)
 int mpcd_step_fp64_noalloc(const mpcd_params* p, int64_t t, int64_t n, double* x, double* y, double* z, double* vx,

@@ -49,8 +49,9 @@ const int kSlotLaunchesBase[kNumSlots] = {1, 1, 3, 1, 1, 0, 1, 0, 1};
 // dense pair is a Step: Full, then its own rotation.
 enum Piece { kPieceFull = 0, kPieceBody = 1, kPieceTail = 2, kPieceStep = 3 };  // Step: Full + Tail
 
-std::mutex g_err_mu;
-std::string g_create_err;
+// Message of the last failure without a handle (create, the allocation-free step), one slot
+// per calling thread.
+thread_local std::string g_create_err;
 
 struct PendingTiming {
   int slot;
@@ -134,7 +135,6 @@ int fail(mpcd_t* h, int code, const std::string& msg) {
     h->err = msg;
     if (code == MPCD_ERR_CUDA || code == MPCD_ERR_TIMEOUT) h->poisoned = true;
   } else {
-    std::lock_guard<std::mutex> lk(g_err_mu);
     g_create_err = msg;
   }
   return code;
@@ -1211,7 +1211,6 @@ int mpcd_set_tuning(mpcd_t* h, const mpcd_tuning* t) {
 
 const char* mpcd_last_error(const mpcd_t* h) {
   if (h) return h->err.c_str();
-  std::lock_guard<std::mutex> lk(g_err_mu);
   return g_create_err.c_str();
 }
 

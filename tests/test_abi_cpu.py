@@ -105,3 +105,30 @@ def test_null_handle_queries(libpath):
     assert lib.mpcd_num_particles(None) == -1
     assert lib.mpcd_step(None, 1) == abi.MPCD_ERR_ARG
     assert lib.mpcd_destroy(None) == 0
+
+
+def test_handle_less_error_message_is_per_thread(libpath):
+    """A failed create (rejected on the host, no device work) leaves its message in the calling
+    thread's slot: two threads failing for different reasons each read their own."""
+    import ctypes
+    import threading
+
+    lib = abi.lib()
+    results = {}
+    barrier = threading.Barrier(2)
+
+    def worker(name, **bad):
+        p = abi.make_params((4, 4, 4), **bad)
+        out = ctypes.c_void_p()
+        rc = lib.mpcd_create(ctypes.byref(p), ctypes.byref(out))
+        barrier.wait()  # both have failed before either reads
+        results[name] = (rc, lib.mpcd_last_error(None).decode())
+
+    ts = [threading.Thread(target=worker, args=("kT",), kwargs=dict(kT=-1.0)),
+          threading.Thread(target=worker, args=("mass",), kwargs=dict(mass=0.0))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert results["kT"][0] == abi.MPCD_ERR_ARG and "kT" in results["kT"][1]
+    assert results["mass"][0] == abi.MPCD_ERR_ARG and "mass" in results["mass"][1]
