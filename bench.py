@@ -55,10 +55,12 @@ FP64_BYTES = {
 FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # rotate on re-sort steps also moves r and the ids
 FP64_RESORT_EXTRA_FUSED = 4.0 + 8.0     # the fused pass moves r anyway; + the ids and the destination
 # FP64-pipe instructions (DFMA, DADD, DSUB, DMUL) per launch, as (per particle, per cell), on
-# GB300's narrow FP64 pipe (2 per clock per SM): streaming 3 DFMA + the 3 DSUB of r - s; the
-# frame applied in float-float arithmetic joins each component with one DADD; cell_frame 71
-# per cell (sums' rounding, u, axis, frame).
-FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 71.0), "rotate": (3.0, 0.0), "rotate_stream": (9.0, 0.0)}
+# GB300's narrow FP64 pipe (2 per clock per SM), as counted by ncu
+# (sm__thread_inst_executed_pipe_fp64_pred_on, profiles/fp64_L64_fp64_instruction_counts.md):
+# streaming 3 DFMA + the 3 DSUB of r - s; the frame applied in float-float arithmetic joins
+# each component with one DADD; cell_frame 44 per cell (u and the axis; R and b are built in
+# float-float arithmetic).
+FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 44.0), "rotate": (3.0, 0.0), "rotate_stream": (9.0, 0.0)}
 SMS, FP64_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_GOPS = SMS * FP64_PER_CLK * SM_MAX_MHZ / 1e3   # 629.3 G FP64 instructions/s
 ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step

@@ -206,21 +206,87 @@ __device__ __forceinline__ double ff_join(float sh, float sl) {
   return __dadd_rn(ff_widen(s), ff_widen(e));
 }
 
+// A float-float value (hi + lo) and the two operations the frame needs, every FP32
+// operation an explicit intrinsic (no contraction): the product keeps the exact error of the
+// high parts' product (an FMA) and the cross terms; the sum adds the high parts by two-sum.
+// Both renormalise (|lo| <= ulp(hi) / 2).
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return FF{h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ FF ff_of(double x) {
+  FF r;
+  ff_split(x, r.hi, r.lo);
+  return r;
+}
+
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float pe = __fmaf_rn(a.hi, b.hi, -p);
+  return ff_norm(p, __fadd_rn(pe, __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi))));
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return ff_norm(s, __fadd_rn(err, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+
 // Frame record of the float-float form (32 floats = 128 bytes per cell): R hi [0, 9), R lo
 // [9, 18), b hi [18, 21), b lo [21, 24), rotate flag [24] (1 or 0).
 constexpr int kFfRhi = 0, kFfRlo = 9, kFfBhi = 18, kFfBlo = 21, kFfFlag = 24;
 
-__device__ __forceinline__ void ff_store_frame(float* f, const double R[9], const double bvec[3]) {
-  float w[28];
+// The frame of a cell with centre-of-mass velocity u directly in float-float form, written
+// as the 128-byte record: the axis n comes from the FP64 draw (random_axis), then
+// R = cos(a) 1 + sin(a) [n]x + (1 - cos(a)) n n^T and b = u - R u are built in float-float
+// arithmetic, so the frame costs the FP64 pipe only the axis.
+__device__ __forceinline__ void make_frame_ff(const Geom& g, int64_t t1, int64_t cell, double u0, double u1, double u2,
+                                              float* rec) {
+  double nd[3];
+  random_axis(g.seed, t1, cell, nd);
+  const FF n[3] = {ff_of(nd[0]), ff_of(nd[1]), ff_of(nd[2])};
+  const FF c = ff_of(g.cos_a), s = ff_of(g.sin_a), w = ff_of(1.0 - g.cos_a);
+  const FF wn[3] = {ff_mul(w, n[0]), ff_mul(w, n[1]), ff_mul(w, n[2])};
+  const FF sn[3] = {ff_mul(s, n[0]), ff_mul(s, n[1]), ff_mul(s, n[2])};
+  FF R[9];
+  R[0] = ff_add(ff_mul(wn[0], n[0]), c);
+  R[1] = ff_add(ff_mul(wn[0], n[1]), ff_neg(sn[2]));
+  R[2] = ff_add(ff_mul(wn[0], n[2]), sn[1]);
+  R[3] = ff_add(ff_mul(wn[1], n[0]), sn[2]);
+  R[4] = ff_add(ff_mul(wn[1], n[1]), c);
+  R[5] = ff_add(ff_mul(wn[1], n[2]), ff_neg(sn[0]));
+  R[6] = ff_add(ff_mul(wn[2], n[0]), ff_neg(sn[1]));
+  R[7] = ff_add(ff_mul(wn[2], n[1]), sn[0]);
+  R[8] = ff_add(ff_mul(wn[2], n[2]), c);
+  const FF u[3] = {ff_of(u0), ff_of(u1), ff_of(u2)};
+  float w28[28];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) ff_split(R[k], w[kFfRhi + k], w[kFfRlo + k]);
+  for (int i = 0; i < 3; ++i) {
+    float sh = u[i].hi, sl = u[i].lo;  // b_i = u_i - sum_j R_ij u_j
 #pragma unroll
-  for (int k = 0; k < 3; ++k) ff_split(bvec[k], w[kFfBhi + k], w[kFfBlo + k]);
-  w[kFfFlag] = 1.0f;
-  w[25] = w[26] = w[27] = 0.0f;
-  float4* o = reinterpret_cast<float4*>(f);
+    for (int j = 0; j < 3; ++j) ff_madd(-R[3 * i + j].hi, -R[3 * i + j].lo, u[j].hi, u[j].lo, sh, sl);
+    const FF b = ff_norm(sh, sl);
+    w28[kFfBhi + i] = b.hi;
+    w28[kFfBlo + i] = b.lo;
+  }
 #pragma unroll
-  for (int k = 0; k < 7; ++k) o[k] = make_float4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+  for (int k = 0; k < 9; ++k) {
+    w28[kFfRhi + k] = R[k].hi;
+    w28[kFfRlo + k] = R[k].lo;
+  }
+  w28[kFfFlag] = 1.0f;
+  w28[25] = w28[26] = w28[27] = 0.0f;
+  float4* o = reinterpret_cast<float4*>(rec);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) o[k] = make_float4(w28[4 * k], w28[4 * k + 1], w28[4 * k + 2], w28[4 * k + 3]);
 }
 
 // v' = R v + b with the frame in float-float form (w: the record's first 28 floats).

@@ -646,6 +646,16 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
     rec[6] = make_double2(0.0, 0.0);
     return;
   }
+  if (!ANG) {  // the rotation applies the frame in float-float arithmetic, built that way here
+    float* f = reinterpret_cast<float*>(s.frame + kFrameStride * c);
+    if (MASS) {
+      make_frame_ff(g, t1, c, S[0] / Mc, S[1] / Mc, S[2] / Mc, f);
+    } else {
+      const double in = inv_count(n);
+      make_frame_ff(g, t1, c, S[0] * in, S[1] * in, S[2] * in, f);
+    }
+    return;
+  }
   double R[9], bv[3];
   if (MASS) {
     make_frame(g, t1, c, S[0] / Mc, S[1] / Mc, S[2] / Mc, R, bv);
@@ -682,10 +692,6 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
     bv[0] -= aw[1] * lbar[2] - aw[2] * lbar[1];
     bv[1] -= aw[2] * lbar[0] - aw[0] * lbar[2];
     bv[2] -= aw[0] * lbar[1] - aw[1] * lbar[0];
-  }
-  if (!ANG) {  // the rotation applies the frame in float-float arithmetic
-    ff_store_frame(reinterpret_cast<float*>(s.frame + kFrameStride * c), R, bv);
-    return;
   }
   rec[0] = make_double2(R[0], R[1]);
   rec[1] = make_double2(R[2], R[3]);
