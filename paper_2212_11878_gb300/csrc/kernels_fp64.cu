@@ -193,12 +193,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_stream_bin_fp64(Geom g, Fp64Buf
 // perm[offset[key] + place] = slot, with the keys of the step in flight (ctl->t + 1), or of
 // s.key when ctl is null (the initial cell-order sort).  The place inside the cell is the
 // arrival rank of the counting atomics, or, with a cursor array, taken here from the cell's
-// cursor.  Either way a cell's entries are in no fixed order; the exact cell sums do not
-// depend on it, and the kernels that need storage order sort the cell's entries.
+// cursor: the storage is nearly in cell order, so a warp's slots mostly share a few keys, and
+// the lanes with equal keys (match.any) take their places with one atomic.  Either way a
+// cell's entries are in no fixed order; the exact cell sums do not depend on it, and the
+// kernels that need storage order sort the cell's entries.
 __global__ void __launch_bounds__(kThreads) k_scatter(int64_t n, Scratch s, const Ctl* __restrict__ ctl) {
   const int32_t* __restrict__ key = ctl ? keys_of(s, ctl->t + 1) : s.key;
   const int32_t* __restrict__ offset = s.offset;
   int32_t* __restrict__ perm = s.perm;
+  if (s.cursor) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {  // warp-uniform
+      const int64_t i = base + lane;
+      const int k = i < n ? key[i] : -1 - lane;  // distinct sentinels past the end
+      const unsigned peers = __match_any_sync(0xffffffffu, k);
+      const int rank = __popc(peers & below);
+      int first = 0;
+      if (k >= 0 && rank == 0) first = atomicAdd(&s.cursor[k], __popc(peers));
+      first = __shfl_sync(0xffffffffu, first, __ffs(peers) - 1);
+      if (k >= 0) perm[offset[k] + first + rank] = static_cast<int32_t>(i);
+    }
+    return;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int k = key[i];
     const int place = s.cursor ? atomicAdd(&s.cursor[k], 1) : s.rank[i];
