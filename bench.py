@@ -351,10 +351,10 @@ def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True, fp64_probe
         d = kernels[dom]
         per_launch = d["algo_bytes_per_invocation"]
         tr = NCU_TRAFFIC.get(("mixed", dom)) if captured else None
-        return {"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
+        return dict(traffic_rates(tr[0] * n if tr else None, d, hbm_peak), **{"kernel": dom, "bound": "hbm", "achieved": d["gbs"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": d["gbs"] / hbm_peak, "traffic": tr[0] * n if tr else None,
                 "traffic_source": tr[1] if tr else None, "peak_source": peak_src + " (hbm_gbs)",
-                "algo_bytes_per_launch": per_launch}
+                "algo_bytes_per_launch": per_launch})
     fp64k = [k for k in kernels if "fp64_gops" in kernels[k]]
     dom = max(fp64k, key=lambda k: kernels[k]["ms_per_step"])
     d = kernels[dom]
@@ -377,7 +377,17 @@ def roofline_of(kernels, mixed, hbm_peak, peak_src, n, captured=True, fp64_probe
                "unit": "G FP64 instructions/s", "frac": alu_frac, "peak_source": alu["fp64_peak_source"],
                "algo_bytes_per_launch": d["algo_bytes_per_invocation"]}
     out.update(traffic=tr[0] * n if tr else None, traffic_source=tr[1] if tr else None, **alu)
+    out.update(traffic_rates(out["traffic"], d, hbm_peak))
     return out
+
+
+def traffic_rates(traffic, d, hbm_peak):
+    """The measured-traffic fraction beside the algorithmic one: ncu's DRAM bytes of a launch
+    over the same CUDA-event launch time."""
+    if not traffic or not d.get("ms_per_invocation"):
+        return {"traffic_gbs": None, "traffic_frac": None}
+    gbs = traffic / (d["ms_per_invocation"] / 1e3) / 1e9
+    return {"traffic_gbs": gbs, "traffic_frac": gbs / hbm_peak}
 
 
 def main():
