@@ -448,3 +448,22 @@ def test_add_momentum_mixed(masses):
     mm = (m if masses else np.full(len(v0), p.mass))[:, None]
     assert np.array_equal(r1, r0)
     assert np.array_equal(v1, (v0 + dp / mm).astype(np.float32).astype(np.float64))
+
+
+def test_add_momentum_ensemble_uses_each_box_mass():
+    """In an ensemble without particle masses each particle's increment is divided by its own
+    box's mass."""
+    params = [abi.make_params((6, 6, 6), precision="mixed", mass=1.0, seed=61),
+              abi.make_params((8, 7, 6), precision="mixed", mass=2.5, kT=2.5, seed=62)]
+    with abi.Box(batch=params) as ens:
+        pb, _ = abi.mpcd_box_offsets(ens.h)
+        ens.step(2)
+        r0, v0 = ens.state()
+        dp = np.random.default_rng(4).normal(0.0, 0.2, (ens.n, 3))
+        abi.mpcd_add_momentum(ens.h, dp)
+        r1, v1 = ens.state()
+    m = np.empty((len(v0), 1))
+    m[pb[0]:pb[1]] = 1.0
+    m[pb[1]:pb[2]] = 2.5
+    assert np.array_equal(r1, r0)
+    assert np.array_equal(v1, (v0 + dp / m).astype(np.float32).astype(np.float64))
