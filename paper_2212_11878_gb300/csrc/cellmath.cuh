@@ -242,7 +242,13 @@ __device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
 
 // Frame record of the float-float form (32 floats = 128 bytes per cell): R hi [0, 9), R lo
 // [9, 18), b hi [18, 21), b lo [21, 24), rotate flag [24] (1 or 0).
-constexpr int kFfRhi = 0, kFfRlo = 9, kFfBhi = 18, kFfBlo = 21, kFfFlag = 24;
+// Row i of R and b: R hi (3), b hi, R lo (3), b lo at floats 8 i .. 8 i + 7 (two float4), so
+// that a row can be loaded and applied on its own; the flag at float 24.
+__host__ __device__ constexpr int ff_rhi(int i, int j) { return 8 * i + j; }
+__host__ __device__ constexpr int ff_rlo(int i, int j) { return 8 * i + 4 + j; }
+__host__ __device__ constexpr int ff_bhi(int i) { return 8 * i + 3; }
+__host__ __device__ constexpr int ff_blo(int i) { return 8 * i + 7; }
+constexpr int kFfFlag = 24;
 
 // The frame of a cell with centre-of-mass velocity u directly in float-float form, written
 // as the 128-byte record: the axis n comes from the FP64 draw (random_axis), then
@@ -274,13 +280,13 @@ __device__ __forceinline__ void make_frame_ff(const Geom& g, int64_t t1, int64_t
 #pragma unroll
     for (int j = 0; j < 3; ++j) ff_madd(-R[3 * i + j].hi, -R[3 * i + j].lo, u[j].hi, u[j].lo, sh, sl);
     const FF b = ff_norm(sh, sl);
-    w28[kFfBhi + i] = b.hi;
-    w28[kFfBlo + i] = b.lo;
+    w28[ff_bhi(i)] = b.hi;
+    w28[ff_blo(i)] = b.lo;
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    w28[kFfRhi + k] = R[k].hi;
-    w28[kFfRlo + k] = R[k].lo;
+    w28[ff_rhi(k / 3, k % 3)] = R[k].hi;
+    w28[ff_rlo(k / 3, k % 3)] = R[k].lo;
   }
   w28[kFfFlag] = 1.0f;
   w28[25] = w28[26] = w28[27] = 0.0f;
@@ -298,9 +304,31 @@ __device__ __forceinline__ void ff_apply_frame(const float w[28], double& v0, do
   double out[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    float sh = w[kFfBhi + i], sl = w[kFfBlo + i];
+    float sh = w[ff_bhi(i)], sl = w[ff_blo(i)];
 #pragma unroll
-    for (int j = 0; j < 3; ++j) ff_madd(w[kFfRhi + 3 * i + j], w[kFfRlo + 3 * i + j], vh[j], vl[j], sh, sl);
+    for (int j = 0; j < 3; ++j) ff_madd(w[ff_rhi(i, j)], w[ff_rlo(i, j)], vh[j], vl[j], sh, sl);
+    out[i] = ff_join(sh, sl);
+  }
+  v0 = out[0];
+  v1 = out[1];
+  v2 = out[2];
+}
+
+// The same, loading each row of the record (two float4) just before it is applied, so that
+// only one row is live at a time.
+__device__ __forceinline__ void ff_apply_frame_rows(const float4* __restrict__ rec, double& v0, double& v1, double& v2) {
+  float vh[3], vl[3];
+  ff_split(v0, vh[0], vl[0]);
+  ff_split(v1, vh[1], vl[1]);
+  ff_split(v2, vh[2], vl[2]);
+  double out[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const float4 hi = rec[2 * i], lo = rec[2 * i + 1];  // R hi (3), b hi | R lo (3), b lo
+    float sh = hi.w, sl = lo.w;
+    ff_madd(hi.x, lo.x, vh[0], vl[0], sh, sl);
+    ff_madd(hi.y, lo.y, vh[1], vl[1], sh, sl);
+    ff_madd(hi.z, lo.z, vh[2], vl[2], sh, sl);
     out[i] = ff_join(sh, sl);
   }
   v0 = out[0];

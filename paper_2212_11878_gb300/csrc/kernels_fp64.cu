@@ -841,12 +841,30 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate_stream(Geom g, Fp64Bufs 
   const double shn[3] = {ctl->shift[0], ctl->shift[1], ctl->shift[2]};  // step t + 1
   const double shl[3] = {ctl->shift_last[0], ctl->shift_last[1], ctl->shift_last[2]};  // step t
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
-    RotSlot q;
-    rotate_load<ANG>(b, s, kin, i, src, q);
-    double r[3] = {b.r[src][0][i], b.r[src][1][i], b.r[src][2][i]};
-    const bool rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1 or 0, as bits
-    double v[3] = {q.v[0], q.v[1], q.v[2]};
-    if (rot) rotate_apply<ANG>(g, q.f, r, shl, v[0], v[1], v[2]);  // l_i on step t's grid
+    double r[3], v[3];
+    bool rot;
+    if (ANG) {
+      RotSlot q;
+      rotate_load<ANG>(b, s, kin, i, src, q);
+      r[0] = b.r[src][0][i];
+      r[1] = b.r[src][1][i];
+      r[2] = b.r[src][2][i];
+      rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1 or 0, as bits
+      v[0] = q.v[0];
+      v[1] = q.v[1];
+      v[2] = q.v[2];
+      if (rot) rotate_apply<ANG>(g, q.f, r, shl, v[0], v[1], v[2]);  // l_i on step t's grid
+    } else {  // float-float frame, loaded row by row as it is applied
+      const float4* __restrict__ rec = reinterpret_cast<const float4*>(s.frame + kFrameStride * (int64_t)kin[i]);
+      v[0] = b.v[src][0][i];
+      v[1] = b.v[src][1][i];
+      v[2] = b.v[src][2][i];
+      r[0] = b.r[src][0][i];
+      r[1] = b.r[src][1][i];
+      r[2] = b.r[src][2][i];
+      rot = rec[6].x != 0.0f;
+      if (rot) ff_apply_frame_rows(rec, v[0], v[1], v[2]);
+    }
     const int64_t dst = resort ? s.inv[i] : i;
     const int32_t pid = resort ? b.id[src][i] : 0;
     const double pm = (MASS && resort) ? ms.m[src][i] : 0.0;
