@@ -632,7 +632,6 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     if ((rc = dalloc(h, &h->scr.partial, (int64_t)scan_tiles(C) + 1))) return bail(rc);
     if (!h->geom.walls && !h->geom.thermostat) {
       if ((rc = dalloc(h, &h->scr.frame, 16 * C))) return bail(rc);
-      if ((rc = dalloc(h, &h->scr.inv, n))) return bail(rc);
       if ((rc = dalloc(h, &h->scr.key2, n))) return bail(rc);  // keys of odd steps (fused pass)
     }
   }

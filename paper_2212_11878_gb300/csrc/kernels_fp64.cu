@@ -573,11 +573,12 @@ __global__ void __launch_bounds__(kThreads) k_collide_fp64_generic(Geom g, Fp64B
 //  k_cell_frame  one thread per cell: exact sums (order-independent, so the arrival order
 //                of the atomics does not matter), centre-of-mass velocity, random axis and
 //                the frame (R, b), written as one 128-byte record per cell.  On re-sort
-//                steps it also restores storage order inside the cell and records each
-//                particle's destination slot.
-//  k_rotate      one thread per storage slot: v' = R v + b with the frame of its cell (nine
-//                FP64 FMAs on full warps, coalesced state access); on re-sort steps the
-//                particle is written to its destination slot in the other buffer set.
+//                steps it also restores storage order inside the cell, so that perm then
+//                lists the storage slots in the new (cell) order.
+//  k_rotate      one thread per slot: v' = R v + b with the frame of its cell (nine FP64
+//                FMAs on full warps, coalesced state access); on re-sort steps slot j of the
+//                other buffer set gathers its particle from storage slot perm[j] (scattered
+//                reads, contiguous writes).
 constexpr int kFrameStride = 16;  // doubles per cell record: R[9], b[3], flag, 3 unused
 
 // Angular-momentum correction of a dense cell from its moments (the variant Sec. 2 mentions):
@@ -641,8 +642,6 @@ __global__ void __launch_bounds__(kThreads) k_cell_frame(Geom g, Fp64Bufs b, Scr
   const int n = s.offset[c + 1] - o;
   int32_t* __restrict__ pm = s.perm + o;
   if (resort || ANG) sort_entries(pm, n);  // ANG: one fixed order for the FP64 moment sums
-  if (resort)
-    for (int j = 0; j < n; ++j) s.inv[pm[j]] = o + j;
   double S[3], SE, Mc = 0.0;
   if (MASS) {  // particle masses: S = sum m v (exact), Mc = sum m
     cell_sums_mass<MOMENTS>(b, cur, ms.m[cur], pm, n, S, SE, Mc);
@@ -775,7 +774,7 @@ __device__ __forceinline__ void rotate_apply(const Geom& g, const double2 f[8], 
 
 template <int MASS, int ANG>
 __device__ __forceinline__ void rotate_finish(const Geom& g, const Fp64Bufs& b, const Fp64Mass& ms, const Scratch& s,
-                                              RotSlot& q, int cur, bool resort, const double* shift) {
+                                              RotSlot& q, int cur, bool resort, const double* shift, int64_t dst) {
   // flag (1 or 0; FP64 or FP32, as bits) in the record's sixth 16-byte word
   const bool rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;
   double v0 = q.v[0], v1 = q.v[1], v2 = q.v[2];
@@ -788,10 +787,9 @@ __device__ __forceinline__ void rotate_finish(const Geom& g, const Fp64Bufs& b, 
     }
     rotate_apply<ANG>(g, q.f, r, shift, v0, v1, v2);
   }
-  const int64_t i = q.i;
+  const int64_t i = q.i;  // the source slot (dst itself unless re-sorting)
   if (resort) {
     const int ob = cur ^ 1;
-    const int dst = s.inv[i];
     b.r[ob][0][dst] = b.r[cur][0][i];
     b.r[ob][1][dst] = b.r[cur][1][i];
     b.r[ob][2][dst] = b.r[cur][2][i];
@@ -819,16 +817,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scra
   const int32_t* __restrict__ key = keys_of(s, t);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     RotSlot q;
-    rotate_load<ANG>(b, s, key, i, src, q);
-    rotate_finish<MASS, ANG>(g, b, ms, s, q, src, resort, ctl->shift_last);
+    const int64_t si = resort ? (int64_t)s.perm[i] : i;  // re-sort: gather slot i's particle
+    rotate_load<ANG>(b, s, key, si, src, q);
+    rotate_finish<MASS, ANG>(g, b, ms, s, q, src, resort, ctl->shift_last, i);
   }
 }
 
 // The rotation of step t fused with the streaming and binning of step t + 1 (one pass over
 // the state instead of two): each slot's velocity gets its cell's frame (v' = R v + b, the
 // same arithmetic as k_rotate), the particle moves on (the same arithmetic as stream_bin),
-// and it is written, on re-sort steps to its cell-order slot in the other buffer set, with
-// its key on step t + 1's shifted grid and its arrival rank in that cell.
+// and it is written with its key on step t + 1's shifted grid and its arrival rank in that
+// cell; on re-sort steps slot i of the other buffer set gathers its particle from storage
+// slot perm[i].
 template <int FORCE, int POW2A, int MASS, int ANG>
 __global__ void __launch_bounds__(kThreads, 4) k_rotate_stream(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
                                                               Fp64Mass ms) {
@@ -841,33 +841,34 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate_stream(Geom g, Fp64Bufs 
   const double shn[3] = {ctl->shift[0], ctl->shift[1], ctl->shift[2]};  // step t + 1
   const double shl[3] = {ctl->shift_last[0], ctl->shift_last[1], ctl->shift_last[2]};  // step t
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t si = resort ? (int64_t)s.perm[i] : i;
     double r[3], v[3];
     bool rot;
     if (ANG) {
       RotSlot q;
-      rotate_load<ANG>(b, s, kin, i, src, q);
-      r[0] = b.r[src][0][i];
-      r[1] = b.r[src][1][i];
-      r[2] = b.r[src][2][i];
+      rotate_load<ANG>(b, s, kin, si, src, q);
+      r[0] = b.r[src][0][si];
+      r[1] = b.r[src][1][si];
+      r[2] = b.r[src][2][si];
       rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1 or 0, as bits
       v[0] = q.v[0];
       v[1] = q.v[1];
       v[2] = q.v[2];
       if (rot) rotate_apply<ANG>(g, q.f, r, shl, v[0], v[1], v[2]);  // l_i on step t's grid
     } else {  // float-float frame, loaded row by row as it is applied
-      const float4* __restrict__ rec = reinterpret_cast<const float4*>(s.frame + kFrameStride * (int64_t)kin[i]);
-      v[0] = b.v[src][0][i];
-      v[1] = b.v[src][1][i];
-      v[2] = b.v[src][2][i];
-      r[0] = b.r[src][0][i];
-      r[1] = b.r[src][1][i];
-      r[2] = b.r[src][2][i];
+      const float4* __restrict__ rec = reinterpret_cast<const float4*>(s.frame + kFrameStride * (int64_t)kin[si]);
+      v[0] = b.v[src][0][si];
+      v[1] = b.v[src][1][si];
+      v[2] = b.v[src][2][si];
+      r[0] = b.r[src][0][si];
+      r[1] = b.r[src][1][si];
+      r[2] = b.r[src][2][si];
       rot = rec[6].x != 0.0f;
       if (rot) ff_apply_frame_rows(rec, v[0], v[1], v[2]);
     }
-    const int64_t dst = resort ? s.inv[i] : i;
-    const int32_t pid = resort ? b.id[src][i] : 0;
-    const double pm = (MASS && resort) ? ms.m[src][i] : 0.0;
+    const int64_t dst = i;
+    const int32_t pid = resort ? b.id[src][si] : 0;
+    const double pm = (MASS && resort) ? ms.m[src][si] : 0.0;
     const int k = move_and_key<0, FORCE, POW2A>(g, r, v, shn);
     b.r[cur][0][dst] = r[0];
     b.r[cur][1][dst] = r[1];
@@ -1162,7 +1163,7 @@ void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl,
 }
 
 bool fp64_dense_collide(const Geom& g, const Scratch& s) {
-  return !g.walls && !g.thermostat && s.frame && s.inv;
+  return !g.walls && !g.thermostat && s.frame;
 }
 
 __global__ void k_gather_masses(int64_t n, const double* __restrict__ m_by_id, const int32_t* __restrict__ id,

@@ -115,7 +115,6 @@ struct Scratch {
   int32_t* partial;  // scan partial sums
   double* moments;   // [5 C] per-cell M, Px, Py, Pz, E (only when recording)
   double* frame;     // [16 C] per-cell record: R (9), b (3), rotate flag, 3 unused
-  int32_t* inv;      // [N] destination slot of each storage slot on re-sort steps
   double* red;       // [3 * reduce blocks] partial sums for the initial mean removal
 };
 
