@@ -10,10 +10,12 @@
 //    collision v' = u + R(n, alpha)(v - u) (paper Sec. 2, parts (ii)-(iii)) is applied as
 //    v' = R v + b with b = u - R u, i.e. nine FMAs per particle.
 //  * Cell coordinates: floor() and the periodic-wrap comparisons are done on the IEEE bit
-//    patterns with integer instructions; only the operations whose rounding decides the
-//    cell (r + v dt, r - s) stay in FP64.
+//    patterns with integer instructions, and for a power-of-two cell size r - s too, in
+//    fixed point, except within a few 2^-32 cells of a face, where the FP64 subtraction
+//    decides; r + v dt stays in FP64.
 #pragma once
 #include <cstdint>
+#include <cstring>
 
 #include "device_common.cuh"
 #include "mpcd_internal.h"
@@ -38,6 +40,17 @@ __device__ __forceinline__ void fx_zero(Fx128& a) {
 __device__ __forceinline__ unsigned long long dbits(double x) {
   return (static_cast<unsigned long long>(static_cast<unsigned>(__double2hiint(x))) << 32) |
          static_cast<unsigned>(__double2loint(x));
+}
+
+// The same on the host too (the fixed-point cell floor below is checked there).
+__host__ __device__ __forceinline__ unsigned long long bits_of(double x) {
+#ifdef __CUDA_ARCH__
+  return dbits(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, sizeof b);
+  return b;
+#endif
 }
 
 __device__ __forceinline__ bool fx_add(Fx128& a, double x) {
@@ -240,10 +253,9 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
 
 __device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
 
-// Frame record of the float-float form (32 floats = 128 bytes per cell): R hi [0, 9), R lo
-// [9, 18), b hi [18, 21), b lo [21, 24), rotate flag [24] (1 or 0).
-// Row i of R and b: R hi (3), b hi, R lo (3), b lo at floats 8 i .. 8 i + 7 (two float4), so
-// that a row can be loaded and applied on its own; the flag at float 24.
+// Frame record of the float-float form (32 floats = 128 bytes per cell): row i of R and b
+// as R hi (3), b hi, R lo (3), b lo at floats 8 i .. 8 i + 7 (two float4), so that a row can
+// be loaded and applied on its own; the rotate flag (1 or 0) at float 24.
 __host__ __device__ constexpr int ff_rhi(int i, int j) { return 8 * i + j; }
 __host__ __device__ constexpr int ff_rlo(int i, int j) { return 8 * i + 4 + j; }
 __host__ __device__ constexpr int ff_bhi(int i) { return 8 * i + 3; }
@@ -337,6 +349,35 @@ __device__ __forceinline__ void ff_apply_frame_rows(const float4* __restrict__ r
 }
 
 // -------------------------------------------------------------- cell coordinates ----
+// x / a in units of 2^-32 (truncated toward zero), a = 2^log2a, from the bit pattern of x,
+// for |x / a| < 2^22; false for larger magnitudes, inf and NaN.
+__host__ __device__ __forceinline__ bool fx32_trunc(double x, int log2a, long long& X) {
+  const unsigned long long b = bits_of(x);
+  const int e = static_cast<int>((b >> 52) & 0x7FFull) - 1023 - log2a;  // |x / a| in [2^e, 2^(e+1))
+  if (e > 21) return false;
+  const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int sh = 20 - e;  // |x / a| 2^32 = m 2^(e - 20); zero and subnormals shift out to 0
+  const unsigned long long q = sh <= 0 ? (m << -sh) : (sh < 64 ? (m >> sh) : 0ull);
+  X = (b >> 63) ? -static_cast<long long>(q) : static_cast<long long>(q);
+  return true;
+}
+
+// floor(fl(x - s) / a) (a = 2^log2a, S = s / a as fx32_trunc gives it) without the FP64
+// subtraction.  D = X - S is within 2 units of 2^-32 of (x - s) / a (each truncation less
+// than one), and rounding x - s to FP64 moves it by at most 2^-53 |x - s| / a, under 2 more
+// units for |x - s| < 2^22 a; so where D lies 8 or more units from a cell face its integer
+// part is the floor of the rounded difference.  False otherwise (and for |x / a| >= 2^22):
+// the caller subtracts in FP64.
+__host__ __device__ __forceinline__ bool cell_floor_fx(double x, long long S, int log2a, int& c) {
+  long long X;
+  if (!fx32_trunc(x, log2a, X)) return false;
+  const long long D = X - S;
+  const unsigned frac = static_cast<unsigned>(static_cast<unsigned long long>(D) & 0xFFFFFFFFull);
+  if (frac - 8u > 0xFFFFFFEFu) return false;  // frac < 8 or frac > 2^32 - 9
+  c = static_cast<int>(D >> 32);
+  return true;
+}
+
 // floor(q * 2^k) for |q * 2^k| < 2^30 from the bit pattern of q (integer pipe only; the
 // power-of-two scale is an exponent shift, so no FP64 multiply is needed).  Larger
 // magnitudes return +-2^30; callers clamp coordinates into range.

@@ -43,12 +43,25 @@ __device__ __forceinline__ double wrap_periodic(double x, double B) {
   return wrap_box(x, B, __double_as_longlong(B));
 }
 
-// Cell coordinate along one axis on the grid shifted by s (POW2A: a is a power of two, so
-// the division is an exponent shift inside floor_bits).
+// floor(fl(x - s) / a) for a power-of-two a with the FP64 subtraction: out of line, for the
+// rare coordinates the fixed-point test cannot decide.
+static __device__ __noinline__ int cell_floor_fp64(double x, double s, int log2a) {
+  return floor_bits(__dsub_rn(x, s), -log2a);
+}
+
+// Cell coordinate along one axis on the grid shifted by s.  POW2A (a a power of two): in
+// 32.32 fixed point on the integer pipe (cell_floor_fx; S is loop-invariant), the FP64
+// subtraction only within 8 / 2^32 cells of a face; either way the floor of the rounded
+// FP64 difference.  Otherwise an FP64 division.
 template <int POW2A>
 __device__ __forceinline__ int cell_coord(double x, double s, const Geom& g, int d) {
-  const double diff = __dsub_rn(x, s);
-  int c = POW2A ? floor_bits(diff, -g.log2a) : floor_bits(__ddiv_rn(diff, g.a));
+  int c;
+  if (POW2A) {
+    long long S;
+    if (!(fx32_trunc(s, g.log2a, S) && cell_floor_fx(x, S, g.log2a, c))) c = cell_floor_fp64(x, s, g.log2a);
+  } else {
+    c = floor_bits(__ddiv_rn(__dsub_rn(x, s), g.a));
+  }
   if (g.walls && d == 2) {  // layers 0 .. Lz; rounding of (z - s)/a may reach Lz + 1
     c += 1;
     return c < 0 ? 0 : (c > g.L[2] ? g.L[2] : c);

@@ -161,6 +161,50 @@ def test_face_positions_bit_exact_keys(orc):
     run_pair(orc, p, r, v, steps=3)
 
 
+@pytest.mark.parametrize("kw", [dict(), dict(a=0.5), dict(a=2.0), dict(walls_z=1)],
+                         ids=["a1", "a_half", "a2", "walls"])
+def test_keys_within_ulps_of_shifted_faces(orc, kw):
+    """Coordinates a few ulps either side of the faces of the grids that the next three steps
+    shift to (dt = 0: nothing moves), the rest uniform: each cell key is the floor of the
+    rounded FP64 difference (r - s) / a bit for bit, however the kernel reaches it (in fixed
+    point away from a face, by the FP64 subtraction next to one).  One step per call (the
+    streaming kernel) and three in one call (the fused rotate-and-stream pass after the
+    first)."""
+    L = (6, 5, 7)
+    p = abi.make_params(L, dt=0.0, seed=303, **kw)
+    op = oracle_params(orc, p)
+    a = p.a
+    box_len = np.asarray(L, dtype=np.float64) * a
+    n = int(round(p.ppc * np.prod(L)))
+    rng = np.random.default_rng(17)
+    r = rng.uniform(0.0, 1.0, (n, 3)) * box_len
+    per_step = n // 4
+    for j in range(3 * per_step):
+        s = orc.shift(op, j // per_step + 1)
+        for d in range(3):
+            while True:
+                x = s[d] + int(rng.integers(0, L[d] + 1)) * a
+                k = int(rng.integers(-6, 7))
+                for _ in range(abs(k)):
+                    x = np.nextafter(x, np.inf if k > 0 else -np.inf)
+                if 0.0 <= x < box_len[d]:
+                    break
+            r[j, d] = x
+    v = rng.standard_normal((n, 3))
+    run_pair(orc, p, r, v, steps=3)
+    with abi.Box(p) as box:
+        box.set_state(r, v, 0)
+        box.step(3)
+        st = orc.presort(op, orc.State(r, v, t=0))
+        for t in range(1, 4):
+            ref = orc.step(op, st, debug=True)
+            assert np.array_equal(ref["shift"], orc.shift(op, t))
+        assert_sort_equal(box.debug_sort(), ref)
+        rg, vg = box.state()
+        rr, vr = st.by_id()
+        assert_state_close(rg, vg, rr, vr, p, tol=1e-12, what="three steps in one call")
+
+
 def test_empty_box(orc):
     p = abi.make_params((4, 4, 4), ppc=0.0)
     with abi.Box(p) as box:
