@@ -52,15 +52,17 @@ FP64_BYTES = {
     "rotate_stream": (48.0 + 48.0 + 4.0 + 4.0 + 4.0 + 8.0, 4.0),
     "end_step": (0.0, 0.0),
 }
-FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0   # rotate on re-sort steps also moves r and the ids
-FP64_RESORT_EXTRA_FUSED = 4.0 + 8.0     # the fused pass moves r anyway; + the ids and the destination
+# on re-sort steps each slot gathers its particle through perm (4 B) and moves its id (4 + 4);
+# the separate rotation also moves r (24 + 24), the fused pass moves r anyway
+FP64_RESORT_EXTRA = 24.0 + 24.0 + 8.0 + 4.0
+FP64_RESORT_EXTRA_FUSED = 8.0 + 4.0
 # FP64-pipe instructions (DFMA, DADD, DSUB, DMUL) per launch, as (per particle, per cell), on
 # GB300's narrow FP64 pipe (2 per clock per SM), as counted by ncu
 # (sm__thread_inst_executed_pipe_fp64_pred_on, profiles/fp64_L64_fp64_instruction_counts.md):
-# streaming 3 DFMA + the 3 DSUB of r - s; the frame applied in float-float arithmetic joins
-# each component with one DADD; cell_frame 44 per cell (u and the axis; R and b are built in
-# float-float arithmetic).
-FP64_OPS = {"stream_bin": (6.0, 0.0), "collide": (0.0, 44.0), "rotate": (3.0, 0.0), "rotate_stream": (9.0, 0.0)}
+# streaming 3 DFMA (r - s is taken in fixed point, in FP64 only next to a cell face); the frame
+# applied in float-float arithmetic joins each component with one DADD; cell_frame 44 per cell
+# (u and the axis; R and b are built in float-float arithmetic).
+FP64_OPS = {"stream_bin": (3.0, 0.0), "collide": (0.0, 44.0), "rotate": (3.0, 0.0), "rotate_stream": (6.0, 0.0)}
 SMS, FP64_PER_CLK, SM_MAX_MHZ = 152, 2, 2070.0
 FP64_PEAK_GOPS = SMS * FP64_PER_CLK * SM_MAX_MHZ / 1e3   # 629.3 G FP64 instructions/s
 ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step
@@ -80,9 +82,7 @@ MIXED_BYTES = {
 ALGO_STEP_BYTES_MIXED = 64.0
 # DRAM bytes (read + write) per particle of a kernel from one ncu capture of the current build,
 # scaled to a launch by the particle count; a kernel changed since its capture has none.
-NCU_TRAFFIC = {("mixed", "collide"): (72.07, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)"),
-               ("fp64", "rotate_stream"): (108.95, "profiles/fp64_L64_rotate_stream_full.md (64^3 capture of an "
-                                                   "ordinary, non-re-sort launch, scaled by the particle count)")}
+NCU_TRAFFIC = {("mixed", "collide"): (72.07, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)")}
 # timed beside an FP64 run: the mixed form at 256^3, the 256-box ensemble, the walled
 # channel with each cell thermostat, the angular-momentum-conserving collision and per-particle
 # masses
