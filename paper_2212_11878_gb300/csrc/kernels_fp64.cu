@@ -214,19 +214,33 @@ __global__ void __launch_bounds__(kThreads) k_scatter(int64_t n, Scratch s, cons
   const int32_t* __restrict__ key = ctl ? keys_of(s, ctl->t + 1) : s.key;
   const int32_t* __restrict__ offset = s.offset;
   int32_t* __restrict__ perm = s.perm;
-  if (s.cursor) {
+  if (s.cursor) {  // eight chunks of 32 slots per warp and round: eight atomics in flight
+    constexpr int kChunks = 8;
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n;
-         base += (int64_t)gridDim.x * blockDim.x) {  // warp-uniform
-      const int64_t i = base + lane;
-      const int k = i < n ? key[i] : -1 - lane;  // distinct sentinels past the end
-      const unsigned peers = __match_any_sync(0xffffffffu, k);
-      const int rank = __popc(peers & below);
-      int first = 0;
-      if (k >= 0 && rank == 0) first = atomicAdd(&s.cursor[k], __popc(peers));
-      first = __shfl_sync(0xffffffffu, first, __ffs(peers) - 1);
-      if (k >= 0) perm[offset[k] + first + rank] = static_cast<int32_t>(i);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * (32 * kChunks); base < n;
+         base += warps * 32 * kChunks) {  // warp-uniform
+      int k[kChunks];
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) {
+        const int64_t i = base + 32 * c + lane;
+        k[c] = i < n ? key[i] : -1 - lane;  // distinct sentinels past the end
+      }
+      unsigned peers[kChunks];
+      int rank[kChunks], first[kChunks];
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) {
+        peers[c] = __match_any_sync(0xffffffffu, k[c]);
+        rank[c] = __popc(peers[c] & below);
+        first[c] = 0;
+        if (k[c] >= 0 && rank[c] == 0) first[c] = atomicAdd(&s.cursor[k[c]], __popc(peers[c]));
+      }
+#pragma unroll
+      for (int c = 0; c < kChunks; ++c) {
+        const int start = __shfl_sync(0xffffffffu, first[c], __ffs(peers[c]) - 1);
+        if (k[c] >= 0) perm[offset[k[c]] + start + rank[c]] = static_cast<int32_t>(base + 32 * c + lane);
+      }
     }
     return;
   }
@@ -1156,7 +1170,7 @@ void launch_stream_bin_fp64(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, cuda
 }
 
 void launch_scatter(const Geom& g, Scratch s, const Ctl* ctl, cudaStream_t st) {
-  k_scatter<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s, ctl);
+  k_scatter<<<grid_for(g.n, s.cursor ? 8 : 1), kThreads, 0, st>>>(g.n, s, ctl);
 }
 
 void launch_collide_fp64_generic(const Geom& g, Fp64Bufs b, Scratch s, Ctl* ctl, bool moments, cudaStream_t st,
