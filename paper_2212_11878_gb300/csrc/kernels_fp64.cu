@@ -1117,8 +1117,7 @@ void launch_gather_by_id(int64_t p0, int64_t p1, const int32_t* slot_of, Fp64Buf
   if (p1 > p0) k_gather_by_id<<<grid_for(p1 - p0), kThreads, 0, st>>>(p0, p1, slot_of, b, cur, r, v);
 }
 
-int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
-                                 const double* m_by_id, double* m_dst, cudaStream_t st) {
+int launch_sort_positions_fp64(const Geom& g, Scratch s, const double* r, cudaStream_t st) {
   s.cursor = nullptr;  // ranks from the counting atomics
   launch_zero_i32(s.count, g.ncell, st);
   if (g.pow2a)
@@ -1128,8 +1127,18 @@ int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const dou
   launch_scan(s.count, s.offset, s.partial, g.ncell, st);
   launch_scatter(g, s, nullptr, st);
   launch_sort_segments(g, s, st);
+  return 7;  // kernels launched: zero, keys, scan (3), scatter, in-cell sort
+}
+
+int launch_gather_state_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
+                             const double* m_by_id, double* m_dst, cudaStream_t st) {
   k_gather_state_aos<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.perm, r, v, b, m_by_id, m_dst);
-  return 8;  // kernels launched: zero, keys, scan (3), scatter, in-cell sort, gather
+  return 1;
+}
+
+int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
+                                 const double* m_by_id, double* m_dst, cudaStream_t st) {
+  return launch_sort_positions_fp64(g, s, r, st) + launch_gather_state_fp64(g, b, s, r, v, m_by_id, m_dst, st);
 }
 
 void launch_add_momentum_fp64(const Geom& g, Fp64Bufs b, int cur, Fp64Mass ms, const double* dp, cudaStream_t st) {

@@ -2128,6 +2128,33 @@ void launch_get_state_mixed(const MixBatch& mb, MixBufs b, int cur, double* r, d
   k_get_state_mixed<<<grid_for(mb.n), kThreads, 0, st>>>(mb, b.rec[cur], r, v);
 }
 
+// The two halves of the single-box check, for a state whose positions arrive before its
+// velocities: the lowest failing index over both lands in *bad (atomicMin), as with the whole.
+__global__ void __launch_bounds__(kThreads) k_check_positions_box(int64_t n, Geom g, const double* __restrict__ r,
+                                                                  unsigned long long* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ok = ok && r[3 * i + d] >= 0.0 && r[3 * i + d] < g.B[d];
+    if (!ok) atomicMin(bad, static_cast<unsigned long long>(i));
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_check_velocities(int64_t n, const double* __restrict__ v,
+                                                               unsigned long long* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (!(isfinite(v[3 * i]) && isfinite(v[3 * i + 1]) && isfinite(v[3 * i + 2])))
+      atomicMin(bad, static_cast<unsigned long long>(i));
+}
+
+void launch_check_positions(const Geom& g, int64_t n, const double* r, unsigned long long* bad, cudaStream_t st) {
+  k_check_positions_box<<<grid_for(n), kThreads, 0, st>>>(n, g, r, bad);
+}
+
+void launch_check_velocities(int64_t n, const double* v, unsigned long long* bad, cudaStream_t st) {
+  k_check_velocities<<<grid_for(n), kThreads, 0, st>>>(n, v, bad);
+}
+
 void launch_check_state(const MixBatch* mb, const Geom& g, int64_t n, const double* r, const double* v,
                         unsigned long long* bad, cudaStream_t st) {
   if (mb)

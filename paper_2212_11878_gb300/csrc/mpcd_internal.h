@@ -150,6 +150,11 @@ void launch_sort_segments(const Geom& g, Scratch s, cudaStream_t st);
 int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaStream_t st);
 // A state in particle-id order (N x 3 arrays r, v; masses m_by_id or null) written straight
 // into buffer set 1 in that cell order (m_dst: the masses in storage order); returns launches.
+// The two halves of launch_set_state_sorted_fp64: the cell order from the positions alone
+// (scratch arrays only), then the gather of the state into buffer set 1.
+int launch_sort_positions_fp64(const Geom& g, Scratch s, const double* r, cudaStream_t st);
+int launch_gather_state_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
+                             const double* m_by_id, double* m_dst, cudaStream_t st);
 int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
                                  const double* m_by_id, double* m_dst, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
@@ -235,6 +240,8 @@ void launch_add_momentum_mixed(const MixBatch& mb, MixBufs b, int cur, MixMass m
 void launch_set_state_mixed(const MixBatch& mb, MixBufs b, const double* r, const double* v, cudaStream_t st);
 // First invalid particle of a state (position outside its box, non-finite velocity) into
 // *bad, which the caller sets to ~0 first: per box of *mb, or for the single box g if mb is NULL.
+void launch_check_positions(const Geom& g, int64_t n, const double* r, unsigned long long* bad, cudaStream_t st);
+void launch_check_velocities(int64_t n, const double* v, unsigned long long* bad, cudaStream_t st);
 void launch_check_state(const MixBatch* mb, const Geom& g, int64_t n, const double* r, const double* v,
                         unsigned long long* bad, cudaStream_t st);
 

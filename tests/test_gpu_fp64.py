@@ -473,3 +473,53 @@ def test_host_state_copy_matches_device_copy(L, resort_k):
         abi.mpcd_get_state_device(box.h, rd.data_ptr(), vd.data_ptr())
         box.sync()
         assert np.array_equal(rh, rd.cpu().numpy()) and np.array_equal(vh, vd.cpu().numpy())
+
+
+@pytest.mark.parametrize("masses", [False, True])
+def test_host_state_upload_matches_device_upload(masses):
+    """mpcd_set_state's overlapped host upload (FP64, 65,536 particles or more: the positions'
+    check and cell-order sort run while the velocities are still being copied) stores exactly
+    what mpcd_set_state_device stores: identical storage order, identical steps after it.  A
+    state with a bad position or velocity is rejected with the lowest failing id and leaves the
+    particles unchanged."""
+    torch = pytest.importorskip("torch")
+    p = abi.make_params((41, 40, 40), seed=29, resort_k=3)
+    rng = np.random.default_rng(30)
+    with abi.Box(p) as a, abi.Box(p) as b:
+        assert a.n >= 65536
+        if masses:
+            m = rng.uniform(0.5, 3.0, a.n)
+            a.set_masses(m)
+            b.set_masses(m)
+        r = rng.uniform(0.0, 1.0, (a.n, 3)) * np.array([41.0, 40.0, 40.0])
+        v = rng.standard_normal((a.n, 3))
+        a.set_state(r, v, 5)
+        rd, vd = torch.from_numpy(r).cuda(), torch.from_numpy(v).cuda()
+        torch.cuda.synchronize()
+        abi.mpcd_set_state_device(b.h, rd.data_ptr(), vd.data_ptr(), 5)
+        b.sync()
+        del rd, vd
+        ra, va = a.state()
+        rb, vb = b.state()
+        assert np.array_equal(ra, rb) and np.array_equal(va, vb)
+        a.step(4)
+        b.step(4)
+        assert np.array_equal(a.debug_sort()["perm"], b.debug_sort()["perm"])
+        sa, sb = a.state(), b.state()
+        assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+        for bad_pos, bad_vel in ((70001, None), (None, 66000), (70001, 66000)):
+            rr, vv = r.copy(), v.copy()
+            if bad_pos is not None:
+                rr[bad_pos, 2] = 40.0                    # on the upper face: outside [0, L a)
+            if bad_vel is not None:
+                vv[bad_vel, 0] = np.nan
+            with pytest.raises(abi.MpcdError) as e:
+                a.set_state(rr, vv, 9)
+            assert e.value.code == abi.MPCD_ERR_ARG
+            assert str(min(x for x in (bad_pos, bad_vel) if x is not None)) in str(e.value)
+            now = a.state()
+            assert np.array_equal(now[0], sa[0]) and np.array_equal(now[1], sa[1])
+        a.step(2)
+        b.step(2)
+        sa, sb = a.state(), b.state()
+        assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
