@@ -615,10 +615,12 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
     if ((rc = build_groups(h))) return bail(rc);
     if ((rc = upload_shifts(h, 0))) return bail(rc);
   } else {
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 2; ++k) {  // one block per buffer set: r (3 n doubles), then v (3 n)
+      double* set = nullptr;
+      if ((rc = dalloc(h, &set, 6 * n))) return bail(rc);
       for (int d = 0; d < 3; ++d) {
-        if ((rc = dalloc(h, &h->f64.r[k][d], n))) return bail(rc);
-        if ((rc = dalloc(h, &h->f64.v[k][d], n))) return bail(rc);
+        h->f64.r[k][d] = set + d * n;
+        h->f64.v[k][d] = set + (3 + d) * n;
       }
       if ((rc = dalloc(h, &h->f64.id[k], n))) return bail(rc);
     }

@@ -857,7 +857,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scra
 // cell; on re-sort steps slot i of the other buffer set gathers its particle from storage
 // slot perm[i].
 template <int FORCE, int POW2A, int MASS, int ANG>
-__global__ void __launch_bounds__(kThreads, 4) k_rotate_stream(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
+__global__ void __launch_bounds__(kThreads, ANG ? 4 : 5) k_rotate_stream(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
                                                               Fp64Mass ms) {
   const int64_t t = ctl->t;
   const bool resort = g.resort_k > 0 && (t % g.resort_k) == 0;
@@ -867,16 +867,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate_stream(Geom g, Fp64Bufs 
   int32_t* __restrict__ kout = keys_of(s, t + 1);
   const double shn[3] = {ctl->shift[0], ctl->shift[1], ctl->shift[2]};  // step t + 1
   const double shl[3] = {ctl->shift_last[0], ctl->shift_last[1], ctl->shift_last[2]};  // step t
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
+  // the buffer sets' r and v from one base each (the layout of a handle's allocation): six
+  // array pointers fewer in registers, five blocks of 256 per SM
+  const int64_t n = g.n;
+  const double* Ssrc = b.r[src][0];  // the same set as Scur on ordinary steps: no __restrict__
+  double* Scur = b.r[cur][0];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t si = resort ? (int64_t)s.perm[i] : i;
     double r[3], v[3];
     bool rot;
     if (ANG) {
       RotSlot q;
       rotate_load<ANG>(b, s, kin, si, src, q);
-      r[0] = b.r[src][0][si];
-      r[1] = b.r[src][1][si];
-      r[2] = b.r[src][2][si];
+      r[0] = Ssrc[0 + si];
+      r[1] = Ssrc[n + si];
+      r[2] = Ssrc[2 * n + si];
       rot = (__double2hiint(q.f[6].x) | __double2loint(q.f[6].x)) != 0;  // flag 1 or 0, as bits
       v[0] = q.v[0];
       v[1] = q.v[1];
@@ -884,12 +889,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate_stream(Geom g, Fp64Bufs 
       if (rot) rotate_apply<ANG>(g, q.f, r, shl, v[0], v[1], v[2]);  // l_i on step t's grid
     } else {  // float-float frame, loaded row by row as it is applied
       const float4* __restrict__ rec = reinterpret_cast<const float4*>(s.frame + kFrameStride * (int64_t)kin[si]);
-      v[0] = b.v[src][0][si];
-      v[1] = b.v[src][1][si];
-      v[2] = b.v[src][2][si];
-      r[0] = b.r[src][0][si];
-      r[1] = b.r[src][1][si];
-      r[2] = b.r[src][2][si];
+      v[0] = Ssrc[3 * n + si];
+      v[1] = Ssrc[4 * n + si];
+      v[2] = Ssrc[5 * n + si];
+      r[0] = Ssrc[0 + si];
+      r[1] = Ssrc[n + si];
+      r[2] = Ssrc[2 * n + si];
       rot = rec[6].x != 0.0f;
       if (rot) ff_apply_frame_rows(rec, v[0], v[1], v[2]);
     }
@@ -897,13 +902,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_rotate_stream(Geom g, Fp64Bufs 
     const int32_t pid = resort ? b.id[src][si] : 0;
     const double pm = (MASS && resort) ? ms.m[src][si] : 0.0;
     const int k = move_and_key<0, FORCE, POW2A>(g, r, v, shn);
-    b.r[cur][0][dst] = r[0];
-    b.r[cur][1][dst] = r[1];
-    b.r[cur][2][dst] = r[2];
+    Scur[0 + dst] = r[0];
+    Scur[n + dst] = r[1];
+    Scur[2 * n + dst] = r[2];
     if (resort || rot || FORCE) {
-      b.v[cur][0][dst] = v[0];
-      b.v[cur][1][dst] = v[1];
-      b.v[cur][2][dst] = v[2];
+      Scur[3 * n + dst] = v[0];
+      Scur[4 * n + dst] = v[1];
+      Scur[5 * n + dst] = v[2];
     }
     if (resort) {
       b.id[cur][dst] = pid;

@@ -55,7 +55,10 @@ struct Ctl {
   float sf_next[3];     // shift of step t + 2 in cell units (mixed form)
 };
 
-// FP64 particle state, structure of arrays, two buffer sets for out-of-place re-sorting.
+// FP64 particle state, structure of arrays, two buffer sets for out-of-place re-sorting.  In
+// a handle each set is one allocation, r[k][d] = r[k][0] + d n and v[k][d] = r[k][0] + (3 + d) n
+// (the fused rotate-and-stream pass addresses all six from r[k][0]); the allocation-free step
+// passes the caller's six arrays and never runs that pass.
 struct Fp64Bufs {
   double* r[2][3];
   double* v[2][3];
