@@ -83,7 +83,7 @@ ALGO_STEP_BYTES_MIXED = 64.0
 # DRAM bytes (read + write) per particle of a kernel from one ncu capture of the current build,
 # scaled to a launch by the particle count; a kernel changed since its capture has none.
 NCU_TRAFFIC = {("mixed", "collide"): (72.07, "profiles/mixed_L128_collide_stream_full.md (128^3 capture)"),
-               ("fp64", "rotate_stream"): (105.0, "profiles/fp64_L64_rotate_stream_full.md (64^3 capture of an "
+               ("fp64", "rotate_stream"): (111.0, "profiles/fp64_L64_rotate_stream_full.md (64^3 capture of an "
                                                   "ordinary, non-re-sort launch, scaled by the particle count)")}
 # timed beside an FP64 run: the mixed form at 256^3, the 256-box ensemble, the walled
 # channel with each cell thermostat, the angular-momentum-conserving collision and per-particle
