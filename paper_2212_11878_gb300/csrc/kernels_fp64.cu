@@ -282,11 +282,17 @@ __device__ __forceinline__ void cell_sums(const Fp64Bufs& b, int cur, int32_t* p
   fx_zero(ae);
   bool ok = true;
   int j = 0;
+  // the next round's perm entries are loaded while this round's velocities are in flight
+  int nx[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) nx[k] = k < n ? pm[k] : 0;
   for (; j + U <= n; j += U) {
     int ii[U];
     double x[U], y[U], z[U];
 #pragma unroll
-    for (int k = 0; k < U; ++k) ii[k] = pm[j + k];
+    for (int k = 0; k < U; ++k) ii[k] = nx[k];
+#pragma unroll
+    for (int k = 0; k < U; ++k) nx[k] = j + U + k < n ? pm[j + U + k] : 0;
 #pragma unroll
     for (int k = 0; k < U; ++k) {
       x[k] = vx[ii[k]];
@@ -302,7 +308,9 @@ __device__ __forceinline__ void cell_sums(const Fp64Bufs& b, int cur, int32_t* p
     }
   }
   for (; j < n; ++j) {
-    const int i = pm[j];
+    const int i = nx[0];  // the tail has fewer than U members, all prefetched
+#pragma unroll
+    for (int k = 0; k + 1 < U; ++k) nx[k] = nx[k + 1];
     const double v0 = vx[i], v1 = vy[i], v2 = vz[i];
     ok &= fx_add(a0, v0);
     ok &= fx_add(a1, v1);
