@@ -17,6 +17,8 @@
 // the streaming FMA and the r - s of the cell key (bit-exact keys), the nine FMAs of the
 // rotation and the per-cell frame.  Wraps, floors and the cell sums run on the integer
 // pipe (cellmath.cuh).
+#include <climits>
+
 #include "cellmath.cuh"
 #include "device_common.cuh"
 #include "mpcd_internal.h"
@@ -253,7 +255,34 @@ __global__ void __launch_bounds__(kThreads) k_scatter(int64_t n, Scratch s, cons
 
 // Insertion sort of a cell's perm entries: the counting atomics hand out arrival ranks in
 // no fixed order, the linked-cell list keeps storage order inside a cell.
+// Up to 16 entries: a bitonic sorting network in registers (compile-time indices, the loads
+// all in flight at once); the same order as the insertion sort, which takes larger cells.
 __device__ __forceinline__ void sort_entries(int32_t* pm, int n) {
+  if (n <= 16) {
+    int a[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = i < n ? pm[i] : INT_MAX;
+#pragma unroll
+    for (int k = 2; k <= 16; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int l = i ^ j;
+          if (l > i) {
+            const int x = a[i], y = a[l];
+            const bool up = (i & k) == 0;
+            a[i] = up ? min(x, y) : max(x, y);
+            a[l] = up ? max(x, y) : min(x, y);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (i < n) pm[i] = a[i];
+    return;
+  }
   for (int j = 1; j < n; ++j) {
     const int x = pm[j];
     int k = j - 1;
