@@ -84,6 +84,8 @@ CASES = {
     "mass_dt": dict(L=(6, 6, 6), mass=1.7, dt=0.37, kT=2.5, alpha_deg=77.0),
     "no_resort": dict(L=(8, 8, 8), resort_k=0),
     "resort_3": dict(L=(8, 8, 8), resort_k=3),
+    "dense_resort_1": dict(L=(4, 4, 4), ppc=40, resort_k=1),     # cells above 16 members re-sorted
+    "sparse_resort_1": dict(L=(9, 8, 7), ppc=3, resort_k=1),     # every cell through the network
     "force": dict(L=(6, 6, 6), g=(0.01, -0.02, 0.005)),
     "walls": dict(L=(6, 5, 8), walls_z=1, g=(0.01, 0.0, 0.0)),
     "walls_thermo": dict(L=(6, 5, 8), walls_z=1, g=(0.02, 0.0, 0.0), thermostat=1, ppc=15),
