@@ -41,7 +41,7 @@ UNIT = "particle updates/s"
 # Algorithmic HBM bytes per launch of each kernel, as (bytes per particle, bytes per cell):
 # what the kernel must read and write once (state, keys, ranks, perm, counts, offsets).
 FP64_BYTES = {
-    "zero_counts": (0.0, 4.0),
+    "zero_counts": (0.0, 8.0),   # counts and cursors
     "stream_bin": (48.0 + 24.0 + 8.0, 4.0),
     "scan": (0.0, 12.0),
     "scatter": (12.0, 4.0),
@@ -69,7 +69,7 @@ ALGO_STEP_BYTES_FP64 = 96.0             # state read + written once per step
 # mixed form: 32-byte records; collide_stream gathers through perm, writes in cell order and
 # writes the next step's keys and ranks
 MIXED_BYTES = {
-    "zero_counts": (0.0, 4.0),
+    "zero_counts": (0.0, 8.0),   # counts and cursors
     "stream_bin": (32.0 + 8.0, 4.0),     # first step only
     "scan": (0.0, 12.0),
     "scatter": (12.0, 4.0),
@@ -478,7 +478,7 @@ def main():
             if fens:  # the ensemble's tile shape, block size and launch form: the autotuner's choice
                 best, best_ms = abi.mpcd_autotune(fbox.h, trial_steps=5)
                 tuned = dict(best.as_dict(), ms_per_step_in_trial=best_ms,
-                             candidates="group_target {128..176} x warps {2,4} x fuse {1,0} (one launch per step or nine)")
+                             candidates="group_target {128..176} x warps {2,4} x fuse {1,0} (one launch per step or eight)")
             fbox.step(args.warmup)
             fbox.sync()
             fval, fms, fl, fkt, _ = timed_steps(abi, torch, dist, fbox, stream, args.form_steps, world)

@@ -218,7 +218,7 @@ typedef struct {
                         /*   conservation): 1 runs a whole step as one persistent cooperative */
                         /*   launch whose phases (zeroing, scan, scatter, group table,        */
                         /*   collision, step end) are separated by bounded grid-wide barriers */
-                        /*   (MPCD_ERR_TIMEOUT if one waits too long), 0 as nine launches.    */
+                        /*   (MPCD_ERR_TIMEOUT if one waits too long), 0 as eight launches.   */
                         /*   Identical results either way.                                    */
 } mpcd_tuning;
 

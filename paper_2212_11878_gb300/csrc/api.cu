@@ -311,10 +311,7 @@ int enqueue_piece(mpcd_t* h, int piece, bool moments, int par = 0) {
       if (le != cudaSuccess) return cuda_fail(h, le, "one-launch step");
       return MPCD_OK;
     }
-    if ((rc = run_slot(h, kSlotZero, [&] {
-           launch_zero_i32(m.count[nx], g.ncell, h->stream);
-           launch_zero_i32(m.cursor, g.ncell, h->stream);
-         })))
+    if ((rc = run_slot(h, kSlotZero, [&] { launch_zero_i32_pair(m.count[nx], m.cursor, g.ncell, h->stream); })))
       return rc;
     if ((rc = run_slot(h, kSlotScan, [&] { launch_scan(m.count[par], m.offset, m.partial, g.ncell, h->stream); })))
       return rc;
@@ -336,11 +333,7 @@ int enqueue_piece(mpcd_t* h, int piece, bool moments, int par = 0) {
     if ((rc = enqueue_piece(h, kPieceFull, moments, par))) return rc;
     return enqueue_piece(h, kPieceTail, moments, par);
   }
-  if ((rc = run_slot(h, kSlotZero, [&] {
-         launch_zero_i32(s.count, g.ncell, h->stream);
-         launch_zero_i32(s.cursor, g.ncell, h->stream);
-       })))
-    return rc;
+  if ((rc = run_slot(h, kSlotZero, [&] { launch_zero_i32_pair(s.count, s.cursor, g.ncell, h->stream); }))) return rc;
   if (piece == kPieceBody) {
     if ((rc = run_slot(h, kSlotRotateStream,
                        [&] { launch_rotate_stream_fp64(g, h->f64, s, h->ctl, h->stream, h->f64m); })))
@@ -534,7 +527,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->tune.group_target = 168;
   h->tune.warps = 4;
   h->tune.resort_k = p[0].resort_k;
-  // FP64: the fused rotate-and-stream pass is faster; mixed: the nine-launch step is (its
+  // FP64: the fused rotate-and-stream pass is faster; mixed: the eight-launch step is (its
   // sort phases run at full occupancy), the one-launch step remains a tuning choice
   h->tune.fuse = p[0].precision == MPCD_FP64 ? 1 : 0;
   // per-box geometry; the handle's geom describes the whole concatenation for the kernels
@@ -560,7 +553,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   h->geom.n = ntot;
   h->geom.ncell = ctot;
   for (int k = 0; k < kNumSlots; ++k) h->per_step[k] = kSlotLaunchesBase[k];
-  h->per_step[kSlotZero] = 2;  // counts and the scatter's cursors
+  h->per_step[kSlotZero] = 1;  // counts and the scatter's cursors, one launch
   if (!h->geom.walls && !h->geom.thermostat) h->per_step[kSlotRotate] = h->per_step[kSlotRotateStream] = 1;
   h->n = ntot;
   h->ncell = ctot;
@@ -578,7 +571,7 @@ int create_common(const mpcd_params* p, int32_t nbox, mpcd_t** out) {
   if (h->precision == MPCD_MIXED) {
     if ((e = prepare_collide_mixed()) != cudaSuccess) return bail(cuda_fail(h, e, "collide kernel setup"));
     h->per_step[kSlotStreamBin] = 0;  // binning is fused into the collide kernel
-    h->per_step[kSlotZero] = 2;
+    h->per_step[kSlotZero] = 1;
     h->per_step[kSlotScatter] = 2;  // scatter + group bounds
     h->per_step[kSlotCollide] = 1;
     h->per_step[kSlotRotate] = h->per_step[kSlotRotateStream] = 0;

@@ -114,6 +114,20 @@ __global__ void __launch_bounds__(kThreads) k_scan_final(const int32_t* __restri
 
 int scan_tiles(int64_t count) { return static_cast<int>((count + kTile - 1) / kTile); }
 
+__global__ void __launch_bounds__(kThreads) k_zero_i32_pair(int32_t* p, int32_t* q, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    p[i] = 0;
+    q[i] = 0;
+  }
+}
+
+void launch_zero_i32_pair(int32_t* p, int32_t* q, int64_t n, cudaStream_t st) {
+  if (n <= 0) return;
+  int64_t blocks = (n + kThreads * 4 - 1) / (kThreads * 4);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_zero_i32_pair<<<static_cast<unsigned>(blocks), kThreads, 0, st>>>(p, q, n);
+}
+
 void launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st) {
   if (n <= 0) return;
   int64_t blocks = (n + kThreads * 4 - 1) / (kThreads * 4);

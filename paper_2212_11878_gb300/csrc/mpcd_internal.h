@@ -124,6 +124,7 @@ struct Scratch {
 // ---- kernel launchers (kernels_*.cu).  All are asynchronous on `st`. ----
 int scan_tiles(int64_t count);
 void launch_zero_i32(int32_t* p, int64_t n, cudaStream_t st);
+void launch_zero_i32_pair(int32_t* p, int32_t* q, int64_t n, cudaStream_t st);  // both arrays, one launch
 void launch_scan(const int32_t* count, int32_t* offset, int32_t* partial, int64_t n, cudaStream_t st);
 
 void launch_init_fp64(const Geom& g, Fp64Bufs b, double* red, int red_blocks, Ctl* ctl, cudaStream_t st);

@@ -152,7 +152,7 @@ def test_tunings_give_identical_results():
                          ids=["periodic", "mbs", "walls_thermostat", "sparse"])
 def test_one_launch_step_equals_launch_sequence(extra, boxes):
     """The mixed step as one persistent cooperative launch (tuning fuse = 1, the default) and
-    as its nine-launch sequence (fuse = 0) give the same bits, over several mpcd_step calls,
+    as its eight-launch sequence (fuse = 0) give the same bits, over several mpcd_step calls,
     with per-cell moments recorded; the one-launch form launches one kernel per step."""
     params = [abi.make_params(precision="mixed", **k, **extra) for k in boxes]
     outs = []
@@ -167,7 +167,7 @@ def test_one_launch_step_equals_launch_sequence(extra, boxes):
             per_step = (abi.mpcd_launch_count(ens.h) - l0) / 5
             mom, _ = ens.moments()
             outs.append((ens.state(), mom, ens.debug_sort()))
-        assert per_step == (1 if fuse else 9)
+        assert per_step == (1 if fuse else 8)
     (r1, v1), m1, d1 = outs[0]
     (r0, v0), m0, d0 = outs[1]
     assert np.array_equal(r1, r0) and np.array_equal(v1, v0) and np.array_equal(m1, m0)
