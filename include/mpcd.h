@@ -138,10 +138,11 @@ int mpcd_get_state(mpcd_t* h, double* r, double* v);
  * Listing 1 `permute` applied once, so that the first steps already find each cell's members
  * in neighbouring slots; the mixed form keeps id order until its first step.  Storage order
  * is visible only through mpcd_debug_sort.  FP64 form with 65,536 particles or more: the
- * positions are uploaded first, and their check and the cell-order sort run on a second
- * stream while the velocities are still being copied; a rejected state then still leaves the
- * particles unchanged, but the last step's sort record is gone (mpcd_debug_sort returns
- * MPCD_ERR_STATE until the next step).  Synchronises. */
+ * positions are uploaded first, and their check, the cell-order sort and their gather run on
+ * a second stream while the velocities are still being copied, into the buffer set that does
+ * not hold the current state; a rejected state then still leaves the particles unchanged, but
+ * the last step's sort record is gone (mpcd_debug_sort returns MPCD_ERR_STATE until the next
+ * step).  Synchronises. */
 int mpcd_set_state(mpcd_t* h, int64_t n, const double* r, const double* v, int64_t t);
 
 /* Per-particle masses (the m of the cell sums sum m v and sum m, Sec. 3.3 Listing 4):

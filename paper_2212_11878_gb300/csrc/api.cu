@@ -920,20 +920,21 @@ static int check_state(mpcd_t* h, const double* r_dev, const double* v_dev) {
 }
 
 // Apply a checked state.  FP64: straight into cell order (the initial sort, R25) in buffer
-// set 1, masses along; `sorted`: the cell order was already built from r_dev (scratch only).
-static int apply_state(mpcd_t* h, int64_t n, const double* r_dev, const double* v_dev, int64_t t, bool sorted) {
+// set 1, masses along; gathered >= 0: the state already stands in cell order in that buffer
+// set (the overlapped host upload), which becomes the current one.
+static int apply_state(mpcd_t* h, int64_t n, const double* r_dev, const double* v_dev, int64_t t, int gathered) {
   int rc = MPCD_OK;
   h->cur = 0;
-  if (h->precision == MPCD_MIXED) {
+  if (gathered >= 0) {
+    h->cur = gathered;
+  } else if (h->precision == MPCD_MIXED) {
     launch_set_state_mixed(h->mb, h->mix, r_dev, v_dev, h->stream);
     if (h->masses)  // the new records are in particle-id order
       launch_gather_masses_mixed(n, h->mix.rec[0], h->mass_buf[2], h->mix_mass_buf[0], h->stream);
   } else if (n > 0) {
     const double* m_by_id = h->masses ? h->mass_buf[2] : nullptr;
     double* m_dst = h->masses ? h->mass_buf[1] : nullptr;
-    h->launches += sorted ? launch_gather_state_fp64(h->geom, h->f64, h->scr, r_dev, v_dev, m_by_id, m_dst, h->stream)
-                          : launch_set_state_sorted_fp64(h->geom, h->f64, h->scr, r_dev, v_dev, m_by_id, m_dst,
-                                                         h->stream);
+    h->launches += launch_set_state_sorted_fp64(h->geom, h->f64, h->scr, r_dev, v_dev, m_by_id, m_dst, h->stream);
     h->cur = 1;
   }
   MPCD_TRY(h, cudaGetLastError());
@@ -959,13 +960,14 @@ int mpcd_set_state_device(mpcd_t* h, int64_t n, const double* r_dev, const doubl
   if (n != h->n) return fail(h, MPCD_ERR_ARG, "n must equal mpcd_num_particles");
   if (!r_dev || !v_dev || t < 0) return fail(h, MPCD_ERR_ARG, "NULL input or negative t");
   if ((rc = check_state(h, r_dev, v_dev))) return rc;
-  return apply_state(h, n, r_dev, v_dev, t, false);
+  return apply_state(h, n, r_dev, v_dev, t, -1);
 }
 
-// FP64 host upload of a large state: the positions go first, and their check and the whole
-// cell-order sort (scratch arrays only) run on the second stream while the velocities are
-// still being copied; the velocities are checked on arrival, and only a state that passes
-// both checks is gathered into the step buffers.
+// FP64 host upload of a large state, gathered into the buffer set that does not hold the
+// current state: the positions go first, and their check, the whole cell-order sort and their
+// gather run on the second stream while the velocities are still being copied; the
+// velocities are checked and gathered on arrival.  One synchronisation at the end: a state
+// that failed a check is never made current, so the current one stays as it was.
 static int set_state_overlapped(mpcd_t* h, int64_t n, const double* r, const double* v, int64_t t,
                                 double* scratch) {
   if (!h->copy_stream) {
@@ -973,6 +975,9 @@ static int set_state_overlapped(mpcd_t* h, int64_t n, const double* r, const dou
     h->chunk_events.assign(8, nullptr);
     for (auto& ev : h->chunk_events) MPCD_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
   }
+  const int target = h->cur ^ 1;
+  const double* m_by_id = h->masses ? h->mass_buf[2] : nullptr;
+  double* m_dst = h->masses ? h->mass_buf[target] : nullptr;
   double* r_dev = scratch;
   double* v_dev = scratch + 3 * n;
   MPCD_TRY(h, cudaMemsetAsync(h->d_bad, 0xFF, sizeof(unsigned long long), h->stream));
@@ -982,12 +987,15 @@ static int set_state_overlapped(mpcd_t* h, int64_t n, const double* r, const dou
   MPCD_TRY(h, cudaStreamWaitEvent(h->copy_stream, h->chunk_events[0], 0));
   launch_check_positions(h->geom, n, r_dev, h->d_bad, h->copy_stream);
   h->launches += 1 + launch_sort_positions_fp64(h->geom, h->scr, r_dev, h->copy_stream);
+  MPCD_TRY(h, cudaEventRecord(h->chunk_events[1], h->copy_stream));  // perm is ready
+  h->launches += launch_gather_positions_fp64(h->geom, h->f64, h->scr, r_dev, target, h->copy_stream);
   MPCD_TRY(h, cudaGetLastError());
-  MPCD_TRY(h, cudaEventRecord(h->chunk_events[1], h->copy_stream));
+  MPCD_TRY(h, cudaEventRecord(h->chunk_events[2], h->copy_stream));
   launch_check_velocities(n, v_dev, h->d_bad, h->stream);
-  h->launches += 1;
-  MPCD_TRY(h, cudaGetLastError());
   MPCD_TRY(h, cudaStreamWaitEvent(h->stream, h->chunk_events[1], 0));
+  h->launches += 1 + launch_gather_velocities_fp64(h->geom, h->f64, h->scr, v_dev, target, m_by_id, m_dst, h->stream);
+  MPCD_TRY(h, cudaGetLastError());
+  MPCD_TRY(h, cudaStreamWaitEvent(h->stream, h->chunk_events[2], 0));
   unsigned long long bad = 0;
   MPCD_TRY(h, cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
@@ -995,7 +1003,7 @@ static int set_state_overlapped(mpcd_t* h, int64_t n, const double* r, const dou
     h->any_step = false;  // the last step's sort record was overwritten by this one
     return fail(h, MPCD_ERR_ARG, "position outside its box or non-finite velocity at particle " + std::to_string(bad));
   }
-  int rc = apply_state(h, n, r_dev, v_dev, t, true);
+  int rc = apply_state(h, n, r_dev, v_dev, t, target);
   if (rc) return rc;
   MPCD_TRY(h, cudaStreamSynchronize(h->stream));
   return MPCD_OK;

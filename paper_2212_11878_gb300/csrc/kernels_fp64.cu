@@ -1113,19 +1113,24 @@ __global__ void __launch_bounds__(kThreads) k_presort_keys_aos(Geom g, const dou
   }
 }
 
+// PARTS: 1 positions and ids, 2 velocities and masses, 3 both; into buffer set `set`.
+template <int PARTS>
 __global__ void __launch_bounds__(kThreads) k_gather_state_aos(int64_t n, const int32_t* __restrict__ perm,
                                                               const double* __restrict__ r, const double* __restrict__ v,
-                                                              Fp64Bufs b, const double* __restrict__ m_by_id,
+                                                              Fp64Bufs b, int set, const double* __restrict__ m_by_id,
                                                               double* __restrict__ m_dst) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = perm[j];
+    if (PARTS & 1) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      b.r[1][d][j] = r[3 * i + d];
-      b.v[1][d][j] = v[3 * i + d];
+      for (int d = 0; d < 3; ++d) b.r[set][d][j] = r[3 * i + d];
+      b.id[set][j] = static_cast<int32_t>(i);
     }
-    b.id[1][j] = static_cast<int32_t>(i);
-    if (m_by_id) m_dst[j] = m_by_id[i];
+    if (PARTS & 2) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) b.v[set][d][j] = v[3 * i + d];
+      if (m_by_id) m_dst[j] = m_by_id[i];
+    }
   }
 }
 
@@ -1176,7 +1181,18 @@ int launch_sort_positions_fp64(const Geom& g, Scratch s, const double* r, cudaSt
 
 int launch_gather_state_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
                              const double* m_by_id, double* m_dst, cudaStream_t st) {
-  k_gather_state_aos<<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.perm, r, v, b, m_by_id, m_dst);
+  k_gather_state_aos<3><<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.perm, r, v, b, 1, m_by_id, m_dst);
+  return 1;
+}
+
+int launch_gather_positions_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, int set, cudaStream_t st) {
+  k_gather_state_aos<1><<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.perm, r, nullptr, b, set, nullptr, nullptr);
+  return 1;
+}
+
+int launch_gather_velocities_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* v, int set,
+                                  const double* m_by_id, double* m_dst, cudaStream_t st) {
+  k_gather_state_aos<2><<<grid_for(g.n), kThreads, 0, st>>>(g.n, s.perm, nullptr, v, b, set, m_by_id, m_dst);
   return 1;
 }
 

@@ -159,6 +159,10 @@ int launch_presort_fp64(const Geom& g, Fp64Bufs b, Scratch s, Fp64Mass ms, cudaS
 int launch_sort_positions_fp64(const Geom& g, Scratch s, const double* r, cudaStream_t st);
 int launch_gather_state_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
                              const double* m_by_id, double* m_dst, cudaStream_t st);
+// The gather's two halves into buffer set `set`: positions and ids; velocities and masses.
+int launch_gather_positions_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, int set, cudaStream_t st);
+int launch_gather_velocities_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* v, int set,
+                                  const double* m_by_id, double* m_dst, cudaStream_t st);
 int launch_set_state_sorted_fp64(const Geom& g, Fp64Bufs b, Scratch s, const double* r, const double* v,
                                  const double* m_by_id, double* m_dst, cudaStream_t st);
 void launch_get_state_fp64(const Geom& g, Fp64Bufs b, int cur, double* r, double* v, cudaStream_t st);
