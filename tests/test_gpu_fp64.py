@@ -525,3 +525,18 @@ def test_host_state_upload_matches_device_upload(masses):
         b.step(2)
         sa, sb = a.state(), b.state()
         assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+        # two uploads in a row land in alternate buffer sets: both parities against the device path
+        for t in (20, 21):
+            r2 = rng.uniform(0.0, 1.0, (a.n, 3)) * np.array([41.0, 40.0, 40.0])
+            v2 = rng.standard_normal((a.n, 3))
+            a.set_state(r2, v2, t)
+            rd, vd = torch.from_numpy(r2).cuda(), torch.from_numpy(v2).cuda()
+            torch.cuda.synchronize()
+            abi.mpcd_set_state_device(b.h, rd.data_ptr(), vd.data_ptr(), t)
+            b.sync()
+            del rd, vd
+            a.step(3)
+            b.step(3)
+            sa, sb = a.state(), b.state()
+            assert np.array_equal(sa[0], sb[0]) and np.array_equal(sa[1], sb[1])
+            assert np.array_equal(a.debug_sort()["perm"], b.debug_sort()["perm"])
