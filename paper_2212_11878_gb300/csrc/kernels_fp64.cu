@@ -875,12 +875,38 @@ __device__ __forceinline__ void rotate_finish(const Geom& g, const Fp64Bufs& b, 
 // are applied, ctl->cur the buffer set the particles end up in (flipped on re-sort steps),
 // ctl->shift_last that step's grid shift.
 template <int MASS, int ANG = 0>
-__global__ void __launch_bounds__(kThreads, 4) k_rotate(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
-                                                       Fp64Mass ms) {
+__global__ void __launch_bounds__(kThreads, ANG ? 4 : 5) k_rotate(Geom g, Fp64Bufs b, Scratch s, Ctl* __restrict__ ctl,
+                                                                 Fp64Mass ms) {
   const int64_t t = ctl->t;
   const bool resort = g.resort_k > 0 && (t % g.resort_k) == 0;
   const int src = resort ? ctl->cur ^ 1 : ctl->cur;
   const int32_t* __restrict__ key = keys_of(s, t);
+  if (!ANG) {  // as in the fused pass: the frame row by row, r and v from one base per set
+    const int64_t n = g.n;
+    const int cur = ctl->cur;
+    const double* Ssrc = b.r[src][0];  // the same set as Scur on ordinary steps
+    double* Scur = b.r[cur][0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t si = resort ? (int64_t)s.perm[i] : i;
+      const float4* __restrict__ rec = reinterpret_cast<const float4*>(s.frame + kFrameStride * (int64_t)key[si]);
+      double v0 = Ssrc[3 * n + si], v1 = Ssrc[4 * n + si], v2 = Ssrc[5 * n + si];
+      const bool rot = rec[6].x != 0.0f;
+      if (rot) ff_apply_frame_rows(rec, v0, v1, v2);
+      if (resort) {
+        Scur[i] = Ssrc[si];
+        Scur[n + i] = Ssrc[n + si];
+        Scur[2 * n + i] = Ssrc[2 * n + si];
+        b.id[cur][i] = b.id[src][si];
+        if (MASS) ms.m[cur][i] = ms.m[src][si];
+      }
+      if (resort || rot) {
+        Scur[3 * n + i] = v0;
+        Scur[4 * n + i] = v1;
+        Scur[5 * n + i] = v2;
+      }
+    }
+    return;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     RotSlot q;
     const int64_t si = resort ? (int64_t)s.perm[i] : i;  // re-sort: gather slot i's particle
